@@ -47,7 +47,7 @@ def lib():
             "oracle_sap": [d, d, d, d, d, i, i, i, i, d, d, d],
             "oracle_block_mr": [d, d, d, d, d, l, i, i, d, d],
             "oracle_block_sites": [d, d, l, d],
-            "oracle_fgcr": [d, d, d, d, d, d, i, i, ctypes.c_double, i, d, i, i, i, d, d],
+            "oracle_fgcr": [d, d, d, d, d, d, i, i, ctypes.c_double, i, d, i, i, i, i, d, d],
             "oracle_num_threads": [],
         }.items():
             fn = getattr(_lib, name)
@@ -143,8 +143,10 @@ def block_mr(L, U, A, bc, block, n, rho_blk, nmr, eo=True):
 
 
 def fgcr(L, U, A, bc, b, x0=None, nkv=16, max_restarts=100, tol=1e-12, precond=False,
-         block=(2, 2, 2, 2), ncy=4, nmr=4, eo=True):
-    """Solve D x = b by (F)GCR; returns (x, iterations, cycles, converged, true_rel_res)."""
+         block=(2, 2, 2, 2), ncy=4, nmr=4, eo=True, max_iters=0):
+    """Solve D x = b by (F)GCR; returns (x, iterations, cycles, converged, true_rel_res).
+
+    max_iters > 0 stops after that many iterations (bounded timing samples)."""
     L = _dims(L)
     bs = _dims(block)
     U, A, b = _c128(U), _c128(A), _c128(b)
@@ -153,5 +155,5 @@ def fgcr(L, U, A, bc, b, x0=None, nkv=16, max_restarts=100, tol=1e-12, precond=F
     res = np.zeros(1, np.float64)
     _check(lib().oracle_fgcr(_p(L), _p(U), _p(A), _p(_bc(bc)), _p(b), _p(x), int(nkv),
                              int(max_restarts), float(tol), int(precond), _p(bs), int(ncy), int(nmr),
-                             int(eo), _p(info), _p(res)), "oracle_fgcr")
+                             int(eo), int(max_iters), _p(info), _p(res)), "oracle_fgcr")
     return x, int(info[0]), int(info[1]), bool(info[2]), float(res[0])

@@ -616,49 +616,17 @@ static int geom_init(sap_geom *g, const int L[4], const double *U_, const double
 }
 
 /*
- * One block solve + residual update (Sec. 4 SAP cycle):
- *   chi = MR(D_blk, rho|_blk); psi|_blk += chi;
- *   rho -= D chi_ext on the block and on every site one hop outside it,
- *   where chi_ext is chi extended by zero.
- */
-static int sap_block(const sap_geom *g, long n, int nmr, int eo, cplx *psi, cplx *rho,
-                     cplx *work, long *sites, cplx *rb, cplx *chi, unsigned char *mark, long *outer)
-{
-    block_sites(g, n, sites);
-    for (long k = 0; k < g->Vb; ++k) memcpy(rb + k * 12, rho + sites[k] * 12, sizeof(cplx) * 12);
-    int err = block_mr(g, sites, rb, nmr, eo, work, chi);
-    for (long k = 0; k < g->Vb; ++k)
-        for (int a = 0; a < 12; ++a) psi[sites[k] * 12 + a] += chi[k * 12 + a];
-    /* sites touched by D chi_ext: the block plus its outer neighbours */
-    long nout = 0;
-    for (long k = 0; k < g->Vb; ++k) mark[sites[k]] = 1;
-    for (long k = 0; k < g->Vb; ++k)
-        for (int mu = 0; mu < 4; ++mu)
-            for (int st = -1; st <= 1; st += 2) {
-                long y = shift(g->L, sites[k], mu, st);
-                if (!mark[y]) { mark[y] = 2; outer[nout++] = y; }
-            }
-    for (long k = 0; k < g->Vb; ++k) memcpy(work + sites[k] * 12, chi + k * 12, sizeof(cplx) * 12);
-    cplx tmp[12];
-    for (long k = 0; k < g->Vb; ++k) {
-        dirac_site(g->L, g->U, g->A, g->bc, work, sites[k], 0, tmp);
-        for (int a = 0; a < 12; ++a) rho[sites[k] * 12 + a] -= tmp[a];
-    }
-    for (long k = 0; k < nout; ++k) {
-        dirac_site(g->L, g->U, g->A, g->bc, work, outer[k], 0, tmp);
-        for (int a = 0; a < 12; ++a) rho[outer[k] * 12 + a] -= tmp[a];
-    }
-    for (long k = 0; k < g->Vb; ++k) { memset(work + sites[k] * 12, 0, sizeof(cplx) * 12); mark[sites[k]] = 0; }
-    for (long k = 0; k < nout; ++k) mark[outer[k]] = 0;
-    return err;
-}
-
-/*
- * psi = M_SAP eta: n_cy cycles, each solving all white blocks (even sum of
- * block coordinates) and then all black blocks.  order = 1 visits the blocks
- * of a colour in reverse order (the result must not depend on it).
- * rho_out (optional) receives the final SAP residual eta - D psi as updated by
- * the procedure.
+ * psi = M_SAP eta (Sec. 4): n_cy cycles; each cycle first solves the equation
+ * on all white blocks (even sum of block coordinates), then updates the
+ * residue on the white blocks and on the border of the black blocks, then does
+ * the same for the black blocks.  Within one colour the block solves are
+ * independent (each reads the residue on its own block only), so they are
+ * computed first -- in parallel -- and the combined correction chi (a sum of
+ * corrections with disjoint supports) is then added to psi and its image
+ * D chi subtracted from the residue:  rho <- rho - D chi  changes rho exactly
+ * on the solved blocks and on the sites one hop outside them.
+ * order = 1 visits the blocks of a colour in reverse order (the result must
+ * not depend on it).  rho_out (optional) receives the final residue.
  */
 int oracle_sap(const int L[4], const double *U_, const double *A_, const double bc[4],
                const int b[4], int ncy, int nmr, int eo, int order,
@@ -671,24 +639,46 @@ int oracle_sap(const int L[4], const double *U_, const double *A_, const double 
     long V = g.V;
     cplx *psi = (cplx *)psi_;
     cplx *rho = (cplx *)malloc(sizeof(cplx) * V * 12);
+    cplx *chi_all = (cplx *)malloc(sizeof(cplx) * V * 12);
+    cplx *dchi = (cplx *)malloc(sizeof(cplx) * V * 12);
     memcpy(rho, eta_, sizeof(cplx) * V * 12);
     memset(psi, 0, sizeof(cplx) * V * 12);
-    cplx *work = (cplx *)calloc((size_t)V * 12, sizeof(cplx));
-    long *sites = (long *)malloc(sizeof(long) * g.Vb);
-    long *outer = (long *)malloc(sizeof(long) * g.Vb * 8);
-    cplx *rb = (cplx *)malloc(sizeof(cplx) * g.Vb * 12);
-    cplx *chi = (cplx *)malloc(sizeof(cplx) * g.Vb * 12);
-    unsigned char *mark = (unsigned char *)calloc((size_t)V, 1);
+    long *list = (long *)malloc(sizeof(long) * g.nblk);
     int err = 0;
     for (int cy = 0; cy < ncy; ++cy)
-        for (int colour = 0; colour < 2; ++colour)
+        for (int colour = 0; colour < 2; ++colour) {
+            long nl = 0;
             for (long j = 0; j < g.nblk; ++j) {
                 long n = order ? g.nblk - 1 - j : j;
-                if (block_colour(&g, n) != colour) continue;
-                if (sap_block(&g, n, nmr, eo, psi, rho, work, sites, rb, chi, mark, outer)) err = -3;
+                if (block_colour(&g, n) == colour) list[nl++] = n;
             }
+            memset(chi_all, 0, sizeof(cplx) * V * 12);
+#pragma omp parallel
+            {
+                cplx *work = (cplx *)calloc((size_t)V * 12, sizeof(cplx));
+                long *sites = (long *)malloc(sizeof(long) * g.Vb);
+                cplx *rb = (cplx *)malloc(sizeof(cplx) * g.Vb * 12);
+                cplx *chi = (cplx *)malloc(sizeof(cplx) * g.Vb * 12);
+#pragma omp for schedule(dynamic)
+                for (long j = 0; j < nl; ++j) {
+                    block_sites(&g, list[j], sites);
+                    for (long k = 0; k < g.Vb; ++k) memcpy(rb + k * 12, rho + sites[k] * 12, sizeof(cplx) * 12);
+                    if (block_mr(&g, sites, rb, nmr, eo, work, chi)) {
+#pragma omp atomic write
+                        err = -3;
+                    }
+                    for (long k = 0; k < g.Vb; ++k) memcpy(chi_all + sites[k] * 12, chi + k * 12, sizeof(cplx) * 12);
+                }
+                free(work); free(sites); free(rb); free(chi);
+            }
+            oracle_apply_D(L, U_, A_, bc, (const double *)chi_all, (double *)dchi, 0);
+            for (long e = 0; e < V * 12; ++e) {
+                psi[e] += chi_all[e];
+                rho[e] -= dchi[e];
+            }
+        }
     if (rho_out) memcpy(rho_out, rho, sizeof(cplx) * V * 12);
-    free(rho); free(work); free(sites); free(outer); free(rb); free(chi); free(mark);
+    free(rho); free(chi_all); free(dchi); free(list);
     return err;
 }
 
@@ -734,11 +724,12 @@ int oracle_block_sites(const int L[4], const int b[4], long n, long *sites)
  * and at the end of each cycle solves the small triangular system, updates x
  * and recomputes the true residual b - D x.
  * info[0] = total iterations, info[1] = restart cycles, info[2] = converged,
- * res[0] = final true |b - D x| / |b|.
+ * res[0] = final true |b - D x| / |b|.  max_iters > 0 stops the recursion
+ * after that many iterations in total (a bounded sample for timing).
  */
 int oracle_fgcr(const int L[4], const double *U_, const double *A_, const double bc[4],
                 const double *b_, double *x_, int nkv, int max_restarts, double tol,
-                int precond, const int bs[4], int ncy, int nmr, int eo,
+                int precond, const int bs[4], int ncy, int nmr, int eo, int max_iters,
                 int *info, double *res)
 {
     init_gamma();
@@ -789,6 +780,7 @@ int oracle_fgcr(const int L[4], const double *U_, const double *A_, const double
             ++iters;
             kused = k + 1;
             if (sqrt(creal(dotv(rho, rho, N))) <= tol * bnorm) break;
+            if (max_iters > 0 && iters >= max_iters) break;
         }
         /* back substitution: A gamma = c, A_kk = |chi_k|, A_jk = a_jk (j < k) */
         for (int k = kused - 1; k >= 0; --k) {
@@ -803,6 +795,7 @@ int oracle_fgcr(const int L[4], const double *U_, const double *A_, const double
         rn = sqrt(creal(dotv(r, r, N)));
         ++cycles;
         if (rn <= tol * bnorm) converged = 1;
+        if (max_iters > 0 && iters >= max_iters) break;
     }
 done:
     if (info) { info[0] = iters; info[1] = cycles; info[2] = converged; }
