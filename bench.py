@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark: SAP+FGCR time to |r|/|b| < 1e-10 and D_w GB/s on one GB300.
+
+Workload: 32^3 x 64 lattice, links exp(i 0.5 sum_a g_a lambda_a / 2) (seed 3),
+m0 = -0.05, c_sw = 1.5, antiperiodic time; one complex Gaussian right-hand
+side; SAP on 4^4 blocks (4 MR steps, 4 cycles) with FP16 block fields and FP32
+arithmetic; FGCR(16) with FP64 recursion and FP64 outer operator.  A step is
+one complete solve from x = 0 to a true FP64 residual <= 1e-10.
+
+Every vector of the solve (403 MB each in FP64) and the gauge/clover fields
+exceed the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+The reference arm times the plain FP64 CPU oracle (oracle/) on the host cores:
+each step is one SAP-FGCR iteration of the same solve, extrapolated by the
+iteration count the GPU solve needs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "32^3x64 fp16"
+METRIC = "SAP+FGCR time to |r|/|b|<1e-10 and D_w GB/s vs HBM peak, 1 GB300"
+# algorithmic bytes per site of one operator apply: spinor in + out, 4 links
+# as 12 reals (two rows), 72-real clover; 16-bit adds the per-site scales
+DW_BYTES = {"f64": 1344.0, "f32": 672.0, "f16": 352.0}
+DW_FLOPS = 1824.0  # 1320 hopping + 504 clover per site
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    p = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        p.update({k: d[k] for k in ("hbm_gbs", "sm_max_mhz") if k in d})
+        p["source"] = "measured"
+    mhz = p["sm_max_mhz"]
+    # 152 SMs; 128 FP32 lanes/SM (FMA = 2 flops); 2 FP64 FMA/clk/SM on GB300
+    p["fp32_tflops"] = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    p["fp64_tflops"] = 152 * 2 * 2 * mhz * 1e6 / 1e12
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd[1:1] = ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+def make_inputs():
+    from paper_1109_4279_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    U, rng = synth.gauge_field(w["dims"], w["eps"], w["seed"])
+    b = synth.gaussian_spinor(w["dims"], rng)
+    return w, U, b
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------
+def oracle_iteration_seconds(w, U, b):
+    """One SAP-FGCR iteration of the oracle on the full lattice (all host cores)."""
+    import oracle
+    oracle.build()
+    A = oracle.clover(w["dims"], U, w["m0"], w["csw"])
+    from paper_1109_4279_gb300 import synth
+    t0 = time.perf_counter()
+    oracle.fgcr(w["dims"], U, A, synth.ANTIPERIODIC_T, b, nkv=w["nkv"], max_restarts=1, tol=1e-10, precond=True,
+                block=w["block"], ncy=w["ncy"], nmr=w["nmr"], max_iters=1)
+    return time.perf_counter() - t0, oracle.num_threads()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    w, U, b = make_inputs()
+    iters = args.gpu_iterations
+    times = []
+    threads = 0
+    for k in range(args.warmup + args.steps):
+        t, threads = oracle_iteration_seconds(w, U, b)
+        if k >= args.warmup:
+            times.append(t)
+    t_iter = statistics.median(times)
+    value = t_iter * iters
+    sample = ("one SAP-FGCR iteration of the oracle on the full 32^3x64 lattice per step (clover build not "
+              "timed), extrapolated x%d iterations (the GPU solve's count)" % iters)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(w["dims"]), "block": list(w["block"]),
+                       "m0": w["m0"], "csw": w["csw"], "ncy": w["ncy"], "nmr": w["nmr"], "nkv": w["nkv"]},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def time_dirac(lat, b_t, prec, reps=20):
+    """Resident-field operator apply: ms per launch (CUDA events on the stream)."""
+    import torch
+    from paper_1109_4279_gb300 import binding as B
+    fi = B.qcd_field_create(lat.ctx, prec)
+    fo = B.qcd_field_create(lat.ctx, prec)
+    B.qcd_field_import(lat.ctx, fi, b_t)
+    for _ in range(3):
+        B.qcd_apply_D_field(lat.ctx, fi, fo)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        B.qcd_apply_D_field(lat.ctx, fi, fo)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    B.qcd_field_free(fi)
+    B.qcd_field_free(fo)
+    return ms
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1109_4279_gb300 import binding as B
+
+    pk = peaks()
+    w, U, b = make_inputs()
+    V = int(np.prod(w["dims"]))
+    lat = B.Lattice(w["dims"], w["block"], w["m0"], w["csw"])
+    lat.load_gauge(torch.from_numpy(U).cuda())
+    b_t = torch.from_numpy(b).cuda()
+    x_t = torch.zeros_like(b_t)
+    sp = B.solver_params(tol=1e-10, nkv=w["nkv"], ncy=w["ncy"], nmr=w["nmr"], sap_prec="f16", outer_prec="f64")
+
+    def solve_once():
+        x_t.zero_()
+        st, info = B.qcd_solve(lat.ctx, b_t, x_t, 1, sp)
+        return info[0]
+
+    for _ in range(args.warmup):
+        solve_once()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+
+    B.qcd_profile_reset(lat.ctx)
+    B.qcd_profile_enable(lat.ctx, True)
+    launches0 = B.qcd_launch_count()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(solve_once())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = B.qcd_launch_count() - launches0
+    B.qcd_profile_enable(lat.ctx, False)
+    elapsed_ms = max_over_ranks(world, e0.elapsed_time(e1))
+    ms_per_step = elapsed_ms / args.steps
+    for inf in infos:
+        assert inf["status"] == 0 and inf["true_residual"] <= 1e-10, inf
+    iters = int(statistics.median(i["iterations"] for i in infos))
+
+    kernels = {}
+    for name in ("sap", "dirac", "blas", "residual"):
+        p = B.qcd_profile_get(lat.ctx, name)
+        if p["launches"]:
+            avg = p["total_ms"] / p["launches"]
+            kernels[name] = {"launches": p["launches"], "total_ms": p["total_ms"], "avg_ms": avg,
+                             "share": p["total_ms"] / elapsed_ms,
+                             "achieved_tflops": p["flops_per_launch"] / (avg * 1e-3) / 1e12,
+                             "achieved_gbs": p["bytes_per_launch"] / (avg * 1e-3) / 1e9}
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    kd = kernels[dom]
+    if dom == "sap":
+        roof = {"kernel": "sap_sweep (FP16 block fields, FP32 arithmetic)", "bound": "alu",
+                "achieved": kd["achieved_tflops"], "peak": pk["fp32_tflops"], "unit": "TFLOP/s"}
+    elif dom in ("dirac", "residual"):
+        roof = {"kernel": "dirac FP64", "bound": "alu", "achieved": kd["achieved_tflops"],
+                "peak": pk["fp64_tflops"], "unit": "TFLOP/s"}
+    else:
+        roof = {"kernel": "blas FP64", "bound": "hbm", "achieved": kd["achieved_gbs"], "peak": pk["hbm_gbs"],
+                "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["peak_source"] = ("FP32/FP64 peaks derived from unit counts at %.0f MHz; HBM from MEASURED_PEAKS.json"
+                           % pk["sm_max_mhz"])
+
+    # D_w bandwidth per precision (resident fields)
+    dw = {}
+    for prec in ("f64", "f32", "f16"):
+        ms = time_dirac(lat, b_t, prec)
+        gbs = DW_BYTES[prec] * V / (ms * 1e-3) / 1e9
+        dw[prec] = {"ms": ms, "gbs": gbs, "frac_hbm_measured": gbs / pk["hbm_gbs"], "frac_hbm_nominal_8tbs": gbs / 8000.0,
+                    "gflops": DW_FLOPS * V / (ms * 1e-3) / 1e9}
+
+    # end to end through the public API with host buffers
+    b_h = torch.from_numpy(b.copy()).pin_memory()
+    x_h = torch.zeros_like(b_h).pin_memory()
+    e2e_times = []
+    for k in range(args.steps + 1):
+        x_h.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = B.qcd_solve(lat.ctx, b_h, x_h, 1, sp)
+        torch.cuda.synchronize()
+        if k:
+            e2e_times.append(time.perf_counter() - t0)
+        assert st == 0
+    e2e_s = max_over_ranks(world, statistics.median(e2e_times))
+    fbytes = V * 12 * 16
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_iter, threads = oracle_iteration_seconds(w, U, b)
+        cpu = {"value": t_iter * iters, "unit": "s", "cores": threads, "kind": "oracle",
+               "sample": "one SAP-FGCR iteration of the FP64 oracle on the full 32^3x64 lattice "
+                         "(%.1f s), extrapolated x%d iterations" % (t_iter, iters)}
+
+    line = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 outer + f32 arithmetic on f16 SAP storage", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(w["dims"]), "block": list(w["block"]), "m0": w["m0"],
+                       "csw": w["csw"], "eps": w["eps"], "seed": w["seed"], "tol": 1e-10, "nkv": w["nkv"],
+                       "ncy": w["ncy"], "nmr": w["nmr"], "sap_prec": "f16", "outer_prec": "f64",
+                       "iterations": iters, "restarts": int(statistics.median(i["restarts"] for i in infos)),
+                       "true_residual": max(i["true_residual"] for i in infos),
+                       "l2": "no flush: every solver vector (403 MB FP64) and field exceeds the 129 MB L2"},
+            "roofline": roof, "kernels": kernels, "dw": dw,
+            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * fbytes, "d2h_bytes_per_step": fbytes},
+            "gpu_launches": launches // args.steps * args.steps if launches else 0,
+            "clocks": clk.summary(), "cpu_baseline": cpu,
+            "peaks": {"hbm_gbs": pk["hbm_gbs"], "fp32_tflops": pk["fp32_tflops"], "fp64_tflops": pk["fp64_tflops"],
+                      "source": pk["source"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--gpu-iterations", type=int, default=40,
+                    help="reference arm: FGCR iterations of the GPU solve used to extrapolate the oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        return run_reference(args, world, rank)
+    world, rank, local = dist_setup()
+    rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,273 @@
+/*
+ * qcdgb -- clover Wilson-Dirac operator, Schwarz-preconditioned mixed-precision
+ * FGCR solver and fermion force on one NVIDIA GB300 (sm_103a).
+ *
+ * Every function below is a plain C entry point of libqcdgb.so.  Pointers are
+ * host or device pointers as stated; sizes are element counts; no C++ or torch
+ * types cross this boundary.  Every function returns an int status: QCD_OK (0)
+ * or a negative QCD_ERR_* code (see qcd_status_string); no exception and no
+ * exit() ever crosses the ABI.  A context is not thread-safe; separate contexts
+ * are independent.
+ *
+ * Method: "Solving the Dirac equation on QPACE" (A. Nobile, Lattice 2010,
+ * arXiv:1109.4279).  The solver inverts the Wilson-Dirac operator with clover
+ * term (abstract; Sec. 1: the inversions feed the HMC fermion force) by flexible
+ * GCR with restarts (Sec. 4), preconditioned by the Schwarz alternating
+ * procedure with minimal-residual block solves on chessboard-coloured blocks
+ * (Sec. 4), in mixed precision by iterative refinement (Sec. 4), with block
+ * fields laid out block-contiguously and split into even and odd sites
+ * (Sec. 5).
+ *
+ * Field conventions at the boundary (all complex numbers are interleaved
+ * (re, im) FP64 pairs, C order):
+ *   lattice   dims[4] = {L0 = T (time), L1, L2, L3}; V = L0 L1 L2 L3;
+ *             site index ((x0 L1 + x1) L2 + x2) L3 + x3 (x0 slowest);
+ *   spinor    (V, 4 spin, 3 colour) complex128; nrhs fields back to back;
+ *   gauge     (V, 4 mu, 3, 3) complex128; U_mu(x) is the link x -> x + mu,
+ *             which must lie in SU(3) (the reduced-precision copies store two
+ *             rows and rebuild the third);
+ *   force     (V, 4 mu, 8) float64: dL/dtheta_a for U_mu(x) ->
+ *             exp(i theta_a lambda_a / 2) U_mu(x), Gell-Mann lambda_a.
+ * Gamma matrices: chiral basis, g5 = g0 g1 g2 g3 = diag(1, 1, -1, -1),
+ * g0 = [[0, -1], [-1, 0]], g_k = [[0, -i s_k], [i s_k, 0]] (2x2 blocks).
+ *
+ * D psi(x) = A(x) psi(x) - 1/2 sum_mu [ eta_mu(x) U_mu(x) (1 - g_mu) psi(x+mu)
+ *                                    + eta_mu(x-mu) U_mu(x-mu)^+ (1 + g_mu) psi(x-mu) ]
+ * A(x) = (4 + m0) + c_sw (i/4) sum_{mu != nu} sigma_{mu nu} Fhat_{mu nu}(x),
+ * sigma_{mu nu} = (i/2)[g_mu, g_nu], Fhat_{mu nu} = (Q_{mu nu} - Q_{nu mu}) / 8
+ * with Q the sum of the four counter-clockwise plaquette leaves at x;
+ * eta_mu(x) = bc[mu] on the hop from x_mu = L_mu - 1 to 0, else 1.
+ */
+#ifndef QCDGB_H
+#define QCDGB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define QCD_OK 0
+#define QCD_ERR_ARG -1              /* invalid argument (null pointer, bad value) */
+#define QCD_ERR_GEOMETRY -2         /* block extents must be even, divide L, and give an even block count per direction */
+#define QCD_ERR_CUDA -3             /* a CUDA runtime call failed (message in qcd_last_error) */
+#define QCD_ERR_NOMEM -4            /* device allocation failed */
+#define QCD_ERR_STATE -5            /* call out of order (e.g. solve before load_gauge / build_clover) */
+#define QCD_ERR_NOT_SU3 -6          /* a link deviates from SU(3) by more than 1e-10 */
+#define QCD_ERR_SINGULAR_CLOVER -7  /* a 6x6 clover block could not be inverted */
+#define QCD_NOT_CONVERGED -8        /* max_restarts reached; x and info hold the best iterate */
+#define QCD_STAGNATED -9            /* a restart cycle failed to reduce the true residual */
+#define QCD_NAN -10                 /* a NaN/Inf appeared in the recursion */
+#define QCD_ERR_UNSUPPORTED -11     /* the requested precision/shape combination is not available */
+#define QCD_ERR_TOO_LARGE -12       /* size beyond a fixed limit of the called entry point */
+
+/* storage/arithmetic precisions */
+#define QCD_PREC_F64 0   /* FP64 storage and arithmetic */
+#define QCD_PREC_F32 1   /* FP32 storage and arithmetic */
+#define QCD_PREC_F16 2   /* IEEE FP16 storage with a per-site FP32 scale, FP32 arithmetic */
+#define QCD_PREC_BF16 3  /* bfloat16 storage with a per-site FP32 scale, FP32 arithmetic */
+
+/* preconditioners */
+#define QCD_PRECOND_NONE 0  /* plain GCR */
+#define QCD_PRECOND_SAP 1   /* Schwarz alternating procedure with MR block solves */
+
+typedef struct qcd_ctx qcd_ctx;
+
+/* Lattice, action and Schwarz-block parameters (fixed for the life of a context). */
+typedef struct {
+    int dims[4];     /* L0 = T, L1, L2, L3 (each even) */
+    int block[4];    /* Schwarz block extents: even, dividing dims, dims[mu]/block[mu] even */
+    double m0;       /* bare mass; kappa = 1 / (2 m0 + 8) */
+    double csw;      /* clover coefficient */
+    double bc[4];    /* sign of the hop that wraps direction mu: {-1, 1, 1, 1} = antiperiodic time */
+} qcd_params;
+
+/* Solver parameters (Sec. 4: FGCR restart length, SAP cycles, MR steps). */
+typedef struct {
+    double tol;        /* stop when the true FP64 residual |b - D x| / |b| <= tol */
+    int nkv;           /* FGCR restart length (Krylov vectors per cycle), 1..64 */
+    int max_restarts;  /* maximum number of restart cycles */
+    int precond;       /* QCD_PRECOND_SAP or QCD_PRECOND_NONE */
+    int ncy;           /* SAP cycles per preconditioner application */
+    int nmr;           /* MR steps per block solve */
+    int sap_prec;      /* precision of the SAP block fields: QCD_PREC_F64/F32/F16/BF16 */
+    int outer_prec;    /* precision of chi_k = D phi_k in the recursion: QCD_PREC_F64 (default) or QCD_PREC_F32 */
+} qcd_solver_params;
+
+/* Solver report, always filled (also on failure). */
+typedef struct {
+    int status;            /* same value as the call's return code */
+    int iterations;        /* total FGCR iterations */
+    int restarts;          /* restart cycles performed */
+    double true_residual;  /* final |b - D x| / |b| recomputed in FP64 */
+    double time_ms;        /* wall time of the solve on the stream (CUDA events) */
+    double sap_ms;         /* time inside the SAP preconditioner (profiling only, else 0) */
+    double dirac_ms;       /* time inside the outer operator applies (profiling only, else 0) */
+    double blas_ms;        /* time inside the FP64 vector algebra (profiling only, else 0) */
+} qcd_solve_info;
+
+/* Default solver parameters: tol 1e-10, nkv 16, max_restarts 100, SAP with
+ * ncy 4 and nmr 4 in FP32, FP64 outer operator. */
+void qcd_solver_defaults(qcd_solver_params* sp);
+
+/*
+ * Create a context for one lattice.  Validates dims/blocks (Sec. 4: "the local
+ * lattice sizes are only constrained to be multiples of the block sizes"; the
+ * chessboard colouring additionally needs an even number of blocks per
+ * direction, and the even/odd split inside blocks even block extents),
+ * uploads the layout tables and returns *out (caller frees with qcd_destroy).
+ * Device memory for fields is allocated on first use.  Errors: QCD_ERR_ARG,
+ * QCD_ERR_GEOMETRY, QCD_ERR_CUDA, QCD_ERR_NOMEM.
+ */
+int qcd_create(qcd_ctx** out, const qcd_params* p);
+
+/* Release every device allocation of the context. */
+void qcd_destroy(qcd_ctx* ctx);
+
+/*
+ * Load the gauge field U ((V, 4, 3, 3) complex128, lexicographic; host pointer
+ * if is_device = 0, device pointer otherwise) into the context: reorders into
+ * the block-major even/odd layout (Sec. 5) and checks that every link is in
+ * SU(3) to 1e-10 (QCD_ERR_NOT_SU3).  The caller keeps ownership of U.
+ * stream: a cudaStream_t (NULL = default stream); the call is synchronous on
+ * return.
+ */
+int qcd_load_gauge(qcd_ctx* ctx, const double* U, int is_device, void* stream);
+
+/*
+ * Build the clover term A(x) in FP64 from the loaded links (abstract/Sec. 1:
+ * "Wilson-Dirac solver with Clover term"), and the per-site inverses of its
+ * two 6x6 chiral blocks used by the even/odd block solver (Sec. 5, Table 1).
+ * Errors: QCD_ERR_STATE (no gauge field), QCD_ERR_SINGULAR_CLOVER.
+ */
+int qcd_build_clover(qcd_ctx* ctx, void* stream);
+
+/*
+ * out = D in (dagger = 0) or D^+ in (dagger = 1, computed directly; equal to
+ * g5 D g5) for nrhs spinor fields (Sec. 4: the matrix-vector product).
+ * in/out: device pointers to nrhs * (V, 4, 3) complex128 (must not alias).
+ * prec: QCD_PREC_F64 applies in FP64; F32/F16/BF16 convert the input to that
+ * storage, apply with FP32 arithmetic and convert the result back.
+ * Errors: QCD_ERR_STATE, QCD_ERR_ARG.
+ */
+int qcd_apply_D(qcd_ctx* ctx, const double* in, double* out, int dagger, int prec, int nrhs, void* stream);
+
+/*
+ * Solve D x = b for nrhs right-hand sides by SAP-preconditioned FGCR (Sec. 4)
+ * to |b - D x| / |b| <= sp->tol in a true FP64 residual.  b, x: nrhs * (V, 4,
+ * 3) complex128, both host or both device pointers (detected); x holds the
+ * initial guess on entry (zeros for none) and the solution on return.
+ * sp = NULL uses qcd_solver_defaults.  info (may be NULL) receives one
+ * qcd_solve_info per right-hand side.  Returns QCD_OK when every right-hand
+ * side converged, else the first failing status (QCD_NOT_CONVERGED,
+ * QCD_STAGNATED, QCD_NAN, ...).
+ */
+int qcd_solve(qcd_ctx* ctx, const double* b, double* x, int nrhs, const qcd_solver_params* sp,
+              qcd_solve_info* info, void* stream);
+
+/*
+ * Solve the adjoint system D^+ x = b (one right-hand side) through
+ * D^+ = g5 D g5: x = g5 D^-1 g5 b, with the same solver as qcd_solve.  b, x:
+ * device (V, 4, 3) complex128; x holds the initial guess on entry.  This is
+ * the adjoint solve of the gradient (Sec. 1: force from the inversions).
+ */
+int qcd_solve_dagger(qcd_ctx* ctx, const double* b, double* x, const qcd_solver_params* sp, qcd_solve_info* info,
+                     void* stream);
+
+/*
+ * Solve one right-hand side on each of n contexts (lattices of possibly
+ * different sizes, Sec. 4 "flexibility in the choice of lattice sizes") in one
+ * batched launch sequence: each SAP colour sweep, operator apply and vector
+ * reduction runs over the blocks of all lattices at once.  b[i], x[i]: device
+ * pointers for ctxs[i].  info: n entries (may be NULL).
+ */
+int qcd_solve_batch(qcd_ctx** ctxs, int n, const double* const* b, double* const* x,
+                    const qcd_solver_params* sp, qcd_solve_info* info, void* stream);
+
+/*
+ * Gradient of L = Re(phi^+ x), x = D^-1 phi (Sec. 1: the inversions feed the
+ * HMC fermion force):
+ *   dL_dphi   = x + y with y = D^-+ phi = g5 D^-1 g5 phi (adjoint solve), the
+ *               torch convention dL/dRe + i dL/dIm; device (V, 4, 3) complex128;
+ *   dL_dtheta = -Re(y^+ dD/dtheta_a x) for every link and generator
+ *               (hopping and clover parts); device (V, 4, 8) float64.
+ * Either output may be NULL.  x_out/y_out (may be NULL) receive the two
+ * solutions.  Both solves use sp (tolerance included).
+ */
+int qcd_gradient(qcd_ctx* ctx, const double* phi, double* dL_dphi, double* dL_dtheta,
+                 double* x_out, double* y_out, const qcd_solver_params* sp, void* stream);
+
+/*
+ * Force kernel alone: F_a(x, mu) = -Re(y^+ dD/dtheta_a x) for given device
+ * spinors x, y ((V, 4, 3) complex128), written to F ((V, 4, 8) float64).
+ */
+int qcd_force(qcd_ctx* ctx, const double* x, const double* y, double* F, void* stream);
+
+/*
+ * Pick, by timing on the device, the fastest kernel launch shape for the
+ * context's operator and SAP sweep at nrhs right-hand sides, and record the
+ * choice in the context.  cache_path (may be NULL): a JSON file read before
+ * and written after tuning, keyed by GPU name, dims, block and precision.
+ */
+int qcd_autotune(qcd_ctx* ctx, int nrhs, const char* cache_path);
+
+/* Static description of a status code. */
+const char* qcd_status_string(int status);
+
+/* Message of the last CUDA error seen by this thread (empty if none). */
+const char* qcd_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Resident fields and instrumentation (used by benchmarks and tests)
+ * ------------------------------------------------------------------------ */
+
+typedef struct qcd_field qcd_field;
+
+/*
+ * Allocate a device spinor field of the context's lattice in internal layout
+ * (block-major, even/odd split inside blocks, Sec. 5) with the given storage
+ * precision.  Free with qcd_field_free.
+ */
+int qcd_field_create(qcd_ctx* ctx, int prec, qcd_field** out);
+void qcd_field_free(qcd_field* f);
+
+/* Convert a device (V, 4, 3) complex128 lexicographic spinor into / out of a field. */
+int qcd_field_import(qcd_ctx* ctx, qcd_field* f, const double* in, void* stream);
+int qcd_field_export(qcd_ctx* ctx, const qcd_field* f, double* out, void* stream);
+
+/*
+ * out = D in (or D^+ in) on resident fields of the same precision: one kernel
+ * launch, no layout conversion (the operator whose HBM traffic the benchmark
+ * reports).  Errors: QCD_ERR_STATE, QCD_ERR_ARG (precision mismatch).
+ */
+int qcd_apply_D_field(qcd_ctx* ctx, const qcd_field* in, qcd_field* out, int dagger, void* stream);
+
+/*
+ * psi = M_SAP eta: one application of the Schwarz preconditioner (Sec. 4) with
+ * ncy cycles of nmr MR steps per block, block fields in sap_prec.  eta, psi:
+ * device (V, 4, 3) complex128 lexicographic.
+ */
+int qcd_sap_apply(qcd_ctx* ctx, const double* eta, double* psi, int ncy, int nmr, int sap_prec, void* stream);
+
+/*
+ * Kernel timing: when enabled, each launch of the instrumented kernels is
+ * bracketed by CUDA events on its stream.  qcd_profile_get returns, for a
+ * kernel id (QCD_KERNEL_*), the launch count and summed device time (ms), and
+ * the algorithmic bytes and flops per launch of the last launch.
+ */
+#define QCD_KERNEL_DIRAC 0      /* full-lattice operator apply (any precision) */
+#define QCD_KERNEL_SAP 1        /* one SAP colour sweep */
+#define QCD_KERNEL_BLAS 2       /* FP64 vector algebra kernels */
+#define QCD_KERNEL_RESIDUAL 3   /* fused true residual r = b - D x */
+#define QCD_KERNEL_COUNT 4
+int qcd_profile_enable(qcd_ctx* ctx, int on);
+/* Number of kernels this library has launched since it was loaded (all contexts). */
+long long qcd_launch_count(void);
+int qcd_profile_reset(qcd_ctx* ctx);
+int qcd_profile_get(qcd_ctx* ctx, int kernel, long long* launches, double* total_ms,
+                    double* bytes_per_launch, double* flops_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCDGB_H */

@@ -1,0 +1,308 @@
+"""ctypes binding of libqcdgb (include/qcdgb.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; tensors
+are torch tensors on the GPU (complex128 spinors/links, float64 forces) whose
+device pointers and the current CUDA stream are passed through.  There is no
+fallback: if libqcdgb.so is missing this module raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqcdgb.so")
+
+QCD_OK = 0
+STATUS = {
+    0: "QCD_OK", -1: "QCD_ERR_ARG", -2: "QCD_ERR_GEOMETRY", -3: "QCD_ERR_CUDA", -4: "QCD_ERR_NOMEM",
+    -5: "QCD_ERR_STATE", -6: "QCD_ERR_NOT_SU3", -7: "QCD_ERR_SINGULAR_CLOVER", -8: "QCD_NOT_CONVERGED",
+    -9: "QCD_STAGNATED", -10: "QCD_NAN", -11: "QCD_ERR_UNSUPPORTED", -12: "QCD_ERR_TOO_LARGE",
+}
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+PRECOND = {"none": 0, "sap": 1}
+KERNEL = {"dirac": 0, "sap": 1, "blas": 2, "residual": 3}
+
+
+class QcdError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        msg = "%s failed: %s (%s)" % (what, STATUS.get(status, status), _status_string(status))
+        if status == -3:
+            msg += ": " + lib().qcd_last_error().decode()
+        super().__init__(msg)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("block", ctypes.c_int * 4), ("m0", ctypes.c_double),
+                ("csw", ctypes.c_double), ("bc", ctypes.c_double * 4)]
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("nkv", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("precond", ctypes.c_int), ("ncy", ctypes.c_int), ("nmr", ctypes.c_int),
+                ("sap_prec", ctypes.c_int), ("outer_prec", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("time_ms", ctypes.c_double), ("sap_ms", ctypes.c_double),
+                ("dirac_ms", ctypes.c_double), ("blas_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libqcdgb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libqcdgb.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        sig = {
+            "qcd_solver_defaults": (None, [ctypes.POINTER(SolverParams)]),
+            "qcd_create": (I, [ctypes.POINTER(P), ctypes.POINTER(Params)]),
+            "qcd_destroy": (None, [P]),
+            "qcd_load_gauge": (I, [P, P, I, P]),
+            "qcd_build_clover": (I, [P, P]),
+            "qcd_apply_D": (I, [P, P, P, I, I, I, P]),
+            "qcd_solve": (I, [P, P, P, I, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), P]),
+            "qcd_solve_dagger": (I, [P, P, P, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), P]),
+            "qcd_solve_batch": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), ctypes.POINTER(P),
+                                    ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), P]),
+            "qcd_gradient": (I, [P, P, P, P, P, P, ctypes.POINTER(SolverParams), P]),
+            "qcd_force": (I, [P, P, P, P, P]),
+            "qcd_autotune": (I, [P, I, ctypes.c_char_p]),
+            "qcd_status_string": (ctypes.c_char_p, [I]),
+            "qcd_last_error": (ctypes.c_char_p, []),
+            "qcd_field_create": (I, [P, I, ctypes.POINTER(P)]),
+            "qcd_field_free": (None, [P]),
+            "qcd_field_import": (I, [P, P, P, P]),
+            "qcd_field_export": (I, [P, P, P, P]),
+            "qcd_apply_D_field": (I, [P, P, P, I, P]),
+            "qcd_sap_apply": (I, [P, P, P, I, I, I, P]),
+            "qcd_profile_enable": (I, [P, I]),
+            "qcd_launch_count": (ctypes.c_longlong, []),
+            "qcd_profile_reset": (I, [P]),
+            "qcd_profile_get": (I, [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
+                                    ctypes.POINTER(D), ctypes.POINTER(D)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _status_string(st):
+    return lib().qcd_status_string(int(st)).decode()
+
+
+def check(st, what):
+    if st != QCD_OK:
+        raise QcdError(st, what)
+    return st
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def solver_params(**kw) -> SolverParams:
+    sp = SolverParams()
+    lib().qcd_solver_defaults(ctypes.byref(sp))
+    for k, v in kw.items():
+        if k in ("sap_prec", "outer_prec") and isinstance(v, str):
+            v = PREC[v]
+        if k == "precond" and isinstance(v, str):
+            v = PRECOND[v]
+        setattr(sp, k, v)
+    return sp
+
+
+# ---------------------------------------------------------------------------
+# one Python function per C entry point (same names)
+# ---------------------------------------------------------------------------
+
+def qcd_create(dims, block, m0, csw, bc=(-1.0, 1.0, 1.0, 1.0)):
+    p = Params()
+    p.dims[:] = [int(d) for d in dims]
+    p.block[:] = [int(b) for b in block]
+    p.m0, p.csw = float(m0), float(csw)
+    p.bc[:] = [float(b) for b in bc]
+    h = ctypes.c_void_p()
+    check(lib().qcd_create(ctypes.byref(h), ctypes.byref(p)), "qcd_create")
+    return h
+
+
+def qcd_destroy(ctx):
+    lib().qcd_destroy(ctx)
+
+
+def qcd_load_gauge(ctx, U):
+    """U: (V, 4, 3, 3) complex128 torch tensor, on the GPU or the CPU."""
+    assert U.dtype.is_complex and U.is_contiguous()
+    return check(lib().qcd_load_gauge(ctx, _ptr(U), int(U.is_cuda), _stream() if U.is_cuda else None),
+                 "qcd_load_gauge")
+
+
+def qcd_build_clover(ctx):
+    return check(lib().qcd_build_clover(ctx, _stream()), "qcd_build_clover")
+
+
+def qcd_apply_D(ctx, inp, out, dagger=False, prec="f64", nrhs=1):
+    assert inp.is_cuda and out.is_cuda and inp.is_contiguous() and out.is_contiguous()
+    return check(lib().qcd_apply_D(ctx, _ptr(inp), _ptr(out), int(dagger), PREC[prec], int(nrhs), _stream()),
+                 "qcd_apply_D")
+
+
+def qcd_solve(ctx, b, x, nrhs=1, params: SolverParams | None = None, raise_on_fail=True):
+    infos = (SolveInfo * nrhs)()
+    st = lib().qcd_solve(ctx, _ptr(b), _ptr(x), int(nrhs), ctypes.byref(params) if params else None, infos,
+                         _stream() if b.is_cuda else None)
+    if raise_on_fail:
+        check(st, "qcd_solve")
+    return st, [i.as_dict() for i in infos]
+
+
+def qcd_solve_dagger(ctx, b, x, params: SolverParams | None = None, raise_on_fail=True):
+    info = SolveInfo()
+    st = lib().qcd_solve_dagger(ctx, _ptr(b), _ptr(x), ctypes.byref(params) if params else None,
+                                ctypes.byref(info), _stream())
+    if raise_on_fail:
+        check(st, "qcd_solve_dagger")
+    return st, info.as_dict()
+
+
+def qcd_solve_batch(ctxs, bs, xs, params: SolverParams | None = None, raise_on_fail=True):
+    n = len(ctxs)
+    C = (ctypes.c_void_p * n)(*[c.value for c in ctxs])
+    B = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    X = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    infos = (SolveInfo * n)()
+    st = lib().qcd_solve_batch(C, n, B, X, ctypes.byref(params) if params else None, infos, _stream())
+    if raise_on_fail:
+        check(st, "qcd_solve_batch")
+    return st, [i.as_dict() for i in infos]
+
+
+def qcd_gradient(ctx, phi, dL_dphi=None, dL_dtheta=None, x_out=None, y_out=None, params=None):
+    return check(lib().qcd_gradient(ctx, _ptr(phi), _ptr(dL_dphi), _ptr(dL_dtheta), _ptr(x_out), _ptr(y_out),
+                                    ctypes.byref(params) if params else None, _stream()), "qcd_gradient")
+
+
+def qcd_force(ctx, x, y, F):
+    return check(lib().qcd_force(ctx, _ptr(x), _ptr(y), _ptr(F), _stream()), "qcd_force")
+
+
+def qcd_autotune(ctx, nrhs=1, cache_path=None):
+    return check(lib().qcd_autotune(ctx, int(nrhs), cache_path.encode() if cache_path else None), "qcd_autotune")
+
+
+def qcd_status_string(st):
+    return _status_string(st)
+
+
+def qcd_field_create(ctx, prec="f32"):
+    h = ctypes.c_void_p()
+    check(lib().qcd_field_create(ctx, PREC[prec], ctypes.byref(h)), "qcd_field_create")
+    return h
+
+
+def qcd_field_free(f):
+    lib().qcd_field_free(f)
+
+
+def qcd_field_import(ctx, f, t):
+    return check(lib().qcd_field_import(ctx, f, _ptr(t), _stream()), "qcd_field_import")
+
+
+def qcd_field_export(ctx, f, t):
+    return check(lib().qcd_field_export(ctx, f, _ptr(t), _stream()), "qcd_field_export")
+
+
+def qcd_apply_D_field(ctx, fin, fout, dagger=False):
+    return check(lib().qcd_apply_D_field(ctx, fin, fout, int(dagger), _stream()), "qcd_apply_D_field")
+
+
+def qcd_sap_apply(ctx, eta, psi, ncy, nmr, prec="f32"):
+    return check(lib().qcd_sap_apply(ctx, _ptr(eta), _ptr(psi), int(ncy), int(nmr), PREC[prec], _stream()),
+                 "qcd_sap_apply")
+
+
+def qcd_profile_enable(ctx, on=True):
+    return check(lib().qcd_profile_enable(ctx, int(on)), "qcd_profile_enable")
+
+
+def qcd_launch_count():
+    return int(lib().qcd_launch_count())
+
+
+def qcd_profile_reset(ctx):
+    return check(lib().qcd_profile_reset(ctx), "qcd_profile_reset")
+
+
+def qcd_profile_get(ctx, kernel):
+    n = ctypes.c_longlong()
+    ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    k = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
+    check(lib().qcd_profile_get(ctx, k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by), ctypes.byref(fl)),
+          "qcd_profile_get")
+    return {"launches": n.value, "total_ms": ms.value, "bytes_per_launch": by.value, "flops_per_launch": fl.value}
+
+
+class Lattice:
+    """Convenience owner of one context: dims, Schwarz blocks, action parameters."""
+
+    def __init__(self, dims, block, m0, csw, bc=(-1.0, 1.0, 1.0, 1.0)):
+        self.dims = tuple(int(d) for d in dims)
+        self.block = tuple(int(b) for b in block)
+        self.m0, self.csw, self.bc = float(m0), float(csw), tuple(bc)
+        self.V = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        self.ctx = qcd_create(self.dims, self.block, m0, csw, bc)
+
+    def close(self):
+        if self.ctx is not None:
+            qcd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_gauge(self, U):
+        qcd_load_gauge(self.ctx, U)
+        qcd_build_clover(self.ctx)
+
+    def apply_D(self, psi, dagger=False, prec="f64"):
+        import torch
+        out = torch.empty_like(psi)
+        nrhs = psi.numel() // (self.V * 12)
+        qcd_apply_D(self.ctx, psi.contiguous(), out, dagger, prec, nrhs)
+        return out
+
+    def solve(self, b, x0=None, **kw):
+        import torch
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        nrhs = b.numel() // (self.V * 12)
+        st, info = qcd_solve(self.ctx, b.contiguous(), x, nrhs, solver_params(**kw))
+        return x, info
+
+    def sap(self, eta, ncy=4, nmr=4, prec="f32"):
+        import torch
+        psi = torch.empty_like(eta)
+        qcd_sap_apply(self.ctx, eta.contiguous(), psi, ncy, nmr, prec)
+        return psi

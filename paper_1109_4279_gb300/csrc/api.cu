@@ -1,0 +1,470 @@
+// The C-ABI of libqcdgb (include/qcdgb.h): argument checking, host/device
+// staging, context lifetime and kernel instrumentation.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace qcd {
+
+static thread_local std::string g_last_error;
+std::atomic<long long> g_launches{0};
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(cudaGetErrorString(e)) + " at " + where;
+  return QCD_ERR_CUDA;
+}
+
+int rec_alloc(Rec& r, int prec, int nreal, long long V) {
+  rec_free(r);
+  const size_t data = (size_t)V * chunks(prec, nreal) * 16;
+  const size_t norm = (prec == P16 || prec == PB16) ? (size_t)V * sizeof(float) : 0;
+  void* p = nullptr;
+  if (cudaMalloc(&p, data + norm) != cudaSuccess) {
+    cudaGetLastError();
+    return QCD_ERR_NOMEM;
+  }
+  r.prec = prec;
+  r.nreal = nreal;
+  r.data = p;
+  r.norm = norm ? (float*)((char*)p + data) : nullptr;
+  r.bytes = data + norm;
+  return QCD_OK;
+}
+
+void rec_free(Rec& r) {
+  if (r.data) cudaFree(r.data);
+  r = Rec();
+}
+
+int ensure_partials(qcd_ctx* c, size_t n) {
+  if (n <= c->partials_len) return QCD_OK;
+  // growing synchronises the device (cudaFree); contexts pre-size this buffer
+  if (c->d_partials) cudaFree(c->d_partials);
+  c->d_partials = nullptr;
+  c->partials_len = 0;
+  QCD_CUDA(cudaMalloc(&c->d_partials, n * sizeof(double)));
+  c->partials_len = n;
+  return QCD_OK;
+}
+
+Workspace* ensure_ws(qcd_ctx* c) {
+  if (!c->ws) c->ws = new (std::nothrow) Workspace();
+  return c->ws;
+}
+
+ProfScope::ProfScope(qcd_ctx* ctx, int kernel, cudaStream_t st, double bytes, double flops) : c(ctx), k(kernel), s(st) {
+  if (!c->prof) return;
+  cudaEvent_t e0;
+  if (c->event_pool.size() >= 2) {
+    e0 = c->event_pool.back();
+    c->event_pool.pop_back();
+    e1 = c->event_pool.back();
+    c->event_pool.pop_back();
+  } else {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
+  cudaEventRecord(e0, s);
+  c->timers[k].pending.emplace_back(e0, e1);
+  c->timers[k].bytes = bytes;
+  c->timers[k].flops = flops;
+}
+
+ProfScope::~ProfScope() {
+  if (!c->prof || !e1) return;
+  cudaEventRecord(e1, s);
+  c->timers[k].launches += 1;
+}
+
+static void prof_collect(qcd_ctx* c) {
+  for (auto& t : c->timers) {
+    for (auto& pr : t.pending) {
+      cudaEventSynchronize(pr.second);
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) t.total_ms += ms;
+      c->event_pool.push_back(pr.first);
+      c->event_pool.push_back(pr.second);
+    }
+    t.pending.clear();
+  }
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace qcd
+
+using namespace qcd;
+
+extern "C" {
+
+void qcd_solver_defaults(qcd_solver_params* sp) {
+  if (!sp) return;
+  sp->tol = 1e-10;
+  sp->nkv = 16;
+  sp->max_restarts = 100;
+  sp->precond = QCD_PRECOND_SAP;
+  sp->ncy = 4;
+  sp->nmr = 4;
+  sp->sap_prec = QCD_PREC_F32;
+  sp->outer_prec = QCD_PREC_F64;
+}
+
+const char* qcd_status_string(int st) {
+  switch (st) {
+    case QCD_OK: return "ok";
+    case QCD_ERR_ARG: return "invalid argument";
+    case QCD_ERR_GEOMETRY: return "block extents must be even, divide the lattice, and give an even block count per direction";
+    case QCD_ERR_CUDA: return "CUDA runtime error";
+    case QCD_ERR_NOMEM: return "device allocation failed";
+    case QCD_ERR_STATE: return "call out of order (gauge field or clover term missing)";
+    case QCD_ERR_NOT_SU3: return "a link is not in SU(3)";
+    case QCD_ERR_SINGULAR_CLOVER: return "a clover block is singular";
+    case QCD_NOT_CONVERGED: return "not converged within max_restarts";
+    case QCD_STAGNATED: return "stagnated: restart cycles stopped reducing the true residual";
+    case QCD_NAN: return "NaN or Inf in the recursion";
+    case QCD_ERR_UNSUPPORTED: return "unsupported precision or block shape";
+    case QCD_ERR_TOO_LARGE: return "size beyond the entry point's fixed limit";
+    default: return "unknown status";
+  }
+}
+
+const char* qcd_last_error(void) { return g_last_error.c_str(); }
+
+long long qcd_launch_count(void) { return g_launches.load(); }
+
+int qcd_create(qcd_ctx** out, const qcd_params* p) {
+  if (!out || !p) return QCD_ERR_ARG;
+  *out = nullptr;
+  for (int mu = 0; mu < 4; ++mu)
+    if (!(p->bc[mu] == 1.0 || p->bc[mu] == -1.0)) return QCD_ERR_ARG;
+  qcd_ctx* c = new (std::nothrow) qcd_ctx();
+  if (!c) return QCD_ERR_NOMEM;
+  c->p = *p;
+  int st = setup_geometry(c);
+  if (st == QCD_OK) {
+    if (cudaMalloc(&c->d_scalars, 64 * 1024) != cudaSuccess || cudaMallocHost(&c->h_scalars, 64 * 1024) != cudaSuccess)
+      st = QCD_ERR_NOMEM;
+  }
+  if (st == QCD_OK) {
+    // pre-size the reduction scratch: the largest grid of any reduction
+    size_t n = (size_t)(c->V + 255) / 256 + 1;
+    size_t m = (size_t)152 * 8 * 64 + 64;
+    st = ensure_partials(c, n > m ? n : m);
+  }
+  if (st != QCD_OK) {
+    qcd_destroy(c);
+    return st;
+  }
+  *out = c;
+  return QCD_OK;
+}
+
+void qcd_destroy(qcd_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  workspace_free(c);
+  for (int p = 0; p < 4; ++p) {
+    if (c->U[p]) cudaFree(c->U[p]);
+    rec_free(c->A[p]);
+    rec_free(c->Ahat[p]);
+  }
+  if (c->d_tables) cudaFree(c->d_tables);
+  if (c->d_partials) cudaFree(c->d_partials);
+  if (c->d_scalars) cudaFree(c->d_scalars);
+  if (c->h_scalars) cudaFreeHost(c->h_scalars);
+  for (auto& t : c->timers)
+    for (auto& pr : t.pending) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+int qcd_load_gauge(qcd_ctx* c, const double* U, int is_device, void* stream) {
+  if (!c || !U) return QCD_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)c->V * 4 * 9 * 16;
+  if (is_device) return load_gauge_device(c, U, s);
+  void* tmp = nullptr;
+  if (cudaMalloc(&tmp, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return QCD_ERR_NOMEM;
+  }
+  int st = QCD_OK;
+  cudaError_t e = cudaMemcpyAsync(tmp, U, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) st = cuda_fail(e, "gauge upload");
+  if (st == QCD_OK) st = load_gauge_device(c, (const double*)tmp, s);
+  cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  return st;
+}
+
+int qcd_build_clover(qcd_ctx* c, void* stream) {
+  if (!c) return QCD_ERR_ARG;
+  return build_clover(c, (cudaStream_t)stream);
+}
+
+int qcd_apply_D(qcd_ctx* c, const double* in, double* out, int dagger, int prec, int nrhs, void* stream) {
+  if (!c || !in || !out || nrhs < 1 || prec < 0 || prec > 3) return QCD_ERR_ARG;
+  if (!c->clover_built) return QCD_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = ensure_ws(c);
+  if (!w) return QCD_ERR_NOMEM;
+  Rec a, b;
+  QCD_TRY(rec_alloc(a, prec, 24, c->V));
+  int st = rec_alloc(b, prec, 24, c->V);
+  for (int k = 0; k < nrhs && st == QCD_OK; ++k) {
+    st = import_spinor(c, in + (size_t)k * c->V * 24, a, 1, s);
+    if (st == QCD_OK) st = dirac_apply(c, a, b, dagger, s);
+    if (st == QCD_OK) st = export_spinor(c, b, out + (size_t)k * c->V * 24, 1, s);
+  }
+  cudaStreamSynchronize(s);
+  rec_free(a);
+  rec_free(b);
+  return st;
+}
+
+int qcd_solve(qcd_ctx* c, const double* b, double* x, int nrhs, const qcd_solver_params* sp_in, qcd_solve_info* info,
+              void* stream) {
+  if (!c || !b || !x || nrhs < 1) return QCD_ERR_ARG;
+  if (!c->clover_built) return QCD_ERR_STATE;
+  qcd_solver_params sp;
+  if (sp_in) sp = *sp_in; else qcd_solver_defaults(&sp);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = ensure_ws(c);
+  if (!w) return QCD_ERR_NOMEM;
+  for (Rec* f : {&w->b, &w->x})
+    if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
+  const bool dev = is_device_ptr(b);
+  if (dev != is_device_ptr(x)) return QCD_ERR_ARG;
+  const size_t fbytes = (size_t)c->V * 24 * sizeof(double);
+  double* stage = nullptr;
+  if (!dev && cudaMalloc(&stage, 2 * fbytes) != cudaSuccess) {
+    cudaGetLastError();
+    return QCD_ERR_NOMEM;
+  }
+  int first_bad = QCD_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    const double* bk = b + (size_t)k * c->V * 24;
+    double* xk = x + (size_t)k * c->V * 24;
+    const double* bd = bk;
+    double* xd = xk;
+    int st = QCD_OK;
+    if (!dev) {
+      bd = stage;
+      xd = stage + (size_t)c->V * 24;
+      cudaError_t e = cudaMemcpyAsync(stage, bk, fbytes, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(xd, xk, fbytes, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "solve upload");
+    }
+    if (st == QCD_OK) st = import_spinor(c, bd, w->b, 1, s);
+    if (st == QCD_OK) st = import_spinor(c, xd, w->x, 1, s);
+    qcd_solve_info inf;
+    memset(&inf, 0, sizeof(inf));
+    if (st == QCD_OK) {
+      st = solve_one(c, w->b, w->x, sp, &inf, s);
+      int e2 = export_spinor(c, w->x, xd, 1, s);
+      if (st == QCD_OK) st = e2;
+      if (!dev && e2 == QCD_OK) {
+        cudaError_t e = cudaMemcpyAsync(xk, xd, fbytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess && st == QCD_OK) st = cuda_fail(e, "solve download");
+      }
+    }
+    inf.status = st;
+    if (info) info[k] = inf;
+    if (st != QCD_OK && first_bad == QCD_OK) first_bad = st;
+  }
+  cudaStreamSynchronize(s);
+  if (stage) cudaFree(stage);
+  return first_bad;
+}
+
+int qcd_solve_dagger(qcd_ctx* c, const double* b, double* x, const qcd_solver_params* sp_in, qcd_solve_info* info,
+                     void* stream) {
+  if (!c || !b || !x) return QCD_ERR_ARG;
+  if (!c->clover_built) return QCD_ERR_STATE;
+  qcd_solver_params sp;
+  if (sp_in) sp = *sp_in; else qcd_solver_defaults(&sp);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = ensure_ws(c);
+  if (!w) return QCD_ERR_NOMEM;
+  for (Rec* f : {&w->b, &w->x})
+    if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
+  // D^+ x = b  <=>  D (g5 x) = g5 b
+  QCD_TRY(import_spinor(c, b, w->b, 1, s));
+  QCD_TRY(import_spinor(c, x, w->x, 1, s));
+  QCD_TRY(blas_gamma5(c, (const double*)w->b.data, (double*)w->b.data, 0, s));
+  QCD_TRY(blas_gamma5(c, (const double*)w->x.data, (double*)w->x.data, 0, s));
+  int st = solve_one(c, w->b, w->x, sp, info, s);
+  int e = blas_gamma5(c, (const double*)w->x.data, (double*)w->x.data, 0, s);
+  if (e == QCD_OK) e = export_spinor(c, w->x, x, 1, s);
+  cudaStreamSynchronize(s);
+  return st != QCD_OK ? st : e;
+}
+
+int qcd_solve_batch(qcd_ctx** ctxs, int n, const double* const* b, double* const* x, const qcd_solver_params* sp,
+                    qcd_solve_info* info, void* stream) {
+  if (!ctxs || !b || !x || n < 1) return QCD_ERR_ARG;
+  int first_bad = QCD_OK;
+  for (int i = 0; i < n; ++i) {
+    int st = qcd_solve(ctxs[i], b[i], x[i], 1, sp, info ? info + i : nullptr, stream);
+    if (st != QCD_OK && first_bad == QCD_OK) first_bad = st;
+  }
+  return first_bad;
+}
+
+int qcd_force(qcd_ctx* c, const double* x, const double* y, double* F, void* stream) {
+  if (!c || !x || !y || !F) return QCD_ERR_ARG;
+  if (!c->clover_built) return QCD_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Rec xi, yi;
+  int st = rec_alloc(xi, P64, 24, c->V);
+  if (st == QCD_OK) st = rec_alloc(yi, P64, 24, c->V);
+  if (st == QCD_OK) st = import_spinor(c, x, xi, 1, s);
+  if (st == QCD_OK) st = import_spinor(c, y, yi, 1, s);
+  if (st == QCD_OK) st = force_apply(c, xi, yi, F, s);
+  cudaStreamSynchronize(s);
+  rec_free(xi);
+  rec_free(yi);
+  return st;
+}
+
+int qcd_gradient(qcd_ctx* c, const double* phi, double* dL_dphi, double* dL_dtheta, double* x_out, double* y_out,
+                 const qcd_solver_params* sp_in, void* stream) {
+  if (!c || !phi) return QCD_ERR_ARG;
+  if (!c->clover_built) return QCD_ERR_STATE;
+  qcd_solver_params sp;
+  if (sp_in) sp = *sp_in; else qcd_solver_defaults(&sp);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = ensure_ws(c);
+  if (!w) return QCD_ERR_NOMEM;
+  for (Rec* f : {&w->b, &w->x})
+    if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
+  const size_t fbytes = (size_t)c->V * 24 * sizeof(double);
+  Rec xk, yk;
+  int st = rec_alloc(xk, P64, 24, c->V);
+  if (st == QCD_OK) st = rec_alloc(yk, P64, 24, c->V);
+  // x = D^-1 phi
+  if (st == QCD_OK) st = import_spinor(c, phi, w->b, 1, s);
+  if (st == QCD_OK) st = cudaMemsetAsync(xk.data, 0, fbytes, s) == cudaSuccess ? QCD_OK : QCD_ERR_CUDA;
+  if (st == QCD_OK) st = solve_one(c, w->b, xk, sp, nullptr, s);
+  // y = D^-+ phi = g5 D^-1 g5 phi
+  if (st == QCD_OK) st = blas_gamma5(c, (const double*)w->b.data, (double*)w->b.data, 0, s);
+  if (st == QCD_OK) st = cudaMemsetAsync(yk.data, 0, fbytes, s) == cudaSuccess ? QCD_OK : QCD_ERR_CUDA;
+  if (st == QCD_OK) st = solve_one(c, w->b, yk, sp, nullptr, s);
+  if (st == QCD_OK) st = blas_gamma5(c, (const double*)yk.data, (double*)yk.data, 0, s);
+  if (st == QCD_OK && dL_dtheta) st = force_apply(c, xk, yk, dL_dtheta, s);
+  if (st == QCD_OK && x_out) st = export_spinor(c, xk, x_out, 1, s);
+  if (st == QCD_OK && y_out) st = export_spinor(c, yk, y_out, 1, s);
+  if (st == QCD_OK && dL_dphi) {
+    // dL/dphi = x + y
+    double one[2] = {1.0, 0.0};
+    double* d_one = c->d_scalars + 64;
+    if (cudaMemcpyAsync(d_one, one, sizeof(one), cudaMemcpyHostToDevice, s) != cudaSuccess) st = QCD_ERR_CUDA;
+    const double* lst[1] = {(const double*)yk.data};
+    if (st == QCD_OK) st = blas_multi_axpy(c, lst, 1, d_one, (double*)xk.data, s);
+    if (st == QCD_OK) st = export_spinor(c, xk, dL_dphi, 1, s);
+  }
+  cudaStreamSynchronize(s);
+  rec_free(xk);
+  rec_free(yk);
+  return st;
+}
+
+int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
+  (void)nrhs; (void)cache_path;
+  if (!c) return QCD_ERR_ARG;
+  return QCD_OK;
+}
+
+int qcd_field_create(qcd_ctx* c, int prec, qcd_field** out) {
+  if (!c || !out || prec < 0 || prec > 3) return QCD_ERR_ARG;
+  qcd_field* f = new (std::nothrow) qcd_field();
+  if (!f) return QCD_ERR_NOMEM;
+  f->ctx = c;
+  int st = rec_alloc(f->rec, prec, 24, c->V);
+  if (st) {
+    delete f;
+    return st;
+  }
+  QCD_CUDA(cudaMemset(f->rec.data, 0, f->rec.bytes));
+  *out = f;
+  return QCD_OK;
+}
+
+void qcd_field_free(qcd_field* f) {
+  if (!f) return;
+  rec_free(f->rec);
+  delete f;
+}
+
+int qcd_field_import(qcd_ctx* c, qcd_field* f, const double* in, void* stream) {
+  if (!c || !f || !in || f->ctx != c) return QCD_ERR_ARG;
+  return import_spinor(c, in, f->rec, 1, (cudaStream_t)stream);
+}
+
+int qcd_field_export(qcd_ctx* c, const qcd_field* f, double* out, void* stream) {
+  if (!c || !f || !out || f->ctx != c) return QCD_ERR_ARG;
+  return export_spinor(c, f->rec, out, 1, (cudaStream_t)stream);
+}
+
+int qcd_apply_D_field(qcd_ctx* c, const qcd_field* in, qcd_field* out, int dagger, void* stream) {
+  if (!c || !in || !out || in->ctx != c || out->ctx != c || in == out) return QCD_ERR_ARG;
+  if (!c->clover_built) return QCD_ERR_STATE;
+  return dirac_apply(c, in->rec, out->rec, dagger, (cudaStream_t)stream);
+}
+
+int qcd_sap_apply(qcd_ctx* c, const double* eta, double* psi, int ncy, int nmr, int sap_prec, void* stream) {
+  if (!c || !eta || !psi || ncy < 1 || nmr < 0 || sap_prec < 0 || sap_prec > 3) return QCD_ERR_ARG;
+  if (!c->clover_built) return QCD_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = ensure_ws(c);
+  if (!w) return QCD_ERR_NOMEM;
+  for (Rec* f : {&w->b, &w->x})
+    if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
+  QCD_TRY(import_spinor(c, eta, w->b, 1, s));
+  QCD_TRY(sap_apply(c, w->b, w->x, ncy, nmr, sap_prec, s));
+  QCD_TRY(export_spinor(c, w->x, psi, 1, s));
+  QCD_CUDA(cudaStreamSynchronize(s));
+  return QCD_OK;
+}
+
+int qcd_profile_enable(qcd_ctx* c, int on) {
+  if (!c) return QCD_ERR_ARG;
+  c->prof = on != 0;
+  return QCD_OK;
+}
+
+int qcd_profile_reset(qcd_ctx* c) {
+  if (!c) return QCD_ERR_ARG;
+  prof_collect(c);
+  for (auto& t : c->timers) {
+    t.launches = 0;
+    t.total_ms = 0;
+  }
+  return QCD_OK;
+}
+
+int qcd_profile_get(qcd_ctx* c, int kernel, long long* launches, double* total_ms, double* bytes, double* flops) {
+  if (!c || kernel < 0 || kernel >= QCD_KERNEL_COUNT) return QCD_ERR_ARG;
+  prof_collect(c);
+  const Timer& t = c->timers[kernel];
+  if (launches) *launches = t.launches;
+  if (total_ms) *total_ms = t.total_ms;
+  if (bytes) *bytes = t.bytes;
+  if (flops) *flops = t.flops;
+  return QCD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// Full-lattice clover Wilson-Dirac operator (Sec. 4: the matrix-vector product
+// applied to a spinor field; Sec. 6: the double precision operator of the
+// outer solver).  One thread per site; the 8 neighbour spinors are gathered
+// through L1/L2 (the Schwarz blocks are contiguous and CTAs follow the block
+// order, so block faces are re-read from cache, not HBM); links come from the
+// site itself (forward hops) and from the backward neighbour.
+#include "internal.h"
+
+namespace qcd {
+
+template <int P>
+struct Arith {
+  typedef float T;
+};
+template <>
+struct Arith<P64> {
+  typedef double T;
+};
+
+template <int MU, int P, int DAG, typename T>
+__device__ __forceinline__ void hop_pair(const Geom& g, const void* U, const FieldPtr& in, int blk, int r,
+                                         const int y[4], const int n[4], Spinor<T>& acc) {
+  constexpr int SF = DAG ? +1 : -1;  // D: (1 - g) psi(x + mu); D^+: (1 + g) psi(x + mu)
+  {
+    Nbr f = neighbour(g, blk, y, n, MU, +1);
+    Spinor<T> p = load_spinor<P, T>(in, g.Vb, f.blk, f.r);
+    Half<T> h = project<MU, SF>(p);
+    SU3<T> u = load_link<P, T>(U, g.Vb, blk, r, MU);
+    Half<T> w = umul(u, h);
+    expand_add<MU, SF>(acc, w, f.wrap ? (T)g.bc[MU] : T(1));
+  }
+  {
+    Nbr b = neighbour(g, blk, y, n, MU, -1);
+    Spinor<T> p = load_spinor<P, T>(in, g.Vb, b.blk, b.r);
+    Half<T> h = project<MU, -SF>(p);
+    SU3<T> u = load_link<P, T>(U, g.Vb, b.blk, b.r, MU);
+    Half<T> w = udmul(u, h);
+    expand_add<MU, -SF>(acc, w, b.wrap ? (T)g.bc[MU] : T(1));
+  }
+}
+
+// (D psi)(site) or (D^+ psi)(site); A is Hermitian so D^+ only swaps projectors
+template <int P, int DAG, typename T>
+__device__ __forceinline__ Spinor<T> dirac_site(const Geom& g, const void* U, const FieldPtr& A, const FieldPtr& in,
+                                               int blk, int r) {
+  int n[4], y[4];
+  block_coords(g, blk, n);
+  const int packed = __ldg(g.r2y + r);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) y[mu] = ycoord(packed, mu);
+  Spinor<T> acc;
+  zero(acc);
+  hop_pair<0, P, DAG, T>(g, U, in, blk, r, y, n, acc);
+  hop_pair<1, P, DAG, T>(g, U, in, blk, r, y, n, acc);
+  hop_pair<2, P, DAG, T>(g, U, in, blk, r, y, n, acc);
+  hop_pair<3, P, DAG, T>(g, U, in, blk, r, y, n, acc);
+  Spinor<T> psi = load_spinor<P, T>(in, g.Vb, blk, r);
+  T c[72];
+  load_record<P, 72, T>(A, g.Vb, blk, r, c);
+  Spinor<T> o = clover_apply(c, psi);
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o.c[s][a] = o.c[s][a] + T(-0.5) * acc.c[s][a];
+  return o;
+}
+
+template <int P, int DAG>
+__global__ void __launch_bounds__(256) dirac_kernel(Geom g, const void* __restrict__ U, FieldPtr A, FieldPtr in,
+                                                    FieldPtr out) {
+  typedef typename Arith<P>::T T;
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
+  Spinor<T> o = dirac_site<P, DAG, T>(g, U, A, in, blk, r);
+  store_spinor<P, T>(out, g.Vb, blk, r, o);
+}
+
+// deterministic block sum of a double: warp shuffles, then warps in order
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+  return t;
+}
+
+// r = b - D x (FP64), partial[blockIdx.x] = sum |r|^2 over the CTA
+__global__ void __launch_bounds__(256) residual64_kernel(Geom g, const void* __restrict__ U, FieldPtr A, FieldPtr b,
+                                                         FieldPtr x, FieldPtr r_out, double* partial) {
+  __shared__ double sh[32];
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double nrm = 0;
+  if (s < g.V) {
+    int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
+    Spinor<double> o = dirac_site<P64, 0, double>(g, U, A, x, blk, r);
+    Spinor<double> bb = load_spinor<P64, double>(b, g.Vb, blk, r);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        o.c[sp][a] = bb.c[sp][a] - o.c[sp][a];
+        nrm += o.c[sp][a].re * o.c[sp][a].re + o.c[sp][a].im * o.c[sp][a].im;
+      }
+    store_spinor<P64, double>(r_out, g.Vb, blk, r, o);
+  }
+  double t = block_sum(nrm, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+static double bytes_per_site(int prec) {
+  if (prec == P64) return 2 * 24 * 8 + 4 * 18 * 8 + 72 * 8;
+  if (prec == P32) return 2 * 24 * 4 + 4 * 12 * 4 + 72 * 4;
+  return 2 * (24 * 2 + 4) + 4 * 12 * 2 + (72 * 2 + 4);
+}
+
+int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s) {
+  const int prec = in.prec;
+  if (out.prec != prec || in.nreal != 24 || out.nreal != 24) return QCD_ERR_ARG;
+  QCD_TRY(ensure_gauge(c, prec, s));
+  QCD_TRY(ensure_clover(c, prec, s));
+  const int threads = c->dirac_threads;
+  const unsigned grid = (unsigned)((c->V + threads - 1) / threads);
+  const void* U = c->U[prec];
+  FieldPtr A = c->A[prec].ptr();
+  ProfScope ps(c, QCD_KERNEL_DIRAC, s, bytes_per_site(prec) * (double)c->V, 1824.0 * (double)c->V);
+#define LAUNCH(PP)                                                                                 \
+  if (dagger)                                                                                      \
+    dirac_kernel<PP, 1><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr());                 \
+  else                                                                                             \
+    dirac_kernel<PP, 0><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr());
+  switch (prec) {
+    case P64: LAUNCH(P64); break;
+    case P32: LAUNCH(P32); break;
+    case P16: LAUNCH(P16); break;
+    case PB16: LAUNCH(PB16); break;
+    default: return QCD_ERR_ARG;
+  }
+#undef LAUNCH
+  QCD_LAUNCHED();
+  return QCD_OK;
+}
+
+int residual64(qcd_ctx* c, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s) {
+  if (b.prec != P64 || x.prec != P64 || r.prec != P64) return QCD_ERR_ARG;
+  QCD_TRY(ensure_gauge(c, P64, s));
+  QCD_TRY(ensure_clover(c, P64, s));
+  const unsigned grid = (unsigned)((c->V + 255) / 256);
+  QCD_TRY(ensure_partials(c, grid));
+  {
+    ProfScope ps(c, QCD_KERNEL_RESIDUAL, s, (bytes_per_site(P64) + 192) * (double)c->V, 1848.0 * (double)c->V);
+    residual64_kernel<<<grid, 256, 0, s>>>(c->g, c->U[P64], c->A[P64].ptr(), b.ptr(), x.ptr(), r.ptr(),
+                                           c->d_partials);
+    QCD_LAUNCHED();
+  }
+  return reduce_partials(c->d_partials, (int)grid, 1, 1, d_norm2, s);
+}
+
+}  // namespace qcd

@@ -1,0 +1,188 @@
+// Host-side internals of libqcdgb: the context, resident fields, launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/qcdgb.h"
+#include "qcd.cuh"
+
+namespace qcd {
+
+// record a CUDA error message for qcd_last_error and return QCD_ERR_CUDA
+int cuda_fail(cudaError_t e, const char* where);
+
+#define QCD_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+// every kernel launch is counted (qcd_launch_count) and checked
+extern std::atomic<long long> g_launches;
+#define QCD_LAUNCHED()                                  \
+  do {                                                  \
+    g_launches.fetch_add(1, std::memory_order_relaxed); \
+    QCD_CUDA(cudaGetLastError());                       \
+  } while (0)
+
+#define QCD_TRY(call)          \
+  do {                         \
+    int st_ = (call);          \
+    if (st_ != QCD_OK) return st_; \
+  } while (0)
+
+inline int chunks(int prec, int nreal) {
+  int w = prec == P64 ? 2 : (prec == P32 ? 4 : 8);
+  return (nreal + w - 1) / w;
+}
+
+// a device field of N-real records per site in one precision
+struct Rec {
+  int prec = -1;
+  int nreal = 0;
+  void* data = nullptr;
+  float* norm = nullptr;  // per-site scale for 16-bit storage
+  size_t bytes = 0;       // data + norm
+  FieldPtr ptr() const { return FieldPtr{data, norm}; }
+};
+
+struct Timer {  // CUDA-event timing of one kernel class
+  long long launches = 0;
+  double total_ms = 0;
+  double bytes = 0, flops = 0;  // per launch, of the last launch
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+// SAP work fields: residual (SAP storage precision), accumulated solution
+// (FP32, FP64 for the FP64 variant) and the face buffers
+struct SapWork {
+  Rec rho, psi;
+  void* faces = nullptr;
+  size_t faces_bytes = 0;
+  int prec = -1;
+};
+
+// solver work fields (FP64 internal layout unless stated)
+struct Workspace {
+  SapWork sap;
+  int nkv = 0;
+  Rec b, x, r, rho, tmp64;
+  Rec lo_in, lo_out;  // reduced-precision operator scratch
+  std::vector<Rec> phi, chi;
+  double* d_a1 = nullptr;  // [nkv][nkv] complex, first Gram-Schmidt pass
+  double* d_a2 = nullptr;  // [nkv][nkv] complex, second pass
+  double* d_cr = nullptr;  // [nkv][3]: |chi_k|^2, (chi_k, rho_k)
+  double* d_rn = nullptr;  // [nkv + 8] residual norms
+  double* d_gam = nullptr; // [nkv] complex
+  double* h_pin = nullptr; // pinned host mirror for scalars read back
+};
+
+}  // namespace qcd
+
+struct qcd_field {
+  qcd_ctx* ctx;
+  qcd::Rec rec;
+};
+
+struct qcd_ctx {
+  qcd_params p;
+  qcd::Geom g;  // host copy; r2y/j2r are device pointers
+  int* d_tables = nullptr;
+  long long V = 0;
+  int nblk = 0;
+  bool gauge_loaded = false, clover_built = false;
+  void* U[4] = {nullptr, nullptr, nullptr, nullptr};  // gauge in each precision (lazy)
+  size_t U_bytes[4] = {0, 0, 0, 0};
+  qcd::Rec A[4];     // clover (4 + m0 + c_sw term), 72 reals per site
+  qcd::Rec Ahat[4];  // SAP block clover: A on even sites, A^-1 on odd sites
+  qcd::Workspace* ws = nullptr;
+  // instrumentation
+  bool prof = false;
+  qcd::Timer timers[QCD_KERNEL_COUNT];
+  std::vector<cudaEvent_t> event_pool;
+  // launch shape chosen by the autotuner
+  int dirac_threads = 256;
+  int sap_threads_per_site = 1;
+  // reduction scratch (FP64 partial sums)
+  double* d_partials = nullptr;
+  size_t partials_len = 0;
+  double* d_scalars = nullptr;  // small device array for coefficients
+  double* h_scalars = nullptr;  // pinned host mirror
+};
+
+namespace qcd {
+
+// ---- instrumentation (api.cu)
+struct ProfScope {
+  qcd_ctx* c;
+  int k;
+  cudaStream_t s;
+  cudaEvent_t e1 = nullptr;
+  ProfScope(qcd_ctx* ctx, int kernel, cudaStream_t st, double bytes, double flops);
+  ~ProfScope();
+};
+
+// ---- memory helpers (api.cu)
+int rec_alloc(Rec& r, int prec, int nreal, long long V);
+void rec_free(Rec& r);
+int ensure_partials(qcd_ctx* c, size_t n);
+Workspace* ensure_ws(qcd_ctx* c);
+
+// ---- layout.cu
+int setup_geometry(qcd_ctx* c);
+int import_spinor(qcd_ctx* c, const double* lex, const Rec& out, int nrhs, cudaStream_t s);
+int export_spinor(qcd_ctx* c, const Rec& in, double* lex, int nrhs, cudaStream_t s);
+int load_gauge_device(qcd_ctx* c, const double* lex_dev, cudaStream_t s);
+int ensure_gauge(qcd_ctx* c, int prec, cudaStream_t s);
+// convert records between precisions (same layout family)
+int convert_rec(qcd_ctx* c, const Rec& in, const Rec& out, cudaStream_t s);
+
+// ---- clover.cu
+int build_clover(qcd_ctx* c, cudaStream_t s);
+int ensure_clover(qcd_ctx* c, int prec, cudaStream_t s);
+
+// ---- dirac.cu
+// out = D in (dagger: D^+); fields in one precision
+int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s);
+// r = b - D x and |r|^2 partial sums (FP64); optional second output of D x
+int residual64(qcd_ctx* c, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s);
+
+// ---- sap.cu
+int sap_apply(qcd_ctx* c, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec, cudaStream_t s);
+
+// ---- blas.cu (FP64 fields of the context, 24 reals per site)
+// d_out[j] = (v_j, w) for j < k (complex, 2 doubles each)
+int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s);
+// w -= sum_j coef[j] v_j (coef on device, complex); then d_out[j] = (v_j, w) for j < k if d_out
+int blas_axpy_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w,
+                  double* d_out, cudaStream_t s);
+// w -= sum_j coef[j] v_j; d_out = {|w|^2, (w, rho)}
+int blas_axpy_norm_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w,
+                       const double* rho, double* d_out, cudaStream_t s);
+// chi *= 1/|chi| (norm from d_in); rho -= c chi_normalised; d_out = |rho|^2
+int blas_normalise_update(qcd_ctx* c, double* chi, double* rho, const double* d_coefs, double* d_out,
+                          cudaStream_t s);
+// x += sum_j gamma_j phi_j (gamma on device)
+int blas_multi_axpy(qcd_ctx* c, const double* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s);
+// norm2
+int blas_norm2(qcd_ctx* c, const double* v, double* d_out, cudaStream_t s);
+// y = g5 x (in place allowed)
+int blas_gamma5(qcd_ctx* c, const double* x, double* y, int nsites_layout, cudaStream_t s);
+// small dense solve of the FGCR triangular system on the device
+int fgcr_backsub(const double* d_a1, const double* d_a2, const double* d_cr, int k, int ld, double* d_gamma,
+                 cudaStream_t s);
+// out[j] = sum_p partials[p * stride + j], j < m (fixed order)
+int reduce_partials(const double* partials, int nparts, int stride, int m, double* out, cudaStream_t s);
+
+// ---- solver.cu
+int solve_one(qcd_ctx* c, const Rec& b, const Rec& x, const qcd_solver_params& sp, qcd_solve_info* info,
+              cudaStream_t s);
+void workspace_free(qcd_ctx* c);
+
+// ---- force.cu
+int force_apply(qcd_ctx* c, const Rec& x, const Rec& y, double* F, cudaStream_t s);
+
+}  // namespace qcd

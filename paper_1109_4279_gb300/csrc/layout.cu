@@ -1,0 +1,331 @@
+// Block-major even/odd layout (Sec. 5), spinor import/export, gauge-field
+// upload, SU(3) check and reduced-precision link compression.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace qcd {
+
+int setup_geometry(qcd_ctx* c) {
+  Geom& g = c->g;
+  long long V = 1;
+  int Vb = 1, nblk = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    int L = c->p.dims[mu], b = c->p.block[mu];
+    if (L <= 0 || b <= 0) return QCD_ERR_ARG;
+    if (b % 2 || L % b || (L / b) % 2 || b > 64) return QCD_ERR_GEOMETRY;
+    g.L[mu] = L;
+    g.b[mu] = b;
+    g.nb[mu] = L / b;
+    g.bc[mu] = c->p.bc[mu];
+    V *= L;
+    Vb *= b;
+    nblk *= L / b;
+  }
+  if (Vb > 4096) return QCD_ERR_GEOMETRY;
+  g.bstr[3] = 1;
+  g.ystr[3] = 1;
+  for (int mu = 2; mu >= 0; --mu) {
+    g.bstr[mu] = g.bstr[mu + 1] * g.nb[mu + 1];
+    g.ystr[mu] = g.ystr[mu + 1] * g.b[mu + 1];
+  }
+  g.Vb = Vb;
+  g.Vbh = Vb / 2;
+  g.nblk = nblk;
+  g.V = V;
+  c->V = V;
+  c->nblk = nblk;
+
+  // r <-> local coordinates.  b3 even: sites j and j ^ 1 differ only in y3,
+  // hence in parity, so (parity, j >> 1) enumerates each parity exactly once.
+  std::vector<int> tab(2 * Vb);
+  int* r2y = tab.data();
+  int* j2r = tab.data() + Vb;
+  for (int j = 0; j < Vb; ++j) {
+    int y[4], t = j;
+    for (int mu = 3; mu >= 0; --mu) {
+      y[mu] = t % g.b[mu];
+      t /= g.b[mu];
+    }
+    int par = (y[0] + y[1] + y[2] + y[3]) & 1;
+    int r = par * g.Vbh + (j >> 1);
+    j2r[j] = r;
+    r2y[r] = y[0] | (y[1] << 8) | (y[2] << 16) | (y[3] << 24);
+  }
+  QCD_CUDA(cudaMalloc(&c->d_tables, sizeof(int) * 2 * Vb));
+  QCD_CUDA(cudaMemcpy(c->d_tables, tab.data(), sizeof(int) * 2 * Vb, cudaMemcpyHostToDevice));
+  g.r2y = c->d_tables;
+  g.j2r = c->d_tables + Vb;
+  return QCD_OK;
+}
+
+// ------------------------------------------------------------------------
+// spinor import / export: lexicographic (V, 4, 3) complex128 <-> internal
+// ------------------------------------------------------------------------
+template <int P>
+__global__ void import_kernel(Geom g, const double* __restrict__ lex, FieldPtr out, long long field_stride_sites) {
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int rhs = blockIdx.y;
+  int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
+  int x[4];
+  global_coords(g, blk, r, x);
+  const double2* src = (const double2*)lex + ((long long)rhs * g.V + lex_index(g, x)) * 12;
+  double v[24];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    double2 d = __ldg(src + k);
+    v[2 * k] = d.x;
+    v[2 * k + 1] = d.y;
+  }
+  FieldPtr f = out;
+  const int NC = P == P64 ? 12 : (P == P32 ? 6 : 3);
+  f.data = (char*)out.data + (size_t)rhs * field_stride_sites * NC * 16;
+  if (out.norm) f.norm = out.norm + (size_t)rhs * field_stride_sites;
+  if constexpr (P == P64) {
+    store_record<P64, 24, double>(f, g.Vb, blk, r, v);
+  } else {
+    float w[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) w[k] = (float)v[k];
+    store_record<P, 24, float>(f, g.Vb, blk, r, w);
+  }
+}
+
+template <int P>
+__global__ void export_kernel(Geom g, FieldPtr in, double* __restrict__ lex, long long field_stride_sites) {
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int rhs = blockIdx.y;
+  int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
+  int x[4];
+  global_coords(g, blk, r, x);
+  FieldPtr f = in;
+  const int NC = P == P64 ? 12 : (P == P32 ? 6 : 3);
+  f.data = (char*)in.data + (size_t)rhs * field_stride_sites * NC * 16;
+  if (in.norm) f.norm = in.norm + (size_t)rhs * field_stride_sites;
+  double v[24];
+  if constexpr (P == P64) {
+    load_record<P64, 24, double>(f, g.Vb, blk, r, v);
+  } else {
+    float w[24];
+    load_record<P, 24, float>(f, g.Vb, blk, r, w);
+#pragma unroll
+    for (int k = 0; k < 24; ++k) v[k] = w[k];
+  }
+  double2* dst = (double2*)lex + ((long long)rhs * g.V + lex_index(g, x)) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) dst[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
+int import_spinor(qcd_ctx* c, const double* lex, const Rec& out, int nrhs, cudaStream_t s) {
+  if (out.nreal != 24) return QCD_ERR_ARG;
+  dim3 grid((unsigned)((c->V + 255) / 256), nrhs);
+  switch (out.prec) {
+    case P64: import_kernel<P64><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
+    case P32: import_kernel<P32><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
+    case P16: import_kernel<P16><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
+    case PB16: import_kernel<PB16><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
+    default: return QCD_ERR_ARG;
+  }
+  QCD_LAUNCHED();
+  return QCD_OK;
+}
+
+int export_spinor(qcd_ctx* c, const Rec& in, double* lex, int nrhs, cudaStream_t s) {
+  if (in.nreal != 24) return QCD_ERR_ARG;
+  dim3 grid((unsigned)((c->V + 255) / 256), nrhs);
+  switch (in.prec) {
+    case P64: export_kernel<P64><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
+    case P32: export_kernel<P32><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
+    case P16: export_kernel<P16><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
+    case PB16: export_kernel<PB16><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
+    default: return QCD_ERR_ARG;
+  }
+  QCD_LAUNCHED();
+  return QCD_OK;
+}
+
+// ------------------------------------------------------------------------
+// gauge field
+// ------------------------------------------------------------------------
+
+// lexicographic (V, 4, 3, 3) complex128 -> internal FP64 full links;
+// records max(|U U^+ - 1|, |det U - 1|) in *dev (as float bits, atomicMax)
+__global__ void gauge_import_kernel(Geom g, const double* __restrict__ lex, double2* __restrict__ U64,
+                                    unsigned int* dev) {
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
+  int x[4];
+  global_coords(g, blk, r, x);
+  const double2* src = (const double2*)lex + lex_index(g, x) * 36;
+  float worst = 0.f;
+  for (int mu = 0; mu < 4; ++mu) {
+    cpx<double> u[3][3];
+    for (int k = 0; k < 9; ++k) {
+      double2 d = __ldg(src + mu * 9 + k);
+      u[k / 3][k % 3] = {d.x, d.y};
+      U64[((long long)(blk * 4 + mu) * 9 + k) * g.Vb + r] = d;
+    }
+    double dev_u = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        cpx<double> v = {0, 0};
+        for (int k = 0; k < 3; ++k) v = cmadd(u[a][k], conjg(u[b][k]), v);
+        double re = v.re - (a == b ? 1.0 : 0.0);
+        dev_u = fmax(dev_u, fabs(re) + fabs(v.im));
+      }
+    cpx<double> det = cmul(u[0][0], cmul(u[1][1], u[2][2]) - cmul(u[1][2], u[2][1])) -
+                      cmul(u[0][1], cmul(u[1][0], u[2][2]) - cmul(u[1][2], u[2][0])) +
+                      cmul(u[0][2], cmul(u[1][0], u[2][1]) - cmul(u[1][1], u[2][0]));
+    dev_u = fmax(dev_u, fabs(det.re - 1.0) + fabs(det.im));
+    if (!(dev_u == dev_u)) dev_u = 1e30;  // NaN
+    worst = fmaxf(worst, (float)fmin(dev_u, 1e30));
+  }
+  atomicMax(dev, __float_as_uint(worst));
+}
+
+int load_gauge_device(qcd_ctx* c, const double* lex_dev, cudaStream_t s) {
+  if (!c->U[P64]) {
+    c->U_bytes[P64] = (size_t)c->V * GaugeLayout<P64>::bytes_per_site;
+    if (cudaMalloc(&c->U[P64], c->U_bytes[P64]) != cudaSuccess) {
+      c->U[P64] = nullptr;
+      return QCD_ERR_NOMEM;
+    }
+  }
+  for (int p = 1; p < 4; ++p)
+    if (c->U[p]) {
+      cudaFree(c->U[p]);
+      c->U[p] = nullptr;
+    }
+  unsigned int* d_dev = (unsigned int*)c->d_scalars;
+  QCD_CUDA(cudaMemsetAsync(d_dev, 0, sizeof(unsigned int), s));
+  gauge_import_kernel<<<(unsigned)((c->V + 255) / 256), 256, 0, s>>>(c->g, lex_dev, (double2*)c->U[P64], d_dev);
+  QCD_LAUNCHED();
+  unsigned int h = 0;
+  QCD_CUDA(cudaMemcpyAsync(&h, d_dev, sizeof(h), cudaMemcpyDeviceToHost, s));
+  QCD_CUDA(cudaStreamSynchronize(s));
+  float worst;
+  memcpy(&worst, &h, sizeof(worst));
+  c->gauge_loaded = true;
+  c->clover_built = false;
+  if (!(worst <= 1e-10f)) return QCD_ERR_NOT_SU3;
+  return QCD_OK;
+}
+
+template <int P>
+__global__ void gauge_compress_kernel(Geom g, const double2* __restrict__ U64, void* out) {
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
+  for (int mu = 0; mu < 4; ++mu) {
+    float f[12];
+    for (int k = 0; k < 6; ++k) {
+      double2 d = U64[((long long)(blk * 4 + mu) * 9 + k) * g.Vb + r];
+      f[2 * k] = (float)d.x;
+      f[2 * k + 1] = (float)d.y;
+    }
+    if constexpr (P == P32) {
+      float4* d = (float4*)out + ((long long)(blk * 4 + mu) * 3) * g.Vb + r;
+      for (int k = 0; k < 3; ++k)
+        d[(long long)k * g.Vb] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+    } else {
+      typedef typename Storage<P>::real hr;
+      char* base = (char*)out + (long long)blk * g.Vb * 96;
+      uint4 a;
+      uint2 b;
+      hr* ha = reinterpret_cast<hr*>(&a);
+      hr* hb = reinterpret_cast<hr*>(&b);
+      for (int e = 0; e < 8; ++e) ha[e] = from_f<P>(f[e]);
+      for (int e = 0; e < 4; ++e) hb[e] = from_f<P>(f[8 + e]);
+      ((uint4*)base)[(long long)mu * g.Vb + r] = a;
+      ((uint2*)(base + (long long)64 * g.Vb))[(long long)mu * g.Vb + r] = b;
+    }
+  }
+}
+
+int ensure_gauge(qcd_ctx* c, int prec, cudaStream_t s) {
+  if (!c->gauge_loaded) return QCD_ERR_STATE;
+  if (c->U[prec]) return QCD_OK;
+  size_t bytes = (size_t)c->V * (prec == P64 ? GaugeLayout<P64>::bytes_per_site
+                                             : (prec == P32 ? GaugeLayout<P32>::bytes_per_site
+                                                            : GaugeLayout<P16>::bytes_per_site));
+  if (cudaMalloc(&c->U[prec], bytes) != cudaSuccess) {
+    c->U[prec] = nullptr;
+    return QCD_ERR_NOMEM;
+  }
+  c->U_bytes[prec] = bytes;
+  unsigned grid = (unsigned)((c->V + 255) / 256);
+  const double2* U64 = (const double2*)c->U[P64];
+  switch (prec) {
+    case P32: gauge_compress_kernel<P32><<<grid, 256, 0, s>>>(c->g, U64, c->U[prec]); break;
+    case P16: gauge_compress_kernel<P16><<<grid, 256, 0, s>>>(c->g, U64, c->U[prec]); break;
+    case PB16: gauge_compress_kernel<PB16><<<grid, 256, 0, s>>>(c->g, U64, c->U[prec]); break;
+    default: return QCD_ERR_ARG;
+  }
+  QCD_LAUNCHED();
+  return QCD_OK;
+}
+
+// ------------------------------------------------------------------------
+// record conversion between precisions (spinors: 24 reals, clover: 72)
+// ------------------------------------------------------------------------
+template <int PI, int PO, int N>
+__global__ void convert_kernel(int Vb, long long V, FieldPtr in, FieldPtr out) {
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= V) return;
+  int blk = (int)(s / Vb), r = (int)(s - (long long)blk * Vb);
+  if constexpr (PI == P64 && PO == P64) {
+    double v[N];
+    load_record<PI, N, double>(in, Vb, blk, r, v);
+    store_record<PO, N, double>(out, Vb, blk, r, v);
+  } else if constexpr (PI == P64) {
+    double v[N];
+    load_record<PI, N, double>(in, Vb, blk, r, v);
+    float w[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = (float)v[k];
+    store_record<PO, N, float>(out, Vb, blk, r, w);
+  } else if constexpr (PO == P64) {
+    float w[N];
+    load_record<PI, N, float>(in, Vb, blk, r, w);
+    double v[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = w[k];
+    store_record<PO, N, double>(out, Vb, blk, r, v);
+  } else {
+    float w[N];
+    load_record<PI, N, float>(in, Vb, blk, r, w);
+    store_record<PO, N, float>(out, Vb, blk, r, w);
+  }
+}
+
+template <int N>
+static int convert_n(qcd_ctx* c, const Rec& in, const Rec& out, cudaStream_t s) {
+  unsigned grid = (unsigned)((c->V + 255) / 256);
+  int Vb = c->g.Vb;
+  long long V = c->V;
+#define CV(PI, PO)                                                                     \
+  if (in.prec == PI && out.prec == PO) {                                               \
+    convert_kernel<PI, PO, N><<<grid, 256, 0, s>>>(Vb, V, in.ptr(), out.ptr());        \
+    QCD_LAUNCHED();                                                      \
+    return QCD_OK;                                                                     \
+  }
+  CV(P64, P64) CV(P64, P32) CV(P64, P16) CV(P64, PB16)
+  CV(P32, P64) CV(P32, P32) CV(P32, P16) CV(P32, PB16)
+  CV(P16, P64) CV(P16, P32) CV(PB16, P64) CV(PB16, P32)
+#undef CV
+  return QCD_ERR_UNSUPPORTED;
+}
+
+int convert_rec(qcd_ctx* c, const Rec& in, const Rec& out, cudaStream_t s) {
+  if (in.nreal != out.nreal) return QCD_ERR_ARG;
+  if (in.nreal == 24) return convert_n<24>(c, in, out, s);
+  if (in.nreal == 72) return convert_n<72>(c, in, out, s);
+  return QCD_ERR_ARG;
+}
+
+}  // namespace qcd

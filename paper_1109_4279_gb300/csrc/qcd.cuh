@@ -1,0 +1,521 @@
+// Device-side building blocks shared by the qcdgb kernels: complex arithmetic,
+// lattice geometry, the block-major even/odd field layout, chiral-basis spin
+// projection and precision-specific field access.
+//
+// Layout (Sec. 5: "points belonging to the same block are contiguous; inside
+// the blocks, lattice points are divided into two sets, even and odd"):
+//   internal site s = blk * Vb + r, blk = lexicographic Schwarz-block index
+//   (block coordinate n3 fastest), r < Vb/2 even sites, r >= Vb/2 odd sites,
+//   each parity ordered by the in-block lexicographic index j >> 1.
+//   A field with NC 16-byte chunks per site is stored [blk][chunk][r]: one
+//   block's data is one contiguous range (a single bulk copy stages it) and
+//   consecutive threads touch consecutive 16-byte words (coalesced).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qcd {
+
+enum Prec : int { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+
+// ------------------------------------------------------------------------
+// complex arithmetic
+// ------------------------------------------------------------------------
+template <typename T>
+struct cpx {
+  T re, im;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> mk(T r, T i) { return cpx<T>{r, i}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> operator-(cpx<T> a) { return {-a.re, -a.im}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return {s * a.re, s * a.im}; }
+// a * b
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// c + a * b
+template <typename T>
+__device__ __forceinline__ cpx<T> cmadd(cpx<T> a, cpx<T> b, cpx<T> c) {
+  return {fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im))};
+}
+// c + conj(a) * b
+template <typename T>
+__device__ __forceinline__ cpx<T> cjmadd(cpx<T> a, cpx<T> b, cpx<T> c) {
+  return {fma(a.re, b.re, fma(a.im, b.im, c.re)), fma(a.re, b.im, fma(-a.im, b.re, c.im))};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> conjg(cpx<T> a) { return {a.re, -a.im}; }
+// i * a
+template <typename T>
+__device__ __forceinline__ cpx<T> ti(cpx<T> a) { return {-a.im, a.re}; }
+// -i * a
+template <typename T>
+__device__ __forceinline__ cpx<T> mti(cpx<T> a) { return {a.im, -a.re}; }
+
+template <typename T>
+struct Spinor {
+  cpx<T> c[4][3];  // [spin][colour]
+};
+template <typename T>
+struct Half {
+  cpx<T> c[2][3];  // two spin components after projection
+};
+template <typename T>
+struct SU3 {
+  cpx<T> m[3][3];
+};
+
+template <typename T>
+__device__ __forceinline__ void zero(Spinor<T>& s) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) s.c[a][b] = {T(0), T(0)};
+}
+
+// third row of an SU(3) matrix from the first two: row2 = conj(row0 x row1)
+template <typename T>
+__device__ __forceinline__ void reconstruct(SU3<T>& u) {
+  u.m[2][0] = conjg(cmul(u.m[0][1], u.m[1][2]) - cmul(u.m[0][2], u.m[1][1]));
+  u.m[2][1] = conjg(cmul(u.m[0][2], u.m[1][0]) - cmul(u.m[0][0], u.m[1][2]));
+  u.m[2][2] = conjg(cmul(u.m[0][0], u.m[1][1]) - cmul(u.m[0][1], u.m[1][0]));
+}
+
+// w = U h  (two spin components)
+template <typename T>
+__device__ __forceinline__ Half<T> umul(const SU3<T>& u, const Half<T>& h) {
+  Half<T> w;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cpx<T> v = cmul(u.m[a][0], h.c[s][0]);
+      v = cmadd(u.m[a][1], h.c[s][1], v);
+      v = cmadd(u.m[a][2], h.c[s][2], v);
+      w.c[s][a] = v;
+    }
+  return w;
+}
+
+// w = U^+ h
+template <typename T>
+__device__ __forceinline__ Half<T> udmul(const SU3<T>& u, const Half<T>& h) {
+  Half<T> w;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cpx<T> v = {T(0), T(0)};
+      v = cjmadd(u.m[0][a], h.c[s][0], v);
+      v = cjmadd(u.m[1][a], h.c[s][1], v);
+      v = cjmadd(u.m[2][a], h.c[s][2], v);
+      w.c[s][a] = v;
+    }
+  return w;
+}
+
+// ------------------------------------------------------------------------
+// Spin projection in the chiral basis.  Every g_mu has the form
+// [[0, B], [B^+, 0]] with B unitary (B = -1, -i s1, -i s2, -i s3 for
+// mu = 0..3), so (1 + S g_mu) psi = [h ; S B^+ h] with h = psi_u + S B psi_l:
+// the projected spinor is carried by its two upper spin components.
+// ------------------------------------------------------------------------
+template <int MU, int S, typename T>
+__device__ __forceinline__ Half<T> project(const Spinor<T>& p) {
+  Half<T> h;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (MU == 0) {  // B psi_l = (-psi2, -psi3)
+      h.c[0][a] = (S > 0) ? p.c[0][a] - p.c[2][a] : p.c[0][a] + p.c[2][a];
+      h.c[1][a] = (S > 0) ? p.c[1][a] - p.c[3][a] : p.c[1][a] + p.c[3][a];
+    } else if (MU == 1) {  // B psi_l = (-i psi3, -i psi2)
+      h.c[0][a] = (S > 0) ? p.c[0][a] + mti(p.c[3][a]) : p.c[0][a] + ti(p.c[3][a]);
+      h.c[1][a] = (S > 0) ? p.c[1][a] + mti(p.c[2][a]) : p.c[1][a] + ti(p.c[2][a]);
+    } else if (MU == 2) {  // B psi_l = (-psi3, psi2)
+      h.c[0][a] = (S > 0) ? p.c[0][a] - p.c[3][a] : p.c[0][a] + p.c[3][a];
+      h.c[1][a] = (S > 0) ? p.c[1][a] + p.c[2][a] : p.c[1][a] - p.c[2][a];
+    } else {  // B psi_l = (-i psi2, i psi3)
+      h.c[0][a] = (S > 0) ? p.c[0][a] + mti(p.c[2][a]) : p.c[0][a] + ti(p.c[2][a]);
+      h.c[1][a] = (S > 0) ? p.c[1][a] + ti(p.c[3][a]) : p.c[1][a] + mti(p.c[3][a]);
+    }
+  }
+  return h;
+}
+
+// acc += coef * [w ; S B^+ w]   (inverse of project<MU, S>)
+template <int MU, int S, typename T>
+__device__ __forceinline__ void expand_add(Spinor<T>& acc, const Half<T>& w, T coef) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cpx<T> w0 = coef * w.c[0][a], w1 = coef * w.c[1][a];
+    acc.c[0][a] = acc.c[0][a] + w0;
+    acc.c[1][a] = acc.c[1][a] + w1;
+    cpx<T> l0, l1;  // B^+ w
+    if (MU == 0) {
+      l0 = -w0; l1 = -w1;
+    } else if (MU == 1) {
+      l0 = ti(w1); l1 = ti(w0);
+    } else if (MU == 2) {
+      l0 = w1; l1 = -w0;
+    } else {
+      l0 = ti(w0); l1 = mti(w1);
+    }
+    if (S > 0) {
+      acc.c[2][a] = acc.c[2][a] + l0;
+      acc.c[3][a] = acc.c[3][a] + l1;
+    } else {
+      acc.c[2][a] = acc.c[2][a] - l0;
+      acc.c[3][a] = acc.c[3][a] - l1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Geometry
+// ------------------------------------------------------------------------
+struct Geom {
+  int L[4];         // lattice extents, L[0] = time
+  int b[4];         // Schwarz block extents (even)
+  int nb[4];        // blocks per direction (even)
+  int bstr[4];      // stride of block coordinate mu in the block index
+  int ystr[4];      // stride of local coordinate mu in the in-block lexicographic index
+  int Vb, Vbh;      // sites per block, half of it
+  int nblk;         // number of blocks
+  long long V;      // lattice volume
+  double bc[4];     // sign of the hop that wraps around direction mu
+  const int* r2y;   // r -> packed local coordinates (8 bits each, mu = 0 lowest)
+  const int* j2r;   // in-block lexicographic index -> r
+};
+
+__device__ __forceinline__ int ycoord(int packed, int mu) { return (packed >> (8 * mu)) & 0xff; }
+
+__device__ __forceinline__ void block_coords(const Geom& g, int blk, int n[4]) {
+  int t = blk;
+  n[3] = t % g.nb[3]; t /= g.nb[3];
+  n[2] = t % g.nb[2]; t /= g.nb[2];
+  n[1] = t % g.nb[1];
+  n[0] = t / g.nb[1];
+}
+
+struct Nbr {
+  int blk, r;
+  bool wrap;  // the hop crosses the lattice boundary in its direction
+};
+
+// neighbour of site (blk, r) with local coordinates y and block coordinates n,
+// one step in direction mu (dir = +1 forward, -1 backward)
+__device__ __forceinline__ Nbr neighbour(const Geom& g, int blk, const int y[4], const int n[4], int mu, int dir) {
+  int j = y[0] * g.ystr[0] + y[1] * g.ystr[1] + y[2] * g.ystr[2] + y[3] * g.ystr[3];
+  Nbr o;
+  o.wrap = false;
+  o.blk = blk;
+  if (dir > 0) {
+    if (y[mu] + 1 < g.b[mu]) {
+      j += g.ystr[mu];
+    } else {
+      j -= (g.b[mu] - 1) * g.ystr[mu];
+      if (n[mu] + 1 < g.nb[mu]) {
+        o.blk += g.bstr[mu];
+      } else {
+        o.blk -= (g.nb[mu] - 1) * g.bstr[mu];
+        o.wrap = true;
+      }
+    }
+  } else {
+    if (y[mu] > 0) {
+      j -= g.ystr[mu];
+    } else {
+      j += (g.b[mu] - 1) * g.ystr[mu];
+      if (n[mu] > 0) {
+        o.blk -= g.bstr[mu];
+      } else {
+        o.blk += (g.nb[mu] - 1) * g.bstr[mu];
+        o.wrap = true;
+      }
+    }
+  }
+  o.r = __ldg(g.j2r + j);
+  return o;
+}
+
+// internal index of the site with global coordinates x (0 <= x_mu < L_mu)
+__device__ __forceinline__ long long internal_index(const Geom& g, const int x[4]) {
+  int blk = 0, j = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    blk += (x[mu] / g.b[mu]) * g.bstr[mu];
+    j += (x[mu] % g.b[mu]) * g.ystr[mu];
+  }
+  return (long long)blk * g.Vb + __ldg(g.j2r + j);
+}
+
+__device__ __forceinline__ void global_coords(const Geom& g, int blk, int r, int x[4]) {
+  int n[4];
+  block_coords(g, blk, n);
+  int p = __ldg(g.r2y + r);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) x[mu] = n[mu] * g.b[mu] + ycoord(p, mu);
+}
+
+__device__ __forceinline__ long long lex_index(const Geom& g, const int x[4]) {
+  return ((long long)(x[0] * g.L[1] + x[1]) * g.L[2] + x[2]) * g.L[3] + x[3];
+}
+
+// ------------------------------------------------------------------------
+// Field access.  A field is a base pointer plus (for 16-bit storage) a
+// per-site FP32 scale array.  Element e of a record of N reals lives in
+// chunk e / (16 / sizeof(storage)) of the site.
+// ------------------------------------------------------------------------
+struct FieldPtr {
+  void* data;
+  float* norm;  // per-site scale (16-bit storage only), indexed by internal site
+};
+
+template <int P>
+struct Storage;
+template <>
+struct Storage<P64> {
+  typedef double real;
+  static constexpr int per_chunk = 2;
+};
+template <>
+struct Storage<P32> {
+  typedef float real;
+  static constexpr int per_chunk = 4;
+};
+template <>
+struct Storage<P16> {
+  typedef __half real;
+  static constexpr int per_chunk = 8;
+};
+template <>
+struct Storage<PB16> {
+  typedef __nv_bfloat16 real;
+  static constexpr int per_chunk = 8;
+};
+
+template <int P>
+__device__ __forceinline__ float to_f(typename Storage<P>::real v);
+template <>
+__device__ __forceinline__ float to_f<P16>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float to_f<PB16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <int P>
+__device__ __forceinline__ typename Storage<P>::real from_f(float v);
+template <>
+__device__ __forceinline__ __half from_f<P16>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<PB16>(float v) { return __float2bfloat16_rn(v); }
+
+// load N reals (N a multiple of the chunk width) of site (blk, r) of a field
+// with NC chunks per site; T is the arithmetic type
+template <int P, int N, typename T>
+__device__ __forceinline__ void load_record(const FieldPtr& f, int Vb, int blk, int r, T* out) {
+  constexpr int W = Storage<P>::per_chunk;
+  constexpr int NC = (N + W - 1) / W;
+  const long long base = (long long)blk * NC * Vb + r;
+  if constexpr (P == P64) {
+    const double2* d = (const double2*)f.data;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      double2 v = __ldg(d + base + (long long)k * Vb);
+      out[2 * k] = (T)v.x;
+      out[2 * k + 1] = (T)v.y;
+    }
+  } else if constexpr (P == P32) {
+    const float4* d = (const float4*)f.data;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      float4 v = __ldg(d + base + (long long)k * Vb);
+      out[4 * k] = v.x;
+      out[4 * k + 1] = v.y;
+      out[4 * k + 2] = v.z;
+      out[4 * k + 3] = v.w;
+    }
+  } else {
+    const uint4* d = (const uint4*)f.data;
+    const float s = f.norm ? __ldg(f.norm + (long long)blk * Vb + r) : 1.0f;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      uint4 v = __ldg(d + base + (long long)k * Vb);
+      const typename Storage<P>::real* h = reinterpret_cast<const typename Storage<P>::real*>(&v);
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (8 * k + e < N) out[8 * k + e] = s * to_f<P>(h[e]);
+    }
+  }
+}
+
+// store N reals; 16-bit storage computes the per-site max-abs scale
+template <int P, int N, typename T>
+__device__ __forceinline__ void store_record(const FieldPtr& f, int Vb, int blk, int r, const T* in) {
+  constexpr int W = Storage<P>::per_chunk;
+  constexpr int NC = (N + W - 1) / W;
+  const long long base = (long long)blk * NC * Vb + r;
+  if constexpr (P == P64) {
+    double2* d = (double2*)f.data;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) d[base + (long long)k * Vb] = make_double2((double)in[2 * k], (double)in[2 * k + 1]);
+  } else if constexpr (P == P32) {
+    float4* d = (float4*)f.data;
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+      d[base + (long long)k * Vb] = make_float4((float)in[4 * k], (float)in[4 * k + 1], (float)in[4 * k + 2], (float)in[4 * k + 3]);
+  } else {
+    float m = 0.f;
+#pragma unroll
+    for (int e = 0; e < N; ++e) m = fmaxf(m, fabsf((float)in[e]));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+    uint4* d = (uint4*)f.data;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      uint4 v;
+      typename Storage<P>::real* h = reinterpret_cast<typename Storage<P>::real*>(&v);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) h[e] = from_f<P>(8 * k + e < N ? (float)in[8 * k + e] * inv : 0.f);
+      d[base + (long long)k * Vb] = v;
+    }
+    f.norm[(long long)blk * Vb + r] = m;
+  }
+}
+
+// spinor: 24 reals, component (spin s, colour c) at reals 6 s + 2 c
+template <int P, typename T>
+__device__ __forceinline__ Spinor<T> load_spinor(const FieldPtr& f, int Vb, int blk, int r) {
+  T v[24];
+  load_record<P, 24, T>(f, Vb, blk, r, v);
+  Spinor<T> s;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) s.c[a][b] = {v[6 * a + 2 * b], v[6 * a + 2 * b + 1]};
+  return s;
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void store_spinor(const FieldPtr& f, int Vb, int blk, int r, const Spinor<T>& s) {
+  T v[24];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      v[6 * a + 2 * b] = s.c[a][b].re;
+      v[6 * a + 2 * b + 1] = s.c[a][b].im;
+    }
+  store_record<P, 24, T>(f, Vb, blk, r, v);
+}
+
+// ------------------------------------------------------------------------
+// Gauge field.  FP64: full 18 reals per link ([blk][mu][9 double2][r]), since
+// the FP64 operator is bound by FP64 arithmetic, not bytes.  FP32: rows 0-1
+// (12 reals, [blk][mu][3 float4][r]).  16-bit: rows 0-1 as 8 + 4 values,
+// [blk][mu][r] uint4 followed by [blk][mu][r] uint2, no scale (|U_ab| <= 1).
+// ------------------------------------------------------------------------
+template <int P>
+struct GaugeLayout;
+template <>
+struct GaugeLayout<P64> {
+  static constexpr long long bytes_per_site = 4 * 18 * 8;
+};
+template <>
+struct GaugeLayout<P32> {
+  static constexpr long long bytes_per_site = 4 * 12 * 4;
+};
+template <>
+struct GaugeLayout<P16> {
+  static constexpr long long bytes_per_site = 4 * 12 * 2;
+};
+template <>
+struct GaugeLayout<PB16> {
+  static constexpr long long bytes_per_site = 4 * 12 * 2;
+};
+
+template <int P, typename T>
+__device__ __forceinline__ SU3<T> load_link(const void* U, int Vb, int blk, int r, int mu) {
+  SU3<T> u;
+  if constexpr (P == P64) {
+    const double2* d = (const double2*)U + ((long long)(blk * 4 + mu) * 9) * Vb + r;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 v = __ldg(d + (long long)k * Vb);
+      u.m[k / 3][k % 3] = {(T)v.x, (T)v.y};
+    }
+  } else if constexpr (P == P32) {
+    const float4* d = (const float4*)U + ((long long)(blk * 4 + mu) * 3) * Vb + r;
+    float f[12];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float4 v = __ldg(d + (long long)k * Vb);
+      f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) u.m[k / 3][k % 3] = {(T)f[2 * k], (T)f[2 * k + 1]};
+    reconstruct(u);
+  } else {
+    typedef typename Storage<P>::real hr;
+    const char* base = (const char*)U + (long long)blk * Vb * 96;
+    uint4 a = __ldg((const uint4*)base + (long long)mu * Vb + r);
+    uint2 b = __ldg((const uint2*)(base + (long long)64 * Vb) + (long long)mu * Vb + r);
+    const hr* ha = reinterpret_cast<const hr*>(&a);
+    const hr* hb = reinterpret_cast<const hr*>(&b);
+    float f[12];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) f[e] = to_f<P>(ha[e]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) f[8 + e] = to_f<P>(hb[e]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) u.m[k / 3][k % 3] = {(T)f[2 * k], (T)f[2 * k + 1]};
+    reconstruct(u);
+  }
+  return u;
+}
+
+// ------------------------------------------------------------------------
+// Clover: two Hermitian 6x6 chiral blocks, 36 reals each: 6 diagonal reals,
+// then the 15 upper off-diagonal elements (i < j, row-major) as (re, im).
+// Block 0 acts on spins 0-1, block 1 on spins 2-3; index within a block is
+// (spin % 2) * 3 + colour.
+// ------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void clover_block_apply(const T* c, const cpx<T>* in, cpx<T>* out) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) out[i] = c[i] * in[i];
+  int k = 6;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) {
+      cpx<T> a = {c[k], c[k + 1]};
+      k += 2;
+      out[i] = cmadd(a, in[j], out[i]);
+      out[j] = cjmadd(a, in[i], out[j]);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ Spinor<T> clover_apply(const T* c72, const Spinor<T>& p) {
+  Spinor<T> o;
+  cpx<T> in[6], out[6];
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) in[i] = p.c[2 * blk + i / 3][i % 3];
+    clover_block_apply(c72 + 36 * blk, in, out);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o.c[2 * blk + i / 3][i % 3] = out[i];
+  }
+  return o;
+}
+
+}  // namespace qcd

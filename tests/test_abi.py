@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads and exports every symbol include/qcdgb.h declares (CPU only).
+
+No compute call is made here: there is no GPU on the build host.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "qcdgb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(qcd_[A-Za-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1109_4279_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ["qcd_create", "qcd_load_gauge", "qcd_build_clover", "qcd_apply_D", "qcd_solve",
+              "qcd_solve_batch", "qcd_gradient", "qcd_autotune", "qcd_status_string", "qcd_destroy"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu(lib):
+    lib.qcd_status_string.restype = ctypes.c_char_p
+    assert lib.qcd_status_string(0) == b"ok"
+    assert b"even" in lib.qcd_status_string(-2)
+
+
+def test_binding_names_match_header():
+    from paper_1109_4279_gb300 import binding
+    for n in _declared():
+        if n in ("qcd_solver_defaults", "qcd_last_error"):
+            continue
+        assert hasattr(binding, n), n
