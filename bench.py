@@ -31,7 +31,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "32^3x64 fp16"
+WORKLOAD = "32^3x64_fp16"
+# the benchmarked solve, and a smaller lattice of the same recipe whose
+# working set still exceeds L2 (used for detailed profiler captures)
+BENCH_WORKLOADS = {
+    "32^3x64_fp16": dict(dims=(64, 32, 32, 32), eps=0.5, seed=3, m0=-0.05, csw=1.5, block=(4, 4, 4, 4),
+                         nmr=4, ncy=4, nkv=16),
+    "24^3x48_fp16": dict(dims=(48, 24, 24, 24), eps=0.5, seed=4, m0=-0.05, csw=1.5, block=(4, 4, 4, 4),
+                         nmr=4, ncy=4, nkv=16),
+}
 METRIC = "SAP+FGCR time to |r|/|b|<1e-10 and D_w GB/s vs HBM peak, 1 GB300"
 # algorithmic bytes per site of one operator apply: spinor in + out, 4 links
 # as 12 reals (two rows), 72-real clover; 16-bit adds the per-site scales
@@ -112,9 +120,9 @@ class ClockSampler:
         return out
 
 
-def make_inputs():
+def make_inputs(workload=WORKLOAD):
     from paper_1109_4279_gb300 import synth
-    w = synth.WORKLOADS[WORKLOAD]
+    w = BENCH_WORKLOADS[workload]
     U, rng = synth.gauge_field(w["dims"], w["eps"], w["seed"])
     b = synth.gaussian_spinor(w["dims"], rng)
     return w, U, b
@@ -140,12 +148,13 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(world, value):
+def max_over_ranks(world, value, device="cuda"):
+    """Largest value over all ranks (the slowest rank's time)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -168,7 +177,7 @@ def oracle_iteration_seconds(w, U, b):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
-    w, U, b = make_inputs()
+    w, U, b = make_inputs(args.workload)
     iters = args.gpu_iterations
     times = []
     threads = 0
@@ -178,12 +187,12 @@ def run_reference(args, world, rank):
             times.append(t)
     t_iter = statistics.median(times)
     value = t_iter * iters
-    sample = ("one SAP-FGCR iteration of the oracle on the full 32^3x64 lattice per step (clover build not "
-              "timed), extrapolated x%d iterations (the GPU solve's count)" % iters)
+    sample = ("one SAP-FGCR iteration of the oracle on the full %s lattice per step (clover build not "
+              "timed), extrapolated x%d iterations (the GPU solve's count)" % (args.workload.split()[0], iters))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dims": list(w["dims"]), "block": list(w["block"]),
+            "config": {"workload": args.workload, "dims": list(w["dims"]), "block": list(w["block"]),
                        "m0": w["m0"], "csw": w["csw"], "ncy": w["ncy"], "nmr": w["nmr"], "nkv": w["nkv"]},
             "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -223,7 +232,7 @@ def run_ours(args, world, rank, local):
     from paper_1109_4279_gb300 import binding as B
 
     pk = peaks()
-    w, U, b = make_inputs()
+    w, U, b = make_inputs(args.workload)
     V = int(np.prod(w["dims"]))
     lat = B.Lattice(w["dims"], w["block"], w["m0"], w["csw"])
     lat.load_gauge(torch.from_numpy(U).cuda())
@@ -321,21 +330,21 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_iter, threads = oracle_iteration_seconds(w, U, b)
         cpu = {"value": t_iter * iters, "unit": "s", "cores": threads, "kind": "oracle",
-               "sample": "one SAP-FGCR iteration of the FP64 oracle on the full 32^3x64 lattice "
-                         "(%.1f s), extrapolated x%d iterations" % (t_iter, iters)}
+               "sample": "one SAP-FGCR iteration of the FP64 oracle on the full %s lattice "
+                         "(%.1f s), extrapolated x%d iterations" % (args.workload.split()[0], t_iter, iters)}
 
     line = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 outer + f32 arithmetic on f16 SAP storage", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dims": list(w["dims"]), "block": list(w["block"]), "m0": w["m0"],
+            "config": {"workload": args.workload, "dims": list(w["dims"]), "block": list(w["block"]), "m0": w["m0"],
                        "csw": w["csw"], "eps": w["eps"], "seed": w["seed"], "tol": 1e-10, "nkv": w["nkv"],
                        "ncy": w["ncy"], "nmr": w["nmr"], "sap_prec": "f16", "outer_prec": "f64",
                        "iterations": iters, "restarts": int(statistics.median(i["restarts"] for i in infos)),
                        "true_residual": max(i["true_residual"] for i in infos),
-                       "l2": "no flush: every solver vector (403 MB FP64) and field exceeds the 129 MB L2"},
+                       "l2": "no flush: every FP64 solver vector (192 B/site) and the gauge/clover fields exceed the 129 MB L2"},
             "roofline": roof, "kernels": kernels, "dw": dw,
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * fbytes, "d2h_bytes_per_step": fbytes},
-            "gpu_launches": launches // args.steps * args.steps if launches else 0,
+            "gpu_launches": launches,
             "clocks": clk.summary(), "cpu_baseline": cpu,
             "peaks": {"hbm_gbs": pk["hbm_gbs"], "fp32_tflops": pk["fp32_tflops"], "fp64_tflops": pk["fp64_tflops"],
                       "source": pk["source"]}}
@@ -351,8 +360,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--gpu-iterations", type=int, default=40,
-                    help="reference arm: FGCR iterations of the GPU solve used to extrapolate the oracle")
+    ap.add_argument("--workload", choices=sorted(BENCH_WORKLOADS), default=WORKLOAD)
+    ap.add_argument("--gpu-iterations", type=int, default=7,
+                    help="reference arm: FGCR iterations the GPU solve of this workload needs (measured: 7)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -64,24 +64,37 @@ int reduce_partials(const double* partials, int nparts, int stride, int m, doubl
   return QCD_OK;
 }
 
-// out[j] = (v_j, w) = sum conj(v_j) w, j < k <= K
-template <int K>
+// true if the Gram-Schmidt pass must be repeated (DGKS criterion): the first
+// pass left less than half of the squared norm, |chi'|^2 < |chi|^2 / 2.
+// gs = {|chi|^2, |chi'|^2, ...}; a null gs means "always".
+__device__ __forceinline__ bool second_pass_needed(const double* gs) {
+  return gs == nullptr || gs[1] < 0.5 * gs[0];
+}
+
+// out[j] = (v_j, w) = sum conj(v_j) w, j < k <= K; with NORM also out[2K] = |w|^2.
+// cond (optional): skip unless second_pass_needed(cond) -- then the partial
+// sums are zero, so the reduced coefficients are zero.
+template <int K, int NORM>
 __global__ void __launch_bounds__(kBlasThreads) multidot_kernel(VecList vl, int k, const double2* __restrict__ w,
-                                                                long long n, double* part) {
-  double acc[2 * K];
+                                                                long long n, const double* cond, double* part) {
+  double acc[2 * K + NORM];
 #pragma unroll
-  for (int j = 0; j < 2 * K; ++j) acc[j] = 0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double2 b = __ldg(w + i);
+  for (int j = 0; j < 2 * K + NORM; ++j) acc[j] = 0;
+  if (cond == nullptr || second_pass_needed(cond)) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+      const double2 b = __ldg(w + i);
 #pragma unroll
-    for (int j = 0; j < K; ++j)
-      if (j < k) {
-        const double2 a = __ldg(vl.v[j] + i);
-        acc[2 * j] = fma(a.x, b.x, fma(a.y, b.y, acc[2 * j]));
-        acc[2 * j + 1] = fma(a.x, b.y, fma(-a.y, b.x, acc[2 * j + 1]));
-      }
+      for (int j = 0; j < K; ++j)
+        if (j < k) {
+          const double2 a = __ldg(vl.v[j] + i);
+          acc[2 * j] = fma(a.x, b.x, fma(a.y, b.y, acc[2 * j]));
+          acc[2 * j + 1] = fma(a.x, b.y, fma(-a.y, b.x, acc[2 * j + 1]));
+        }
+      if (NORM) acc[2 * K] = fma(b.x, b.x, fma(b.y, b.y, acc[2 * K]));
+    }
   }
-  cta_reduce_store<2 * K>(acc, part);
+  cta_reduce_store<2 * K + NORM>(acc, part);
 }
 
 // w -= sum_j c_j v_j; then out[j] = (v_j, w) (DOT = 1) or out = {|w|^2, (w, rho)} (DOT = 2)
@@ -89,8 +102,9 @@ template <int K, int DOT>
 __global__ void __launch_bounds__(kBlasThreads) axpy_dot_kernel(VecList vl, int k, const double* __restrict__ coef,
                                                                 double2* __restrict__ w,
                                                                 const double2* __restrict__ rho, long long n,
-                                                                double* part) {
+                                                                const double* cond, double* part) {
   constexpr int M = DOT == 1 ? 2 * K : 3;
+  if (cond != nullptr && !second_pass_needed(cond)) return;  // block-uniform: no partials written
   double acc[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) acc[j] = 0;
@@ -125,15 +139,24 @@ __global__ void __launch_bounds__(kBlasThreads) axpy_dot_kernel(VecList vl, int 
   cta_reduce_store<M>(acc, part);
 }
 
-// coefs = {|chi|^2, Re (chi, rho), Im (chi, rho)}:  chi /= |chi|;
-// rho -= ((chi, rho) / |chi|^2) chi_unnormalised;  partial |rho|^2
+// Final Gram-Schmidt coefficients of iteration k: gs = {|chi|^2 before,
+// pass-1 {|chi'|^2, Re, Im (chi', rho)}, pass-2 {...}}; the pass-2 values
+// are used when the second pass ran.  Thread 0 of CTA 0 stores them in
+// cr = {|chi_k|^2, (chi_k, rho_k)}.  Then chi /= |chi|;
+// rho -= ((chi, rho) / |chi|^2) chi_unnormalised;  partial |rho|^2.
 __global__ void __launch_bounds__(kBlasThreads) normalise_update_kernel(double2* __restrict__ chi,
                                                                         double2* __restrict__ rho,
-                                                                        const double* __restrict__ coefs, long long n,
-                                                                        double* part) {
-  const double nrm2 = coefs[0];
+                                                                        const double* __restrict__ gs, int two_pass,
+                                                                        double* cr, long long n, double* part) {
+  const double* co = (two_pass && second_pass_needed(gs)) ? gs + 4 : gs + 1;
+  const double nrm2 = co[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cr[0] = co[0];
+    cr[1] = co[1];
+    cr[2] = co[2];
+  }
   const double inv = nrm2 > 0 ? 1.0 / sqrt(nrm2) : 0.0;
-  const double cre = nrm2 > 0 ? coefs[1] / nrm2 : 0.0, cim = nrm2 > 0 ? coefs[2] / nrm2 : 0.0;
+  const double cre = nrm2 > 0 ? co[1] / nrm2 : 0.0, cim = nrm2 > 0 ? co[2] / nrm2 : 0.0;
   double acc[1] = {0};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double2 x = chi[i];
@@ -215,7 +238,8 @@ static VecList make_list(const double* const* v, int k) {
   return vl;
 }
 
-int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s) {
+int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s,
+                  const double* cond, double* d_norm) {
   if (k <= 0) return QCD_OK;
   if (k > kMaxVec) return QCD_ERR_ARG;
   const long long n = c->V * 12;
@@ -225,17 +249,27 @@ int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, do
   if (k <= 4) K = 4; else if (k <= 8) K = 8; else if (k <= 16) K = 16; else K = 32;
   int done = 0;
   while (done < k) {
-    int kk = k - done < K ? k - done : K;
-    QCD_TRY(ensure_partials(c, (size_t)grid * 2 * K));
+    const int kk = k - done < K ? k - done : K;
+    const int norm = (d_norm != nullptr && done == 0) ? 1 : 0;
+    const int M = 2 * K + norm;
+    QCD_TRY(ensure_partials(c, (size_t)grid * M));
     VecList vl = make_list(v + done, kk);
+    const double2* w2 = (const double2*)w;
+#define MD(KK)                                                                                                   \
+  if (norm)                                                                                                      \
+    multidot_kernel<KK, 1><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, c->d_partials);                  \
+  else                                                                                                           \
+    multidot_kernel<KK, 0><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, c->d_partials);
     switch (K) {
-      case 4: multidot_kernel<4><<<grid, kBlasThreads, 0, s>>>(vl, kk, (const double2*)w, n, c->d_partials); break;
-      case 8: multidot_kernel<8><<<grid, kBlasThreads, 0, s>>>(vl, kk, (const double2*)w, n, c->d_partials); break;
-      case 16: multidot_kernel<16><<<grid, kBlasThreads, 0, s>>>(vl, kk, (const double2*)w, n, c->d_partials); break;
-      default: multidot_kernel<32><<<grid, kBlasThreads, 0, s>>>(vl, kk, (const double2*)w, n, c->d_partials); break;
+      case 4: MD(4); break;
+      case 8: MD(8); break;
+      case 16: MD(16); break;
+      default: MD(32); break;
     }
+#undef MD
     QCD_LAUNCHED();
-    QCD_TRY(reduce_partials(c->d_partials, (int)grid, 2 * K, 2 * kk, d_out + 2 * done, s));
+    QCD_TRY(reduce_partials(c->d_partials, (int)grid, M, 2 * kk, d_out + 2 * done, s));
+    if (norm) QCD_TRY(reduce_partials(c->d_partials + 2 * K, (int)grid, M, 1, d_norm, s));
     done += kk;
   }
   return QCD_OK;
@@ -243,7 +277,7 @@ int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, do
 
 template <int DOT>
 static int axpy_dot_impl(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w, const double* rho,
-                         double* d_out, cudaStream_t s) {
+                         double* d_out, cudaStream_t s, const double* cond = nullptr) {
   if (k > 32) return QCD_ERR_UNSUPPORTED;
   const long long n = c->V * 12;
   const unsigned grid = blas_grid(n);
@@ -255,10 +289,10 @@ static int axpy_dot_impl(qcd_ctx* c, const double* const* v, int k, const double
   VecList vl = make_list(v, k);
   const double2* r2 = (const double2*)rho;
   switch (K) {
-    case 4: axpy_dot_kernel<4, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, c->d_partials); break;
-    case 8: axpy_dot_kernel<8, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, c->d_partials); break;
-    case 16: axpy_dot_kernel<16, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, c->d_partials); break;
-    default: axpy_dot_kernel<32, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, c->d_partials); break;
+    case 4: axpy_dot_kernel<4, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, c->d_partials); break;
+    case 8: axpy_dot_kernel<8, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, c->d_partials); break;
+    case 16: axpy_dot_kernel<16, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, c->d_partials); break;
+    default: axpy_dot_kernel<32, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, c->d_partials); break;
   }
   QCD_LAUNCHED();
   return reduce_partials(c->d_partials, (int)grid, M, DOT == 1 ? 2 * k : 3, d_out, s);
@@ -271,7 +305,7 @@ int blas_axpy_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coe
 }
 
 int blas_axpy_norm_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w, const double* rho,
-                       double* d_out, cudaStream_t s) {
+                       double* d_out, cudaStream_t s, const double* cond) {
   if (k <= 0) {
     // nothing to subtract: only the norm and the dot
     const long long n = c->V * 12;
@@ -279,21 +313,23 @@ int blas_axpy_norm_dot(qcd_ctx* c, const double* const* v, int k, const double* 
     QCD_TRY(ensure_partials(c, (size_t)grid * 3));
     VecList vl = make_list(v, 0);
     ProfScope ps(c, QCD_KERNEL_BLAS, s, 32.0 * n, 8.0 * n);
-    axpy_dot_kernel<4, 2><<<grid, kBlasThreads, 0, s>>>(vl, 0, d_coef, (double2*)w, (const double2*)rho, n,
+    axpy_dot_kernel<4, 2><<<grid, kBlasThreads, 0, s>>>(vl, 0, d_coef, (double2*)w, (const double2*)rho, n, cond,
                                                         c->d_partials);
     QCD_LAUNCHED();
     return reduce_partials(c->d_partials, (int)grid, 3, 3, d_out, s);
   }
-  return axpy_dot_impl<2>(c, v, k, d_coef, w, rho, d_out, s);
+  return axpy_dot_impl<2>(c, v, k, d_coef, w, rho, d_out, s, cond);
 }
 
-int blas_normalise_update(qcd_ctx* c, double* chi, double* rho, const double* d_coefs, double* d_out, cudaStream_t s) {
+int blas_normalise_update(qcd_ctx* c, double* chi, double* rho, const double* d_gs, int two_pass, double* d_cr,
+                          double* d_out, cudaStream_t s) {
   const long long n = c->V * 12;
   const unsigned grid = blas_grid(n);
   QCD_TRY(ensure_partials(c, (size_t)grid));
   {
     ProfScope ps(c, QCD_KERNEL_BLAS, s, 64.0 * n, 8.0 * n);
-    normalise_update_kernel<<<grid, kBlasThreads, 0, s>>>((double2*)chi, (double2*)rho, d_coefs, n, c->d_partials);
+    normalise_update_kernel<<<grid, kBlasThreads, 0, s>>>((double2*)chi, (double2*)rho, d_gs, two_pass, d_cr, n,
+                                                          c->d_partials);
     QCD_LAUNCHED();
   }
   return reduce_partials(c->d_partials, (int)grid, 1, 1, d_out, s);

@@ -38,9 +38,9 @@ __device__ __forceinline__ M3 m3dag(const M3& a) {
 // link U_mu at global coordinates x + shift (periodic), from the FP64 copy
 __device__ __forceinline__ M3 link_at(const Geom& g, const double2* U64, const int x[4], int mu, int s0, int s1,
                                       int d0, int d1) {
-  int y[4] = {x[0], x[1], x[2], x[3]};
-  y[d0] = (y[d0] + s0 + g.L[d0]) % g.L[d0];
-  y[d1] = (y[d1] + s1 + g.L[d1]) % g.L[d1];
+  int y[4];  // selects only, no dynamically indexed writes
+#pragma unroll
+  for (int d = 0; d < 4; ++d) y[d] = (x[d] + (d == d0 ? s0 : 0) + (d == d1 ? s1 : 0) + g.L[d]) % g.L[d];
   long long s = internal_index(g, y);
   int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
   SU3<double> u = load_link<P64, double>(U64, g.Vb, blk, r, mu);

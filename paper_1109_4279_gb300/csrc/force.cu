@@ -82,10 +82,16 @@ __device__ __forceinline__ C3 link64(const Geom& g, const double2* U, long long 
   return o;
 }
 
+// internal index of x + s_mu mu-hat + s_nu nu-hat (periodic).  Written with
+// selects only: no dynamically indexed local arrays, whose copies the
+// compiler is free to place in overlapping stack slots.
 __device__ __forceinline__ long long shifted(const Geom& g, const int x[4], int mu, int smu, int nu, int snu) {
-  int y[4] = {x[0], x[1], x[2], x[3]};
-  y[mu] = (y[mu] + smu + g.L[mu]) % g.L[mu];
-  if (nu >= 0) y[nu] = (y[nu] + snu + g.L[nu]) % g.L[nu];
+  int y[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const int o = (d == mu ? smu : 0) + (d == nu ? snu : 0);
+    y[d] = (x[d] + o + g.L[d]) % g.L[d];
+  }
   return internal_index(g, y);
 }
 
@@ -201,7 +207,10 @@ __global__ void force_kernel(Geom g, const double2* __restrict__ U, FieldPtr xf,
   // ---- hopping part
   const long long sp = shifted(g, x, mu, 1, -1, 0);
   const int bp = (int)(sp / g.Vb), rp = (int)(sp - (long long)bp * g.Vb);
-  const double eta = (x[mu] == g.L[mu] - 1) ? g.bc[mu] : 1.0;
+  const int xmu = mu == 0 ? x[0] : (mu == 1 ? x[1] : (mu == 2 ? x[2] : x[3]));
+  const int Lmu = mu == 0 ? g.L[0] : (mu == 1 ? g.L[1] : (mu == 2 ? g.L[2] : g.L[3]));
+  const double bcmu = mu == 0 ? g.bc[0] : (mu == 1 ? g.bc[1] : (mu == 2 ? g.bc[2] : g.bc[3]));
+  const double eta = (xmu == Lmu - 1) ? bcmu : 1.0;
   Spinor<double> x_here = load_spinor<P64, double>(xf, g.Vb, blk, r);
   Spinor<double> y_here = load_spinor<P64, double>(yf, g.Vb, blk, r);
   Spinor<double> x_up = load_spinor<P64, double>(xf, g.Vb, bp, rp);

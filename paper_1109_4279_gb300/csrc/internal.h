@@ -77,6 +77,7 @@ struct Workspace {
   double* d_cr = nullptr;  // [nkv][3]: |chi_k|^2, (chi_k, rho_k)
   double* d_rn = nullptr;  // [nkv + 8] residual norms
   double* d_gam = nullptr; // [nkv] complex
+  double* d_gs = nullptr;  // [nkv][8] Gram-Schmidt norms and pass results
   double* h_pin = nullptr; // pinned host mirror for scalars read back
 };
 
@@ -154,17 +155,21 @@ int residual64(qcd_ctx* c, const Rec& b, const Rec& x, const Rec& r, double* d_n
 int sap_apply(qcd_ctx* c, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec, cudaStream_t s);
 
 // ---- blas.cu (FP64 fields of the context, 24 reals per site)
-// d_out[j] = (v_j, w) for j < k (complex, 2 doubles each)
-int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s);
-// w -= sum_j coef[j] v_j (coef on device, complex); then d_out[j] = (v_j, w) for j < k if d_out
+// Gram-Schmidt building blocks.  cond (optional) = {|chi|^2, |chi'|^2}: the
+// call is skipped unless |chi'|^2 < |chi|^2 / 2 (second pass, DGKS criterion).
+// d_out[j] = (v_j, w) for j < k (complex); d_norm (optional) = |w|^2
+int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s,
+                  const double* cond = nullptr, double* d_norm = nullptr);
+// w -= sum_j coef[j] v_j (coef on device, complex); then d_out[j] = (v_j, w) for j < k
 int blas_axpy_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w,
                   double* d_out, cudaStream_t s);
 // w -= sum_j coef[j] v_j; d_out = {|w|^2, (w, rho)}
 int blas_axpy_norm_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w,
-                       const double* rho, double* d_out, cudaStream_t s);
-// chi *= 1/|chi| (norm from d_in); rho -= c chi_normalised; d_out = |rho|^2
-int blas_normalise_update(qcd_ctx* c, double* chi, double* rho, const double* d_coefs, double* d_out,
-                          cudaStream_t s);
+                       const double* rho, double* d_out, cudaStream_t s, const double* cond = nullptr);
+// gs = {|chi|^2, pass-1 {|chi'|^2, (chi', rho)}, pass-2 {...}}: picks the final
+// coefficients into cr, chi /= |chi|, rho -= (chi, rho) chi, d_out = |rho|^2
+int blas_normalise_update(qcd_ctx* c, double* chi, double* rho, const double* d_gs, int two_pass, double* d_cr,
+                          double* d_out, cudaStream_t s);
 // x += sum_j gamma_j phi_j (gamma on device)
 int blas_multi_axpy(qcd_ctx* c, const double* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s);
 // norm2

@@ -519,3 +519,63 @@ __device__ __forceinline__ Spinor<T> clover_apply(const T* c72, const Spinor<T>&
 }
 
 }  // namespace qcd
+
+namespace qcd {
+
+// ------------------------------------------------------------------------
+// Runtime-direction form of the projection above, for kernels that loop over
+// mu instead of instantiating four copies (smaller code).  In the chiral
+// basis B psi_l has components ph_k psi_{sigma_k}: (sigma_0, sigma_1) = (2, 3)
+// or (3, 2) ("swap") and phases ph_k in {+-1, +-i}; the expansion puts
+// conj(ph_k) w_k on spin sigma_k.
+// ------------------------------------------------------------------------
+template <typename T>
+struct SpinDir {
+  bool swap;
+  cpx<T> ph0, ph1;
+};
+
+template <typename T>
+__device__ __forceinline__ SpinDir<T> spin_dir(int mu) {
+  SpinDir<T> d;
+  const T o = T(1), z = T(0);
+  switch (mu) {
+    case 0: d.swap = false; d.ph0 = {-o, z}; d.ph1 = {-o, z}; break;  // B = -1
+    case 1: d.swap = true; d.ph0 = {z, -o}; d.ph1 = {z, -o}; break;   // B = -i s1
+    case 2: d.swap = true; d.ph0 = {-o, z}; d.ph1 = {o, z}; break;    // B = -i s2
+    default: d.swap = false; d.ph0 = {z, -o}; d.ph1 = {z, o}; break;  // B = -i s3
+  }
+  return d;
+}
+
+// h = upper components of (1 + S g_mu) p
+template <int S, typename T>
+__device__ __forceinline__ Half<T> project_rt(const Spinor<T>& p, const SpinDir<T>& d) {
+  Half<T> h;
+  const cpx<T> a0 = {T(S) * d.ph0.re, T(S) * d.ph0.im}, a1 = {T(S) * d.ph1.re, T(S) * d.ph1.im};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cpx<T> l0 = d.swap ? p.c[3][c] : p.c[2][c];
+    const cpx<T> l1 = d.swap ? p.c[2][c] : p.c[3][c];
+    h.c[0][c] = cmadd(a0, l0, p.c[0][c]);
+    h.c[1][c] = cmadd(a1, l1, p.c[1][c]);
+  }
+  return h;
+}
+
+// acc += coef * [w ; S B^+ w]
+template <int S, typename T>
+__device__ __forceinline__ void expand_add_rt(Spinor<T>& acc, const Half<T>& w, T coef, const SpinDir<T>& d) {
+  const cpx<T> b0 = {T(S) * coef * d.ph0.re, -T(S) * coef * d.ph0.im};
+  const cpx<T> b1 = {T(S) * coef * d.ph1.re, -T(S) * coef * d.ph1.im};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc.c[0][c] = acc.c[0][c] + coef * w.c[0][c];
+    acc.c[1][c] = acc.c[1][c] + coef * w.c[1][c];
+    const cpx<T> l0 = cmul(b0, w.c[0][c]), l1 = cmul(b1, w.c[1][c]);
+    acc.c[2][c] = acc.c[2][c] + (d.swap ? l1 : l0);
+    acc.c[3][c] = acc.c[3][c] + (d.swap ? l0 : l1);
+  }
+}
+
+}  // namespace qcd

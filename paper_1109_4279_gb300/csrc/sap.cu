@@ -4,9 +4,15 @@
 // Table 1: even/odd preconditioning inside the block solver).
 //
 // One launch = one colour half-sweep: one CTA per block of that colour, one
-// thread per (even site, odd site) pair.  The block's links, clover blocks and
-// residual are staged in shared memory, so the n_mr MR steps never touch HBM
-// (Sec. 4: "all the data necessary for a block solve fit the local store").
+// thread per (even site, odd site) pair.  The block's links and clover blocks
+// are staged in shared memory, so the n_mr MR steps never touch HBM (Sec. 4:
+// "all the data necessary for a block solve fit the local store").  With
+// 16-bit block fields the staged copy keeps the storage format (two link rows,
+// scaled clover halves) and is brought in by bulk (TMA) copies of the block's
+// contiguous ranges; the third link row and the scales are applied on use.
+// This halves the shared-memory footprint (two CTAs per SM) and the
+// shared-memory bytes per hop.  FP32 and FP64 block fields are expanded to
+// full matrices at stage-in.
 //
 // Residual update on the neighbouring blocks (Sec. 4: "the residue is then
 // updated ... on the internal border of the black blocks") goes through face
@@ -40,6 +46,7 @@ struct SapArgs {
   void* faces;          // [blk][NCF chunks][F] face data
   int F;                // face sites per block
   int fo[8];            // offset of face 2 mu + dir inside a block's face list
+  int* err;             // set to 1 if a staging wait timed out
 };
 
 template <typename T>
@@ -106,26 +113,137 @@ __device__ __forceinline__ Half<T> face_load(const SapArgs& a, int blk, int f, i
   return h;
 }
 
-// shared-memory block fields, SoA so that consecutive threads hit consecutive banks
+// ------------------------------------------------------------------------
+// Shared-memory copies of a block's links and clover blocks
+// ------------------------------------------------------------------------
+
+// FP32 / FP64: full matrices, SoA ([mu][18][Vb] links, [72][Vb] clover)
 template <typename T>
-struct Smem {
-  T* U;     // [4 mu][18][Vb]
-  T* A;     // [72][Vb]
-  T* r;     // [24][Vbh] even-site MR residual
-  T* t;     // [24][Vbh] odd-site temporary
-  T* rho_o; // [24][Vbh] odd-site source
-  T* red;   // reduction scratch
+struct ExpandedStage {
+  T* U;
+  T* A;
+  int Vb;
+  static constexpr size_t bytes(int Vb) { return sizeof(T) * (size_t)(4 * 18 + 72) * Vb; }
+  __device__ __forceinline__ SU3<T> link(int r, int mu) const {
+    SU3<T> u;
+    const T* p = U + (mu * 18) * Vb + r;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u.m[k / 3][k % 3] = {p[(2 * k) * Vb], p[(2 * k + 1) * Vb]};
+    return u;
+  }
+  __device__ __forceinline__ Spinor<T> clover(int r, const Spinor<T>& in) const {
+    T c[72];
+#pragma unroll
+    for (int k = 0; k < 72; ++k) c[k] = A[k * Vb + r];
+    return clover_apply(c, in);
+  }
 };
 
-template <typename T>
-__device__ __forceinline__ SU3<T> s_link(const Smem<T>& sm, int Vb, int r, int mu) {
-  SU3<T> u;
-  const T* p = sm.U + (long long)mu * 18 * Vb + r;
+// 16-bit: the storage format itself -- links [4 mu][Vb] uint4 + [4 mu][Vb]
+// uint2 (rows 0-1), clover [9][Vb] uint4 (scaled halves) + [Vb] float scales
+template <int P>
+struct HalfStage {
+  const unsigned char* base;
+  int Vb;
+  typedef typename Storage<P>::real hr;
+  static constexpr size_t bytes(int Vb) { return (size_t)(96 + 144 + 4) * Vb; }
+  __device__ __forceinline__ SU3<float> link(int r, int mu) const {
+    const uint4 a = ((const uint4*)base)[mu * Vb + r];
+    const uint2 b = ((const uint2*)(base + 64 * Vb))[mu * Vb + r];
+    const hr* ha = reinterpret_cast<const hr*>(&a);
+    const hr* hb = reinterpret_cast<const hr*>(&b);
+    SU3<float> u;
+    u.m[0][0] = {to_f<P>(ha[0]), to_f<P>(ha[1])};
+    u.m[0][1] = {to_f<P>(ha[2]), to_f<P>(ha[3])};
+    u.m[0][2] = {to_f<P>(ha[4]), to_f<P>(ha[5])};
+    u.m[1][0] = {to_f<P>(ha[6]), to_f<P>(ha[7])};
+    u.m[1][1] = {to_f<P>(hb[0]), to_f<P>(hb[1])};
+    u.m[1][2] = {to_f<P>(hb[2]), to_f<P>(hb[3])};
+    reconstruct(u);
+    return u;
+  }
+  __device__ __forceinline__ Spinor<float> clover(int r, const Spinor<float>& in) const {
+    const uint4* A = (const uint4*)(base + 96 * Vb);
+    float c[72];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) u.m[k / 3][k % 3] = {p[(2 * k) * Vb], p[(2 * k + 1) * Vb]};
-  return u;
+    for (int k = 0; k < 9; ++k) {
+      const uint4 v = A[k * Vb + r];
+      const hr* h = reinterpret_cast<const hr*>(&v);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) c[8 * k + e] = to_f<P>(h[e]);
+    }
+    Spinor<float> o = clover_apply(c, in);
+    const float s = ((const float*)(base + 240 * Vb))[r];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) o.c[a][b] = s * o.c[a][b];
+    return o;
+  }
+};
+
+// ------------------------------------------------------------------------
+// bulk copy global -> shared with an mbarrier (TMA, non-tensor form)
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(b))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// wait for phase 0 of the barrier for at most ~2^31 cycles (about a second)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, 0)) {
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  return true;
+}
+
+// issue the bulk copies of a block's 16-bit links and clover (thread 0 only)
+template <int P>
+__device__ __forceinline__ void stage_issue(const SapArgs& a, int blk, unsigned char* dst, uint64_t* bar) {
+  const int Vb = a.g.Vb;
+  const unsigned char* srcs[3] = {(const unsigned char*)a.U + (size_t)blk * 96 * Vb,
+                                  (const unsigned char*)a.Ahat.data + (size_t)blk * 144 * Vb,
+                                  (const unsigned char*)(a.Ahat.norm + (size_t)blk * Vb)};
+  const uint32_t sizes[3] = {(uint32_t)(96 * Vb), (uint32_t)(144 * Vb), (uint32_t)(4 * Vb)};
+  mbar_expect_tx(bar, sizes[0] + sizes[1] + sizes[2]);
+  size_t off = 0;
+  for (int k = 0; k < 3; ++k) {
+    for (uint32_t o = 0; o < sizes[k]; o += 16384) {
+      const uint32_t n = sizes[k] - o < 16384 ? sizes[k] - o : 16384;
+      bulk_copy_g2s(dst + off + o, srcs[k] + o, n, bar);
+    }
+    off += sizes[k];
+  }
+}
+
+// ------------------------------------------------------------------------
+// block operator pieces
+// ------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ Spinor<T> s_spinor(const T* base, int n, int i) {
   Spinor<T> s;
@@ -147,45 +265,34 @@ __device__ __forceinline__ void s_spinor_store(T* base, int n, int i, const Spin
     }
 }
 
-template <typename T>
-__device__ __forceinline__ Spinor<T> s_clover(const Smem<T>& sm, int Vb, int r, const Spinor<T>& p) {
-  T c[72];
-#pragma unroll
-  for (int k = 0; k < 72; ++k) c[k] = sm.A[k * Vb + r];
-  return clover_apply(c, p);
+// neighbour indices of one site packed two per int (16 bits each, 0xffff = outside)
+__device__ __forceinline__ int nb_get(const int* pk, int k) {
+  const int v = (pk[k >> 1] >> (16 * (k & 1))) & 0xffff;
+  return v == 0xffff ? -1 : v;
 }
 
 // hops of D restricted to the block (Dirichlet: hops that leave the block are
-// dropped) evaluated at site r from a field living on the opposite parity:
-// returns -1/2 sum_mu [U_mu(r)(1 - g) v(r + mu) + U_mu(r - mu)^+ (1 + g) v(r - mu)]
-// nb[2 mu + 0/1]: forward/backward neighbour's index into `src` (-1 if outside),
-// nr[2 mu + 1]: backward neighbour's site index r (for its link)
-template <int MU, typename T>
-__device__ __forceinline__ void block_hop(const Smem<T>& sm, int Vb, int n, int r, const T* src, const int* nb,
-                                          const int* nr, Spinor<T>& acc) {
-  if (nb[2 * MU] >= 0) {
-    Spinor<T> p = s_spinor(src, n, nb[2 * MU]);
-    Half<T> h = project<MU, -1>(p);
-    Half<T> w = umul(s_link(sm, Vb, r, MU), h);
-    expand_add<MU, -1>(acc, w, T(1));
-  }
-  if (nb[2 * MU + 1] >= 0) {
-    Spinor<T> p = s_spinor(src, n, nb[2 * MU + 1]);
-    Half<T> h = project<MU, +1>(p);
-    Half<T> w = udmul(s_link(sm, Vb, nr[2 * MU + 1], MU), h);
-    expand_add<MU, +1>(acc, w, T(1));
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ Spinor<T> hops(const Smem<T>& sm, int Vb, int n, int r, const T* src, const int* nb,
-                                          const int* nr) {
+// dropped) at site r from a field v on the opposite parity stored at
+// src[index], index = neighbour site - off:
+//   -1/2 sum_mu [U_mu(r)(1 - g) v(r + mu) + U_mu(r - mu)^+ (1 + g) v(r - mu)]
+// One loop over mu (runtime spin phases): a single copy of the hop code.
+template <typename T, typename ST>
+__device__ __forceinline__ Spinor<T> hops(const ST& st, int n, int r, const T* src, const int* pk, int off) {
   Spinor<T> acc;
   zero(acc);
-  block_hop<0, T>(sm, Vb, n, r, src, nb, nr, acc);
-  block_hop<1, T>(sm, Vb, n, r, src, nb, nr, acc);
-  block_hop<2, T>(sm, Vb, n, r, src, nb, nr, acc);
-  block_hop<3, T>(sm, Vb, n, r, src, nb, nr, acc);
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    const SpinDir<T> d = spin_dir<T>(mu);
+    const int kf = nb_get(pk, 2 * mu), kb = nb_get(pk, 2 * mu + 1);
+    if (kf >= 0) {
+      const Half<T> h = project_rt<-1>(s_spinor(src, n, kf), d);
+      expand_add_rt<-1>(acc, umul(st.link(r, mu), h), T(1), d);
+    }
+    if (kb >= 0) {
+      const Half<T> h = project_rt<+1>(s_spinor(src, n, kb), d);
+      expand_add_rt<+1>(acc, udmul(st.link(kb + off, mu), h), T(1), d);
+    }
+  }
 #pragma unroll
   for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -237,61 +344,93 @@ struct PsiPrec<P64> {
 };
 
 // receive the face contributions of the other colour at site (blk, r)
-template <typename T>
-__device__ __forceinline__ void receive_faces(const SapArgs& a, const Smem<T>& sm, int blk, int r, const int y[4],
+template <typename T, typename ST>
+__device__ __forceinline__ void receive_faces(const SapArgs& a, const ST& st, int blk, int r, const int y[4],
                                               const int n[4], Spinor<T>& rho) {
   const Geom& g = a.g;
-#define RECV(MU)                                                                             \
-  if (y[MU] == g.b[MU] - 1) {                                                                \
-    int nbk = n[MU] + 1 < g.nb[MU] ? blk + g.bstr[MU] : blk - (g.nb[MU] - 1) * g.bstr[MU];   \
-    Half<T> h = face_load<T>(a, nbk, 2 * MU, face_index(g, y, MU));                          \
-    expand_add<MU, -1>(rho, umul(s_link(sm, g.Vb, r, MU), h), T(1));                         \
-  }                                                                                          \
-  if (y[MU] == 0) {                                                                          \
-    int nbk = n[MU] > 0 ? blk - g.bstr[MU] : blk + (g.nb[MU] - 1) * g.bstr[MU];              \
-    Half<T> w = face_load<T>(a, nbk, 2 * MU + 1, face_index(g, y, MU));                      \
-    expand_add<MU, +1>(rho, w, T(1));                                                        \
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    const SpinDir<T> d = spin_dir<T>(mu);
+    if (y[mu] == g.b[mu] - 1) {  // from block + mu: U_mu(y) (1 - g) part, projected by the sender
+      const int nbk = n[mu] + 1 < g.nb[mu] ? blk + g.bstr[mu] : blk - (g.nb[mu] - 1) * g.bstr[mu];
+      const Half<T> h = face_load<T>(a, nbk, 2 * mu, face_index(g, y, mu));
+      expand_add_rt<-1>(rho, umul(st.link(r, mu), h), T(1), d);
+    }
+    if (y[mu] == 0) {  // from block - mu: U^+ (1 + g) part, multiplied by the sender
+      const int nbk = n[mu] > 0 ? blk - g.bstr[mu] : blk + (g.nb[mu] - 1) * g.bstr[mu];
+      const Half<T> w = face_load<T>(a, nbk, 2 * mu + 1, face_index(g, y, mu));
+      expand_add_rt<+1>(rho, w, T(1), d);
+    }
   }
-  RECV(0) RECV(1) RECV(2) RECV(3)
-#undef RECV
 }
 
 // write the face contributions of the correction chi at site (blk, r)
-template <typename T>
-__device__ __forceinline__ void send_faces(const SapArgs& a, const Smem<T>& sm, int blk, int r, const int y[4],
+template <typename T, typename ST>
+__device__ __forceinline__ void send_faces(const SapArgs& a, const ST& st, int blk, int r, const int y[4],
                                            const int n[4], const Spinor<T>& chi) {
   const Geom& g = a.g;
-#define SEND(MU)                                                                                  \
-  if (y[MU] == 0) { /* to y = x - mu: 1/2 eta_mu(y) (1 - g) chi, projected */                     \
-    const T eta = (n[MU] == 0) ? (T)g.bc[MU] : T(1);                                              \
-    Half<T> h = project<MU, -1>(chi);                                                             \
-    _Pragma("unroll") for (int s = 0; s < 2; ++s)                                                 \
-      _Pragma("unroll") for (int c = 0; c < 3; ++c) h.c[s][c] = (T(0.5) * eta) * h.c[s][c];       \
-    face_store<T>(a, blk, 2 * MU, face_index(g, y, MU), h);                                       \
-  }                                                                                               \
-  if (y[MU] == g.b[MU] - 1) { /* to y = x + mu: 1/2 eta_mu(x) U_mu(x)^+ (1 + g) chi, projected */ \
-    const T eta = (n[MU] == g.nb[MU] - 1) ? (T)g.bc[MU] : T(1);                                   \
-    Half<T> w = udmul(s_link(sm, g.Vb, r, MU), project<MU, +1>(chi));                             \
-    _Pragma("unroll") for (int s = 0; s < 2; ++s)                                                 \
-      _Pragma("unroll") for (int c = 0; c < 3; ++c) w.c[s][c] = (T(0.5) * eta) * w.c[s][c];       \
-    face_store<T>(a, blk, 2 * MU + 1, face_index(g, y, MU), w);                                   \
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    const SpinDir<T> d = spin_dir<T>(mu);
+    if (y[mu] == 0) {  // to y = x - mu: 1/2 eta_mu(y) (1 - g) chi, projected
+      const T f = T(0.5) * ((n[mu] == 0) ? (T)g.bc[mu] : T(1));
+      Half<T> h = project_rt<-1>(chi, d);
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) h.c[s][c] = f * h.c[s][c];
+      face_store<T>(a, blk, 2 * mu, face_index(g, y, mu), h);
+    }
+    if (y[mu] == g.b[mu] - 1) {  // to y = x + mu: 1/2 eta_mu(x) U_mu(x)^+ (1 + g) chi, projected
+      const T f = T(0.5) * ((n[mu] == g.nb[mu] - 1) ? (T)g.bc[mu] : T(1));
+      Half<T> w = udmul(st.link(r, mu), project_rt<+1>(chi, d));
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w.c[s][c] = f * w.c[s][c];
+      face_store<T>(a, blk, 2 * mu + 1, face_index(g, y, mu), w);
+    }
   }
-  SEND(0) SEND(1) SEND(2) SEND(3)
-#undef SEND
 }
+
+template <int P>
+struct StageFor {
+  typedef HalfStage<P> type;
+};
+template <>
+struct StageFor<P32> {
+  typedef ExpandedStage<float> type;
+};
+template <>
+struct StageFor<P64> {
+  typedef ExpandedStage<double> type;
+};
 
 template <int P, typename T>
 __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typedef typename StageFor<P>::type ST;
+  constexpr bool kHalf = (P == P16 || P == PB16);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const Geom& g = a.g;
   const int Vb = g.Vb, Vbh = g.Vbh;
-  Smem<T> sm;
-  sm.U = (T*)smem_raw;
-  sm.A = sm.U + 4 * 18 * Vb;
-  sm.r = sm.A + 72 * Vb;
-  sm.t = sm.r + 24 * Vbh;
-  sm.rho_o = sm.t + 24 * Vbh;
-  sm.red = sm.rho_o + 24 * Vbh;
+
+  // shared memory: staged block fields, then the FP vectors r (even), t (odd),
+  // rho_o (odd source), the reduction scratch and the staging barrier
+  ST st;
+  const size_t stage_bytes = ST::bytes(Vb);
+  if constexpr (kHalf) {
+    st.base = smem_raw;
+    st.Vb = Vb;
+  } else {
+    st.U = (T*)smem_raw;
+    st.A = st.U + 4 * 18 * Vb;
+    st.Vb = Vb;
+  }
+  T* s_r = (T*)(smem_raw + stage_bytes);
+  T* s_t = s_r + 24 * Vbh;
+  T* s_rho_o = s_t + 24 * Vbh;
+  T* s_red = s_rho_o + 24 * Vbh;
+  uint64_t* bar = (uint64_t*)(s_red + 3 * 32);
 
   // block of the requested colour: pairs (2k, 2k+1) differ in n3 only, hence in colour
   int blk = 2 * blockIdx.x;
@@ -301,31 +440,39 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
     ++blk;
     ++n[3];
   }
+
+  // ---- stage the block's links and clover
+  if constexpr (kHalf) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      stage_issue<P>(a, blk, smem_raw, bar);
+    }
+  } else {
+    for (int r = threadIdx.x; r < Vb; r += blockDim.x) {
+#pragma unroll 1
+      for (int mu = 0; mu < 4; ++mu) {
+        SU3<T> u = load_link<P, T>(a.U, Vb, blk, r, mu);
+        T* p = st.U + (mu * 18) * Vb + r;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          p[(2 * k) * Vb] = u.m[k / 3][k % 3].re;
+          p[(2 * k + 1) * Vb] = u.m[k / 3][k % 3].im;
+        }
+      }
+      T c[72];
+      load_record<P, 72, T>(a.Ahat, Vb, blk, r, c);
+#pragma unroll
+      for (int k = 0; k < 72; ++k) st.A[k * Vb + r] = c[k];
+    }
+  }
+
   // thread i owns even site i and odd site Vbh + i; threads i >= Vbh (only
   // when a block has fewer than 64 sites) take part in barriers and sums only
   const int i = threadIdx.x;
   const bool act = i < Vbh;
   const int re = act ? i : 0, ro = act ? Vbh + i : Vbh;
 
-  // ---- stage links and clover of the block in shared memory
-  for (int r = i; r < Vb; r += blockDim.x) {
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      SU3<T> u = load_link<P, T>(a.U, Vb, blk, r, mu);
-      T* p = sm.U + (long long)mu * 18 * Vb + r;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        p[(2 * k) * Vb] = u.m[k / 3][k % 3].re;
-        p[(2 * k + 1) * Vb] = u.m[k / 3][k % 3].im;
-      }
-    }
-    T c[72];
-    load_record<P, 72, T>(a.Ahat, Vb, blk, r, c);
-#pragma unroll
-    for (int k = 0; k < 72; ++k) sm.A[k * Vb + r] = c[k];
-  }
-
-  // ---- in-block neighbour tables of the two owned sites
+  // ---- in-block neighbour tables of the two owned sites (while the copies fly)
   int ye[4], yo[4];
   {
     const int pe = __ldg(g.r2y + re), po = __ldg(g.r2y + ro);
@@ -335,27 +482,23 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
       yo[mu] = ycoord(po, mu);
     }
   }
-  // even site: nbe = index into the odd vector t, nre = site index (links);
-  // odd site: nbo = index into the even vector r (= site index)
-  int nbe[8], nre[8], nbo[8];
+  // even site: indices into the odd vector t (site - Vbh); odd site: into r (= site)
+  int pke[4], pko[4];
   {
     const int je = ye[0] * g.ystr[0] + ye[1] * g.ystr[1] + ye[2] * g.ystr[2] + ye[3] * g.ystr[3];
     const int jo = yo[0] * g.ystr[0] + yo[1] * g.ystr[1] + yo[2] * g.ystr[2] + yo[3] * g.ystr[3];
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-      int f = ye[mu] + 1 < g.b[mu] ? __ldg(g.j2r + je + g.ystr[mu]) : -1;
-      int b = ye[mu] > 0 ? __ldg(g.j2r + je - g.ystr[mu]) : -1;
-      nbe[2 * mu] = f >= 0 ? f - Vbh : -1;
-      nbe[2 * mu + 1] = b >= 0 ? b - Vbh : -1;
-      nre[2 * mu] = f;
-      nre[2 * mu + 1] = b;
-      nbo[2 * mu] = yo[mu] + 1 < g.b[mu] ? __ldg(g.j2r + jo + g.ystr[mu]) : -1;
-      nbo[2 * mu + 1] = yo[mu] > 0 ? __ldg(g.j2r + jo - g.ystr[mu]) : -1;
+      const int ef = ye[mu] + 1 < g.b[mu] ? __ldg(g.j2r + je + g.ystr[mu]) - Vbh : 0xffff;
+      const int eb = ye[mu] > 0 ? __ldg(g.j2r + je - g.ystr[mu]) - Vbh : 0xffff;
+      const int of = yo[mu] + 1 < g.b[mu] ? __ldg(g.j2r + jo + g.ystr[mu]) : 0xffff;
+      const int ob = yo[mu] > 0 ? __ldg(g.j2r + jo - g.ystr[mu]) : 0xffff;
+      pke[mu] = ef | (eb << 16);
+      pko[mu] = of | (ob << 16);
     }
   }
-  __syncthreads();
 
-  // ---- residual of the two sites (+ incoming faces)
+  // ---- residual of the two sites
   Spinor<T> rho_e, rho_o;
   zero(rho_e);
   zero(rho_o);
@@ -375,56 +518,77 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
       rho_e = load_spinor<P, T>(a.rho, Vb, blk, re);
       rho_o = load_spinor<P, T>(a.rho, Vb, blk, ro);
     }
-    if (a.faces_in) {
-      receive_faces<T>(a, sm, blk, re, ye, n, rho_e);
-      receive_faces<T>(a, sm, blk, ro, yo, n, rho_o);
+  }
+  if constexpr (kHalf) {
+    // every thread waits (bounded) for the staging copies; a time-out is made
+    // block-uniform, recorded, and the block is skipped
+    const bool ok = mbar_wait_bounded(bar);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(a.err, 1);
+      mbar_wait_bounded(bar);  // let copies still in flight land before the CTA exits
+      return;
     }
-    s_spinor_store(sm.rho_o, Vbh, i, rho_o);
+  } else {
+    __syncthreads();
+  }
+  if (act) {
+    if (a.faces_in) {
+      receive_faces<T>(a, st, blk, re, ye, n, rho_e);
+      receive_faces<T>(a, st, blk, ro, yo, n, rho_o);
+    }
+    s_spinor_store(s_rho_o, Vbh, i, rho_o);
     // etahat = rho_e - D_eo A_oo^-1 rho_o: first t = A_oo^-1 rho_o
-    s_spinor_store(sm.t, Vbh, i, s_clover(sm, Vb, ro, rho_o));
+    s_spinor_store(s_t, Vbh, i, st.clover(ro, rho_o));
   }
   __syncthreads();
   Spinor<T> r, x;
   zero(r);
   zero(x);
   if (act) {
-    Spinor<T> q = hops(sm, Vb, Vbh, re, sm.t, nbe, nre);
+    const Spinor<T> q = hops<T>(st, Vbh, re, s_t, pke, Vbh);
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int c = 0; c < 3; ++c) r.c[s][c] = rho_e.c[s][c] - q.c[s][c];
-    s_spinor_store(sm.r, Vbh, i, r);
+    s_spinor_store(s_r, Vbh, i, r);
   }
   __syncthreads();
 
-  // ---- MR on Dhat = A_ee - D_eo A_oo^-1 D_oe, x_e = 0, r = etahat
-  for (int it = 0; it < a.nmr; ++it) {
-    // odd site: t = A_oo^-1 D_oe r
-    if (act) {
-      Spinor<T> u = hops(sm, Vb, Vbh, ro, sm.r, nbo, nbo);
-      s_spinor_store(sm.t, Vbh, i, s_clover(sm, Vb, ro, u));
-    }
-    __syncthreads();
-    // even site: p = A_ee r - D_eo t; alpha = (p, r) / (p, p)
-    T pr_re = 0, pr_im = 0, pp = 0;
+  // ---- MR on Dhat = A_ee - D_eo A_oo^-1 D_oe, x_e = 0, r = etahat.  Each
+  // step runs two phases through one code path: phase 0 (odd sites)
+  // t = A_oo^-1 D_oe r, phase 1 (even sites) p = A_ee r - D_eo t.
+#pragma unroll 1
+  for (int step = 0; step < 2 * a.nmr; ++step) {
+    const int ph = step & 1;
     Spinor<T> p;
     zero(p);
     if (act) {
-      p = s_clover(sm, Vb, re, r);
-      Spinor<T> q = hops(sm, Vb, Vbh, re, sm.t, nbe, nre);
+      const Spinor<T> hq = ph ? hops<T>(st, Vbh, re, s_t, pke, Vbh) : hops<T>(st, Vbh, ro, s_r, pko, 0);
+      const Spinor<T> cl = st.clover(ph ? re : ro, ph ? r : hq);
+      if (ph == 0) {
+        s_spinor_store(s_t, Vbh, i, cl);
+      } else {
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+        for (int s = 0; s < 4; ++s)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          cpx<T> v = p.c[s][c] - q.c[s][c];
-          p.c[s][c] = v;
-          cpx<T> w = r.c[s][c];
-          pr_re += v.re * w.re + v.im * w.im;
-          pr_im += v.re * w.im - v.im * w.re;
-          pp += v.re * v.re + v.im * v.im;
-        }
+          for (int c = 0; c < 3; ++c) p.c[s][c] = cl.c[s][c] - hq.c[s][c];
+      }
     }
-    cta_sum3(pr_re, pr_im, pp, sm.red);
+    if (ph == 0) {
+      __syncthreads();
+      continue;
+    }
+    T pr_re = 0, pr_im = 0, pp = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const cpx<T> v = p.c[s][c], w = r.c[s][c];
+        pr_re += v.re * w.re + v.im * w.im;
+        pr_im += v.re * w.im - v.im * w.re;
+        pp += v.re * v.re + v.im * v.im;
+      }
+    cta_sum3(pr_re, pr_im, pp, s_red);
     const T inv = pp > T(0) ? T(1) / pp : T(0);
     const cpx<T> alpha = {pr_re * inv, pr_im * inv};
     if (act) {
@@ -435,29 +599,30 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
           x.c[s][c] = cmadd(alpha, r.c[s][c], x.c[s][c]);
           r.c[s][c] = r.c[s][c] - cmul(alpha, p.c[s][c]);
         }
-      s_spinor_store(sm.r, Vbh, i, r);
+      s_spinor_store(s_r, Vbh, i, r);
     }
     __syncthreads();
   }
 
   // ---- chi_o = A_oo^-1 (rho_o - D_oe chi_e)
-  if (act) s_spinor_store(sm.r, Vbh, i, x);
+  if (act) s_spinor_store(s_r, Vbh, i, x);
   __syncthreads();
   if (!act) return;
   Spinor<T> chi_o;
   {
-    Spinor<T> u = hops(sm, Vb, Vbh, ro, sm.r, nbo, nbo);
-    Spinor<T> src = s_spinor(sm.rho_o, Vbh, i);
+    Spinor<T> u = hops<T>(st, Vbh, ro, s_r, pko, 0);
+    const Spinor<T> src = s_spinor(s_rho_o, Vbh, i);
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
       for (int c = 0; c < 3; ++c) u.c[s][c] = src.c[s][c] - u.c[s][c];
-    chi_o = s_clover(sm, Vb, ro, u);
+    chi_o = st.clover(ro, u);
   }
 
   // ---- outputs: solution, block residual (r on even, 0 on odd), faces
   constexpr int PS = PsiPrec<P>::value;
   typedef typename std::conditional<PS == P64, double, float>::type TS;
+#pragma unroll 1
   for (int half = 0; half < 2; ++half) {
     const int rs = half ? ro : re;
     const Spinor<T>& chi = half ? chi_o : x;
@@ -473,12 +638,12 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
     if (a.psi_mode <= 1) {
       store_spinor<PS, TS>(a.psi, Vb, blk, rs, v);
     } else {
-      Spinor<double> d;
+      Spinor<double> dv;
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) d.c[s][c] = {(double)v.c[s][c].re, (double)v.c[s][c].im};
-      store_spinor<P64, double>(a.out, Vb, blk, rs, d);
+        for (int c = 0; c < 3; ++c) dv.c[s][c] = {(double)v.c[s][c].re, (double)v.c[s][c].im};
+      store_spinor<P64, double>(a.out, Vb, blk, rs, dv);
     }
   }
   if (a.write_rho) {
@@ -488,18 +653,28 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
     store_spinor<P, T>(a.rho, Vb, blk, ro, z);
   }
   if (a.faces_out) {
-    send_faces<T>(a, sm, blk, re, ye, n, x);
-    send_faces<T>(a, sm, blk, ro, yo, n, chi_o);
+    send_faces<T>(a, st, blk, re, ye, n, x);
+    send_faces<T>(a, st, blk, ro, yo, n, chi_o);
   }
 }
 
-template <typename T>
+template <int P, typename T>
 static size_t sap_smem_bytes(const Geom& g) {
-  return sizeof(T) * ((size_t)4 * 18 * g.Vb + 72 * (size_t)g.Vb + 3 * 24 * (size_t)g.Vbh + 3 * 32);
+  typedef typename StageFor<P>::type ST;
+  return ST::bytes(g.Vb) + sizeof(T) * (3 * 24 * (size_t)g.Vbh + 3 * 32) + 16;
+}
+
+template <int P, typename T>
+static int launch_sweep(const SapArgs& a, unsigned grid, int threads, cudaStream_t s, int maxsm) {
+  const size_t smem = sap_smem_bytes<P, T>(a.g);
+  if (smem > (size_t)maxsm) return QCD_ERR_UNSUPPORTED;
+  QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sap_sweep_kernel<P, T><<<grid, threads, smem, s>>>(a);
+  return QCD_OK;
 }
 
 static int sap_apply_impl(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec,
-                   cudaStream_t s) {
+                          cudaStream_t s) {
   const Geom& g = c->g;
   if (eta64.prec != P64 || psi64.prec != P64) return QCD_ERR_ARG;
   if (ncy < 1 || nmr < 0) return QCD_ERR_ARG;
@@ -507,11 +682,9 @@ static int sap_apply_impl(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& p
   QCD_TRY(ensure_gauge(c, prec, s));
   QCD_TRY(ensure_clover(c, prec, s));
   const bool dbl = prec == P64;
-  const size_t smem = dbl ? sap_smem_bytes<double>(g) : sap_smem_bytes<float>(g);
   int dev = 0, maxsm = 0;
   QCD_CUDA(cudaGetDevice(&dev));
   QCD_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem > (size_t)maxsm) return QCD_ERR_UNSUPPORTED;
   // work fields
   if (w.prec != prec) {
     rec_free(w.rho);
@@ -539,6 +712,7 @@ static int sap_apply_impl(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& p
   a.psi = w.psi.ptr();
   a.out = psi64.ptr();
   a.faces = w.faces;
+  a.err = (int*)(c->d_scalars + 128);
   int off = 0;
   for (int mu = 0; mu < 4; ++mu) {
     a.fo[2 * mu] = off;
@@ -549,8 +723,9 @@ static int sap_apply_impl(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& p
   a.F = off;
   const unsigned grid = (unsigned)(c->nblk / 2);
   const int threads = g.Vbh < 32 ? 32 : ((g.Vbh + 31) / 32) * 32;
-  // flops: per site and MR step the Schur operator costs about one D (1824),
-  // plus the source/back-substitution (about one more D) per sweep
+  // flops (the 1320 + 504 convention): per solved site the Schur operator
+  // costs about one D per MR step, plus about one more D for the source and
+  // the back-substitution
   const double flops = (double)(nmr + 1) * 1824.0 * (double)c->V / 2.0;
   const double sb = dbl ? 8 : (prec == P32 ? 4 : 2);
   const double bytes = (double)c->V / 2 * (4 * (dbl ? 18 : 12) * sb + 72 * sb + 2 * 24 * sb + 2 * 24 * (dbl ? 8 : 4));
@@ -565,30 +740,15 @@ static int sap_apply_impl(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& p
       a.write_rho = !last;
       a.psi_mode = last ? (cy == 0 ? 2 : 3) : (cy == 0 ? 0 : 1);
       ProfScope ps(c, QCD_KERNEL_SAP, s, bytes, flops);
-      if (dbl) {
-        QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        sap_sweep_kernel<P64, double><<<grid, threads, smem, s>>>(a);
-      } else {
-        switch (prec) {
-          case P32:
-            QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P32, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            sap_sweep_kernel<P32, float><<<grid, threads, smem, s>>>(a);
-            break;
-          case P16:
-            QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            sap_sweep_kernel<P16, float><<<grid, threads, smem, s>>>(a);
-            break;
-          case PB16:
-            QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<PB16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            sap_sweep_kernel<PB16, float><<<grid, threads, smem, s>>>(a);
-            break;
-          default: return QCD_ERR_ARG;
-        }
+      int st;
+      switch (prec) {
+        case P64: st = launch_sweep<P64, double>(a, grid, threads, s, maxsm); break;
+        case P32: st = launch_sweep<P32, float>(a, grid, threads, s, maxsm); break;
+        case P16: st = launch_sweep<P16, float>(a, grid, threads, s, maxsm); break;
+        case PB16: st = launch_sweep<PB16, float>(a, grid, threads, s, maxsm); break;
+        default: return QCD_ERR_ARG;
       }
+      if (st != QCD_OK) return st;
       QCD_LAUNCHED();
     }
   return QCD_OK;

@@ -5,7 +5,8 @@
 //
 // Iteration k of a cycle (rho_0 = r = b - D x):
 //   phi_k = M_SAP rho_k;  chi_k = D phi_k;
-//   chi_k -= sum_j a_jk chi_j   (classical Gram-Schmidt, applied twice);
+//   chi_k -= sum_j a_jk chi_j   (classical Gram-Schmidt; a second pass when
+//                                the first cancelled more than half the norm);
 //   chi_k /= |chi_k|;  c_k = (chi_k, rho_k);  rho_{k+1} = rho_k - c_k chi_k.
 // At the end of a cycle the upper-triangular system H gamma = c is solved on
 // the device, x += sum_k gamma_k phi_k, and r = b - D x is recomputed in FP64
@@ -33,12 +34,14 @@ static int ws_reserve(qcd_ctx* c, Workspace& w, int nkv) {
     cudaFree(w.d_cr);
     cudaFree(w.d_rn);
     cudaFree(w.d_gam);
+    cudaFree(w.d_gs);
     cudaFreeHost(w.h_pin);
     QCD_CUDA(cudaMalloc(&w.d_a1, sizeof(double) * 2 * nkv * nkv));
     QCD_CUDA(cudaMalloc(&w.d_a2, sizeof(double) * 2 * nkv * nkv));
     QCD_CUDA(cudaMalloc(&w.d_cr, sizeof(double) * 3 * nkv));
     QCD_CUDA(cudaMalloc(&w.d_rn, sizeof(double) * (nkv + 8)));
     QCD_CUDA(cudaMalloc(&w.d_gam, sizeof(double) * 2 * nkv));
+    QCD_CUDA(cudaMalloc(&w.d_gs, sizeof(double) * 8 * nkv));
     QCD_CUDA(cudaMallocHost(&w.h_pin, sizeof(double) * (nkv + 8)));
     w.nkv = nkv;
   }
@@ -127,10 +130,17 @@ int solve_one(qcd_ctx* c, const Rec& b, const Rec& x, const qcd_solver_params& s
         double* chik = (double*)w.chi[k].data;
         double* a1 = w.d_a1 + 2 * (size_t)k * sp.nkv;
         double* a2 = w.d_a2 + 2 * (size_t)k * sp.nkv;
-        QCD_TRY(blas_multidot(c, chi_p.data(), k, chik, a1, s));
-        QCD_TRY(blas_axpy_dot(c, chi_p.data(), k, a1, chik, a2, s));
-        QCD_TRY(blas_axpy_norm_dot(c, chi_p.data(), k, a2, chik, (const double*)w.rho.data, w.d_cr + 3 * k, s));
-        QCD_TRY(blas_normalise_update(c, chik, (double*)w.rho.data, w.d_cr + 3 * k, w.d_rn + k, s));
+        // classical Gram-Schmidt; the second pass runs (decided on the device)
+        // only if the first one cancelled more than half of the squared norm
+        double* gs = w.d_gs + 8 * (size_t)k;
+        const double* rho_p = (const double*)w.rho.data;
+        QCD_TRY(blas_multidot(c, chi_p.data(), k, chik, a1, s, nullptr, gs));
+        QCD_TRY(blas_axpy_norm_dot(c, chi_p.data(), k, a1, chik, rho_p, gs + 1, s));
+        if (k > 0) {
+          QCD_TRY(blas_multidot(c, chi_p.data(), k, chik, a2, s, gs));
+          QCD_TRY(blas_axpy_norm_dot(c, chi_p.data(), k, a2, chik, rho_p, gs + 4, s, gs));
+        }
+        QCD_TRY(blas_normalise_update(c, chik, (double*)w.rho.data, gs, k > 0, w.d_cr + 3 * k, w.d_rn + k, s));
         double rk2 = 0;
         QCD_TRY(read_scalar(w, w.d_rn + k, &rk2, s));
         ++inf.iterations;
@@ -185,6 +195,7 @@ void workspace_free(qcd_ctx* c) {
   cudaFree(w->d_cr);
   cudaFree(w->d_rn);
   cudaFree(w->d_gam);
+  cudaFree(w->d_gs);
   if (w->h_pin) cudaFreeHost(w->h_pin);
   delete w;
   c->ws = nullptr;
