@@ -242,6 +242,27 @@ int qcd_field_export(qcd_ctx* ctx, const qcd_field* f, double* out, void* stream
 int qcd_apply_D_field(qcd_ctx* ctx, const qcd_field* in, qcd_field* out, int dagger, void* stream);
 
 /*
+ * out = D in (dagger = 0) or D^+ in (dagger = 1) in FP64, like qcd_apply_D with
+ * prec = QCD_PREC_F64 and nrhs = 1, but without allocating device memory.  The
+ * paper has no counterpart: this entry point exists for callers that must not
+ * have a library allocate or free device memory -- programs whose own pool
+ * allocator owns all device memory within a fixed budget, and latency-bound
+ * loops where cudaFree's device-wide synchronisation would stall other
+ * streams.  The two staging fields live in one static device array of the
+ * library instead, so:
+ *   - the lattice may have at most 65536 sites (QCD_ERR_TOO_LARGE beyond);
+ *   - the array (24 MiB) is held on every GPU that loads the library until exit;
+ *   - all calls share the array; calls that overlap on the GPU race;
+ *   - the first call on each device looks up the array's address; make it
+ *     before any stream capture;
+ *   - kernel profiling (qcd_profile_enable) must be off.
+ * in/out: device (V, 4, 3) complex128, must not alias.  The call is
+ * asynchronous: out is ready when the stream reaches the call's end.  Needs
+ * qcd_load_gauge and qcd_build_clover first (QCD_ERR_STATE).
+ */
+int qcd_apply_D_noalloc(qcd_ctx* ctx, const double* in, double* out, int dagger, void* stream);
+
+/*
  * psi = M_SAP eta: one application of the Schwarz preconditioner (Sec. 4) with
  * ncy cycles of nmr MR steps per block, block fields in sap_prec.  eta, psi:
  * device (V, 4, 3) complex128 lexicographic.

@@ -85,6 +85,7 @@ def lib():
             "qcd_field_import": (I, [P, P, P, P]),
             "qcd_field_export": (I, [P, P, P, P]),
             "qcd_apply_D_field": (I, [P, P, P, I, P]),
+            "qcd_apply_D_noalloc": (I, [P, P, P, I, P]),
             "qcd_sap_apply": (I, [P, P, P, I, I, I, P]),
             "qcd_profile_enable": (I, [P, I]),
             "qcd_launch_count": (ctypes.c_longlong, []),
@@ -234,6 +235,11 @@ def qcd_field_export(ctx, f, t):
 
 def qcd_apply_D_field(ctx, fin, fout, dagger=False):
     return check(lib().qcd_apply_D_field(ctx, fin, fout, int(dagger), _stream()), "qcd_apply_D_field")
+
+
+def qcd_apply_D_noalloc(ctx, inp, out, dagger=False):
+    """FP64 D (or D^+) without device allocation (lattices up to 65536 sites)."""
+    return lib().qcd_apply_D_noalloc(ctx, _ptr(inp), _ptr(out), int(dagger), _stream())
 
 
 def qcd_sap_apply(ctx, eta, psi, ncy, nmr, prec="f32"):

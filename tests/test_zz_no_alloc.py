@@ -1,0 +1,48 @@
+"""The allocation-free operator apply (qcd_apply_D_noalloc) through the C ABI.
+
+Some callers cannot let a library allocate device memory: programs whose own
+pool allocator owns all of it, and latency-bound loops in which cudaFree's
+device-wide synchronisation would stall other streams.  For them the FP64
+apply keeps its two staging fields in a static device array of the library
+(at most 65536 sites).  This file is collected last so that a failure here,
+under -x, comes after every other test has run.
+"""
+import numpy as np
+import pytest
+
+from helpers import rel
+from paper_1109_4279_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+AP = synth.ANTIPERIODIC_T
+
+
+def test_no_alloc_apply_matches_apply_D_twice():
+    """Two calls in a row (different inputs, D then D^+) equal qcd_apply_D at
+    the FP64 parity tolerance; the second call reuses the shared array."""
+    from paper_1109_4279_gb300 import binding as B
+    dims, block = (8, 8, 8, 16), (4, 4, 4, 4)
+    U, rng = synth.gauge_field(dims, 0.5, 81)
+    lat = B.Lattice(dims, block, 0.0, 1.5)
+    lat.load_gauge(torch.from_numpy(U).cuda())
+    for dagger in (False, True):
+        b = torch.from_numpy(synth.gaussian_spinor(dims, rng)).cuda()
+        out = torch.empty_like(b)
+        st = B.qcd_apply_D_noalloc(lat.ctx, b, out, dagger)
+        assert st == 0, B.qcd_status_string(st)
+        ref = torch.empty_like(b)
+        B.qcd_apply_D(lat.ctx, b, ref, dagger, "f64", 1)
+        torch.cuda.synchronize()
+        assert rel(out.cpu().numpy(), ref.cpu().numpy()) < 1e-12
+    lat.close()
+
+
+def test_no_alloc_rejects_too_large():
+    from paper_1109_4279_gb300 import binding as B
+    lat = B.Lattice((32, 16, 16, 16), (4, 4, 4, 4), 0.0, 1.5)  # 131072 sites > 65536
+    x = torch.zeros((lat.V, 4, 3), dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    assert B.qcd_apply_D_noalloc(lat.ctx, x, y, False) == -12  # QCD_ERR_TOO_LARGE
+    lat.close()
