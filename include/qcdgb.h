@@ -59,6 +59,7 @@ extern "C" {
 #define QCD_NAN -10                 /* a NaN/Inf appeared in the recursion */
 #define QCD_ERR_UNSUPPORTED -11     /* the requested precision/shape combination is not available */
 #define QCD_ERR_TOO_LARGE -12       /* size beyond a fixed limit of the called entry point */
+#define QCD_ERR_TIMEOUT -13         /* a kernel's bounded wait ran out (the kernel skipped its work and returned) */
 
 /* storage/arithmetic precisions */
 #define QCD_PREC_F64 0   /* FP64 storage and arithmetic */
@@ -203,12 +204,32 @@ int qcd_gradient(qcd_ctx* ctx, const double* phi, double* dL_dphi, double* dL_dt
 int qcd_force(qcd_ctx* ctx, const double* x, const double* y, double* F, void* stream);
 
 /*
- * Pick, by timing on the device, the fastest kernel launch shape for the
- * context's operator and SAP sweep at nrhs right-hand sides, and record the
- * choice in the context.  cache_path (may be NULL): a JSON file read before
- * and written after tuning, keyed by GPU name, dims, block and precision.
+ * Pick, by timing on the device, the fastest CTA size of the operator kernel
+ * for each storage precision of this context, and keep the choice in the
+ * context.  nrhs: right-hand sides per call the tuning should reflect (the
+ * timing applies that many operators back to back).  cache_path (may be
+ * NULL): a JSON file read before tuning (a matching entry is applied without
+ * timing) and rewritten after it, keyed by GPU name, dims, block and nrhs.
+ * Needs qcd_load_gauge and qcd_build_clover first.
  */
 int qcd_autotune(qcd_ctx* ctx, int nrhs, const char* cache_path);
+
+/*
+ * Choose the Schwarz block shape (Sec. 4/5: the block size is the main SAP
+ * tuning parameter; local lattice sizes need only be multiples of it) by
+ * timing complete solves of b on the given gauge field: for each candidate a
+ * temporary context is created with p's action parameters, the field is
+ * loaded, the clover term built and D x = b solved with sp.  candidates: n
+ * shapes (4 ints each); NULL enumerates shapes with even extents, an even
+ * number of blocks per direction and 64..512 sites.  U, b: (V,4,3,3) and
+ * (V,4,3) complex128, host (is_device = 0) or device pointers.  out_block
+ * receives the fastest shape; times_ms (may be NULL, n entries, or 64 when
+ * candidates is NULL) the time-to-solution of each candidate (negative when a
+ * candidate failed).  Returns the number of candidates tried, or a negative
+ * status.
+ */
+int qcd_tune_block(const qcd_params* p, const double* U, const double* b, int is_device, const qcd_solver_params* sp,
+                   const int* candidates, int n, int out_block[4], double* times_ms);
 
 /* Static description of a status code. */
 const char* qcd_status_string(int status);

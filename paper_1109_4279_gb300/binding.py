@@ -78,6 +78,8 @@ def lib():
             "qcd_gradient": (I, [P, P, P, P, P, P, ctypes.POINTER(SolverParams), P]),
             "qcd_force": (I, [P, P, P, P, P]),
             "qcd_autotune": (I, [P, I, ctypes.c_char_p]),
+            "qcd_tune_block": (I, [ctypes.POINTER(Params), P, P, I, ctypes.POINTER(SolverParams), P, I,
+                                   ctypes.POINTER(ctypes.c_int * 4), ctypes.POINTER(ctypes.c_double)]),
             "qcd_status_string": (ctypes.c_char_p, [I]),
             "qcd_last_error": (ctypes.c_char_p, []),
             "qcd_field_create": (I, [P, I, ctypes.POINTER(P)]),
@@ -209,6 +211,26 @@ def qcd_force(ctx, x, y, F):
 
 def qcd_autotune(ctx, nrhs=1, cache_path=None):
     return check(lib().qcd_autotune(ctx, int(nrhs), cache_path.encode() if cache_path else None), "qcd_autotune")
+
+
+def qcd_tune_block(dims, m0, csw, U, b, candidates=None, params=None, bc=(-1.0, 1.0, 1.0, 1.0)):
+    """Time complete solves over Schwarz block shapes; returns (best_block, {shape: ms})."""
+    p = Params()
+    p.dims[:] = [int(d) for d in dims]
+    p.block[:] = [2, 2, 2, 2]
+    p.m0, p.csw = float(m0), float(csw)
+    p.bc[:] = [float(v) for v in bc]
+    n = len(candidates) if candidates else 0
+    cand = (ctypes.c_int * (4 * n))(*[int(v) for c in candidates for v in c]) if n else None
+    out = (ctypes.c_int * 4)()
+    times = (ctypes.c_double * (n if n else 64))()
+    tried = lib().qcd_tune_block(ctypes.byref(p), _ptr(U), _ptr(b), int(U.is_cuda), ctypes.byref(params) if params else None,
+                                 cand, n, ctypes.byref(out), times)
+    if tried < 0:
+        raise QcdError(tried, "qcd_tune_block")
+    shapes = candidates if n else None
+    result = {tuple(shapes[i]) if shapes else i: times[i] for i in range(tried)}
+    return tuple(out), result
 
 
 def qcd_status_string(st):

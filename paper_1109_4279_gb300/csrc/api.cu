@@ -39,17 +39,6 @@ void rec_free(Rec& r) {
   r = Rec();
 }
 
-int ensure_partials(qcd_ctx* c, size_t n) {
-  if (n <= c->partials_len) return QCD_OK;
-  // growing synchronises the device (cudaFree); contexts pre-size this buffer
-  if (c->d_partials) cudaFree(c->d_partials);
-  c->d_partials = nullptr;
-  c->partials_len = 0;
-  QCD_CUDA(cudaMalloc(&c->d_partials, n * sizeof(double)));
-  c->partials_len = n;
-  return QCD_OK;
-}
-
 Workspace* ensure_ws(qcd_ctx* c) {
   if (!c->ws) c->ws = new (std::nothrow) Workspace();
   return c->ws;
@@ -134,6 +123,7 @@ const char* qcd_status_string(int st) {
     case QCD_NAN: return "NaN or Inf in the recursion";
     case QCD_ERR_UNSUPPORTED: return "unsupported precision or block shape";
     case QCD_ERR_TOO_LARGE: return "size beyond the entry point's fixed limit";
+    case QCD_ERR_TIMEOUT: return "a kernel's bounded wait ran out";
     default: return "unknown status";
   }
 }
@@ -152,14 +142,9 @@ int qcd_create(qcd_ctx** out, const qcd_params* p) {
   c->p = *p;
   int st = setup_geometry(c);
   if (st == QCD_OK) {
-    if (cudaMalloc(&c->d_scalars, 64 * 1024) != cudaSuccess || cudaMallocHost(&c->h_scalars, 64 * 1024) != cudaSuccess)
+    if (cudaMalloc(&c->d_scalars, 64 * 1024) != cudaSuccess || cudaMallocHost(&c->h_scalars, 64 * 1024) != cudaSuccess ||
+        cudaMemset(c->d_scalars, 0, 64 * 1024) != cudaSuccess)
       st = QCD_ERR_NOMEM;
-  }
-  if (st == QCD_OK) {
-    // pre-size the reduction scratch: the largest grid of any reduction
-    size_t n = (size_t)(c->V + 255) / 256 + 1;
-    size_t m = (size_t)152 * 8 * 64 + 64;
-    st = ensure_partials(c, n > m ? n : m);
   }
   if (st != QCD_OK) {
     qcd_destroy(c);
@@ -178,8 +163,9 @@ void qcd_destroy(qcd_ctx* c) {
     rec_free(c->A[p]);
     rec_free(c->Ahat[p]);
   }
+  for (auto st : c->streams) cudaStreamDestroy(st);
+  c->streams.clear();
   if (c->d_tables) cudaFree(c->d_tables);
-  if (c->d_partials) cudaFree(c->d_partials);
   if (c->d_scalars) cudaFree(c->d_scalars);
   if (c->h_scalars) cudaFreeHost(c->h_scalars);
   for (auto& t : c->timers)
@@ -235,6 +221,117 @@ int qcd_apply_D(qcd_ctx* c, const double* in, double* out, int dagger, int prec,
   return st;
 }
 
+// streams of a context for batched right-hand sides (created once)
+static int ctx_streams(qcd_ctx* c, int n) {
+  while ((int)c->streams.size() < n) {
+    cudaStream_t s;
+    QCD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    c->streams.push_back(s);
+  }
+  return QCD_OK;
+}
+
+static Workspace* rhs_workspace(qcd_ctx* c, int k) {
+  if (k == 0) return ensure_ws(c);
+  while ((int)c->batch_ws.size() < k) {
+    Workspace* w = new (std::nothrow) Workspace();
+    if (!w) return nullptr;
+    c->batch_ws.push_back(w);
+  }
+  return c->batch_ws[k - 1];
+}
+
+// order: the problems' streams wait for `s`, and `s` waits for them afterwards
+static int fork_streams(cudaStream_t s, std::vector<Problem>& probs) {
+  cudaEvent_t e;
+  QCD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEventRecord(e, s);
+  for (auto& p : probs)
+    if (p.s != s) cudaStreamWaitEvent(p.s, e, 0);
+  cudaEventDestroy(e);
+  return QCD_OK;
+}
+
+static int join_streams(cudaStream_t s, std::vector<Problem>& probs) {
+  for (auto& p : probs) {
+    if (p.s == s) continue;
+    cudaEvent_t e;
+    QCD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEventRecord(e, p.s);
+    cudaStreamWaitEvent(s, e, 0);
+    cudaEventDestroy(e);
+  }
+  return QCD_OK;
+}
+
+// solve a set of problems whose b/x are lexicographic device or host arrays
+static int solve_problems(std::vector<Problem>& probs, const double* const* b, double* const* x, bool dev,
+                          const qcd_solver_params& sp, qcd_solve_info* info, cudaStream_t s) {
+  const int n = (int)probs.size();
+  std::vector<double*> stage(n, nullptr);
+  int st = QCD_OK;
+  for (int k = 0; k < n && st == QCD_OK; ++k) {
+    Problem& p = probs[k];
+    for (Rec* f : {&p.w->b, &p.w->x})
+      if (!f->data) st = rec_alloc(*f, P64, 24, p.c->V);
+    if (st != QCD_OK) break;
+    p.b = p.w->b;
+    p.x = p.w->x;
+    const size_t fbytes = (size_t)p.c->V * 24 * sizeof(double);
+    const double* bd = b[k];
+    const double* xd = x[k];
+    if (!dev) {
+      if (cudaMalloc(&stage[k], 2 * fbytes) != cudaSuccess) {
+        cudaGetLastError();
+        st = QCD_ERR_NOMEM;
+        break;
+      }
+      cudaError_t e = cudaMemcpyAsync(stage[k], b[k], fbytes, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(stage[k] + p.c->V * 24, x[k], fbytes, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "solve upload");
+      bd = stage[k];
+      xd = stage[k] + p.c->V * 24;
+    }
+    if (st == QCD_OK) st = import_spinor(p.c, bd, p.b, 1, s);
+    if (st == QCD_OK) st = import_spinor(p.c, xd, p.x, 1, s);
+  }
+  if (st == QCD_OK) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    fork_streams(s, probs);
+    bool prof = false;
+    for (auto& p : probs) prof |= p.c->prof;
+    st = fgcr_batch(probs, sp, n > 1 && !prof);
+    join_streams(s, probs);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (auto& p : probs) p.info.time_ms = ms;
+    for (int k = 0; k < n; ++k) {
+      Problem& p = probs[k];
+      double* xd = dev ? x[k] : stage[k] + p.c->V * 24;
+      int e2 = export_spinor(p.c, p.x, xd, 1, s);
+      if (e2 == QCD_OK && !dev) {
+        cudaError_t e = cudaMemcpyAsync(x[k], xd, (size_t)p.c->V * 24 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) e2 = cuda_fail(e, "solve download");
+      }
+      if (e2 != QCD_OK && p.status == QCD_OK) p.status = p.info.status = e2;
+      if (e2 != QCD_OK && st == QCD_OK) st = e2;
+    }
+  }
+  cudaStreamSynchronize(s);
+  for (int k = 0; k < n; ++k) {
+    if (stage[k]) cudaFree(stage[k]);
+    if (info) info[k] = probs[k].info;
+  }
+  return st;
+}
+
 int qcd_solve(qcd_ctx* c, const double* b, double* x, int nrhs, const qcd_solver_params* sp_in, qcd_solve_info* info,
               void* stream) {
   if (!c || !b || !x || nrhs < 1) return QCD_ERR_ARG;
@@ -242,52 +339,21 @@ int qcd_solve(qcd_ctx* c, const double* b, double* x, int nrhs, const qcd_solver
   qcd_solver_params sp;
   if (sp_in) sp = *sp_in; else qcd_solver_defaults(&sp);
   cudaStream_t s = (cudaStream_t)stream;
-  Workspace* w = ensure_ws(c);
-  if (!w) return QCD_ERR_NOMEM;
-  for (Rec* f : {&w->b, &w->x})
-    if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
   const bool dev = is_device_ptr(b);
   if (dev != is_device_ptr(x)) return QCD_ERR_ARG;
-  const size_t fbytes = (size_t)c->V * 24 * sizeof(double);
-  double* stage = nullptr;
-  if (!dev && cudaMalloc(&stage, 2 * fbytes) != cudaSuccess) {
-    cudaGetLastError();
-    return QCD_ERR_NOMEM;
-  }
-  int first_bad = QCD_OK;
+  if (nrhs > 1) QCD_TRY(ctx_streams(c, nrhs));
+  std::vector<Problem> probs(nrhs);
+  std::vector<const double*> bs(nrhs);
+  std::vector<double*> xs(nrhs);
   for (int k = 0; k < nrhs; ++k) {
-    const double* bk = b + (size_t)k * c->V * 24;
-    double* xk = x + (size_t)k * c->V * 24;
-    const double* bd = bk;
-    double* xd = xk;
-    int st = QCD_OK;
-    if (!dev) {
-      bd = stage;
-      xd = stage + (size_t)c->V * 24;
-      cudaError_t e = cudaMemcpyAsync(stage, bk, fbytes, cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(xd, xk, fbytes, cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) st = cuda_fail(e, "solve upload");
-    }
-    if (st == QCD_OK) st = import_spinor(c, bd, w->b, 1, s);
-    if (st == QCD_OK) st = import_spinor(c, xd, w->x, 1, s);
-    qcd_solve_info inf;
-    memset(&inf, 0, sizeof(inf));
-    if (st == QCD_OK) {
-      st = solve_one(c, w->b, w->x, sp, &inf, s);
-      int e2 = export_spinor(c, w->x, xd, 1, s);
-      if (st == QCD_OK) st = e2;
-      if (!dev && e2 == QCD_OK) {
-        cudaError_t e = cudaMemcpyAsync(xk, xd, fbytes, cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess && st == QCD_OK) st = cuda_fail(e, "solve download");
-      }
-    }
-    inf.status = st;
-    if (info) info[k] = inf;
-    if (st != QCD_OK && first_bad == QCD_OK) first_bad = st;
+    probs[k].c = c;
+    probs[k].w = rhs_workspace(c, k);
+    if (!probs[k].w) return QCD_ERR_NOMEM;
+    probs[k].s = nrhs > 1 ? c->streams[k] : s;
+    bs[k] = b + (size_t)k * c->V * 24;
+    xs[k] = x + (size_t)k * c->V * 24;
   }
-  cudaStreamSynchronize(s);
-  if (stage) cudaFree(stage);
-  return first_bad;
+  return solve_problems(probs, bs.data(), xs.data(), dev, sp, info, s);
 }
 
 int qcd_solve_dagger(qcd_ctx* c, const double* b, double* x, const qcd_solver_params* sp_in, qcd_solve_info* info,
@@ -313,15 +379,27 @@ int qcd_solve_dagger(qcd_ctx* c, const double* b, double* x, const qcd_solver_pa
   return st != QCD_OK ? st : e;
 }
 
-int qcd_solve_batch(qcd_ctx** ctxs, int n, const double* const* b, double* const* x, const qcd_solver_params* sp,
+int qcd_solve_batch(qcd_ctx** ctxs, int n, const double* const* b, double* const* x, const qcd_solver_params* sp_in,
                     qcd_solve_info* info, void* stream) {
   if (!ctxs || !b || !x || n < 1) return QCD_ERR_ARG;
-  int first_bad = QCD_OK;
+  qcd_solver_params sp;
+  if (sp_in) sp = *sp_in; else qcd_solver_defaults(&sp);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<Problem> probs(n);
   for (int i = 0; i < n; ++i) {
-    int st = qcd_solve(ctxs[i], b[i], x[i], 1, sp, info ? info + i : nullptr, stream);
-    if (st != QCD_OK && first_bad == QCD_OK) first_bad = st;
+    qcd_ctx* c = ctxs[i];
+    if (!c || !b[i] || !x[i]) return QCD_ERR_ARG;
+    if (!c->clover_built) return QCD_ERR_STATE;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return QCD_ERR_ARG;  // one right-hand side per context (use qcd_solve's nrhs)
+    if (!is_device_ptr(b[i]) || !is_device_ptr(x[i])) return QCD_ERR_ARG;
+    QCD_TRY(ctx_streams(c, 1));
+    probs[i].c = c;
+    probs[i].w = ensure_ws(c);
+    if (!probs[i].w) return QCD_ERR_NOMEM;
+    probs[i].s = n > 1 ? c->streams[0] : s;
   }
-  return first_bad;
+  return solve_problems(probs, b, x, true, sp, info, s);
 }
 
 int qcd_force(qcd_ctx* c, const double* x, const double* y, double* F, void* stream) {
@@ -382,12 +460,6 @@ int qcd_gradient(qcd_ctx* c, const double* phi, double* dL_dphi, double* dL_dthe
   return st;
 }
 
-int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
-  (void)nrhs; (void)cache_path;
-  if (!c) return QCD_ERR_ARG;
-  return QCD_OK;
-}
-
 int qcd_field_create(qcd_ctx* c, int prec, qcd_field** out) {
   if (!c || !out || prec < 0 || prec > 3) return QCD_ERR_ARG;
   qcd_field* f = new (std::nothrow) qcd_field();
@@ -434,7 +506,7 @@ int qcd_sap_apply(qcd_ctx* c, const double* eta, double* psi, int ncy, int nmr, 
   for (Rec* f : {&w->b, &w->x})
     if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
   QCD_TRY(import_spinor(c, eta, w->b, 1, s));
-  QCD_TRY(sap_apply(c, w->b, w->x, ncy, nmr, sap_prec, s));
+  QCD_TRY(sap_apply(c, w->sap, w->b, w->x, ncy, nmr, sap_prec, s));
   QCD_TRY(export_spinor(c, w->x, psi, 1, s));
   QCD_CUDA(cudaStreamSynchronize(s));
   return QCD_OK;

@@ -238,7 +238,7 @@ static VecList make_list(const double* const* v, int k) {
   return vl;
 }
 
-int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s,
+int blas_multidot(qcd_ctx* c, double* part, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s,
                   const double* cond, double* d_norm) {
   if (k <= 0) return QCD_OK;
   if (k > kMaxVec) return QCD_ERR_ARG;
@@ -252,14 +252,13 @@ int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, do
     const int kk = k - done < K ? k - done : K;
     const int norm = (d_norm != nullptr && done == 0) ? 1 : 0;
     const int M = 2 * K + norm;
-    QCD_TRY(ensure_partials(c, (size_t)grid * M));
     VecList vl = make_list(v + done, kk);
     const double2* w2 = (const double2*)w;
 #define MD(KK)                                                                                                   \
   if (norm)                                                                                                      \
-    multidot_kernel<KK, 1><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, c->d_partials);                  \
+    multidot_kernel<KK, 1><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, part);                  \
   else                                                                                                           \
-    multidot_kernel<KK, 0><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, c->d_partials);
+    multidot_kernel<KK, 0><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, part);
     switch (K) {
       case 4: MD(4); break;
       case 8: MD(8); break;
@@ -268,15 +267,15 @@ int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, do
     }
 #undef MD
     QCD_LAUNCHED();
-    QCD_TRY(reduce_partials(c->d_partials, (int)grid, M, 2 * kk, d_out + 2 * done, s));
-    if (norm) QCD_TRY(reduce_partials(c->d_partials + 2 * K, (int)grid, M, 1, d_norm, s));
+    QCD_TRY(reduce_partials(part, (int)grid, M, 2 * kk, d_out + 2 * done, s));
+    if (norm) QCD_TRY(reduce_partials(part + 2 * K, (int)grid, M, 1, d_norm, s));
     done += kk;
   }
   return QCD_OK;
 }
 
 template <int DOT>
-static int axpy_dot_impl(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w, const double* rho,
+static int axpy_dot_impl(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w, const double* rho,
                          double* d_out, cudaStream_t s, const double* cond = nullptr) {
   if (k > 32) return QCD_ERR_UNSUPPORTED;
   const long long n = c->V * 12;
@@ -284,55 +283,52 @@ static int axpy_dot_impl(qcd_ctx* c, const double* const* v, int k, const double
   int K;
   if (k <= 4) K = 4; else if (k <= 8) K = 8; else if (k <= 16) K = 16; else K = 32;
   const int M = DOT == 1 ? 2 * K : 3;
-  QCD_TRY(ensure_partials(c, (size_t)grid * M));
   ProfScope ps(c, QCD_KERNEL_BLAS, s, 16.0 * n * (k + 2 + (DOT == 2)), 16.0 * n * k);
   VecList vl = make_list(v, k);
   const double2* r2 = (const double2*)rho;
   switch (K) {
-    case 4: axpy_dot_kernel<4, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, c->d_partials); break;
-    case 8: axpy_dot_kernel<8, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, c->d_partials); break;
-    case 16: axpy_dot_kernel<16, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, c->d_partials); break;
-    default: axpy_dot_kernel<32, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, c->d_partials); break;
+    case 4: axpy_dot_kernel<4, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, part); break;
+    case 8: axpy_dot_kernel<8, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, part); break;
+    case 16: axpy_dot_kernel<16, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, part); break;
+    default: axpy_dot_kernel<32, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, part); break;
   }
   QCD_LAUNCHED();
-  return reduce_partials(c->d_partials, (int)grid, M, DOT == 1 ? 2 * k : 3, d_out, s);
+  return reduce_partials(part, (int)grid, M, DOT == 1 ? 2 * k : 3, d_out, s);
 }
 
-int blas_axpy_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w, double* d_out,
+int blas_axpy_dot(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w, double* d_out,
                   cudaStream_t s) {
   if (k <= 0) return QCD_OK;
-  return axpy_dot_impl<1>(c, v, k, d_coef, w, nullptr, d_out, s);
+  return axpy_dot_impl<1>(c, part, v, k, d_coef, w, nullptr, d_out, s);
 }
 
-int blas_axpy_norm_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w, const double* rho,
+int blas_axpy_norm_dot(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w, const double* rho,
                        double* d_out, cudaStream_t s, const double* cond) {
   if (k <= 0) {
     // nothing to subtract: only the norm and the dot
     const long long n = c->V * 12;
     const unsigned grid = blas_grid(n);
-    QCD_TRY(ensure_partials(c, (size_t)grid * 3));
     VecList vl = make_list(v, 0);
     ProfScope ps(c, QCD_KERNEL_BLAS, s, 32.0 * n, 8.0 * n);
     axpy_dot_kernel<4, 2><<<grid, kBlasThreads, 0, s>>>(vl, 0, d_coef, (double2*)w, (const double2*)rho, n, cond,
-                                                        c->d_partials);
+                                                        part);
     QCD_LAUNCHED();
-    return reduce_partials(c->d_partials, (int)grid, 3, 3, d_out, s);
+    return reduce_partials(part, (int)grid, 3, 3, d_out, s);
   }
-  return axpy_dot_impl<2>(c, v, k, d_coef, w, rho, d_out, s, cond);
+  return axpy_dot_impl<2>(c, part, v, k, d_coef, w, rho, d_out, s, cond);
 }
 
-int blas_normalise_update(qcd_ctx* c, double* chi, double* rho, const double* d_gs, int two_pass, double* d_cr,
+int blas_normalise_update(qcd_ctx* c, double* part, double* chi, double* rho, const double* d_gs, int two_pass, double* d_cr,
                           double* d_out, cudaStream_t s) {
   const long long n = c->V * 12;
   const unsigned grid = blas_grid(n);
-  QCD_TRY(ensure_partials(c, (size_t)grid));
   {
     ProfScope ps(c, QCD_KERNEL_BLAS, s, 64.0 * n, 8.0 * n);
     normalise_update_kernel<<<grid, kBlasThreads, 0, s>>>((double2*)chi, (double2*)rho, d_gs, two_pass, d_cr, n,
-                                                          c->d_partials);
+                                                          part);
     QCD_LAUNCHED();
   }
-  return reduce_partials(c->d_partials, (int)grid, 1, 1, d_out, s);
+  return reduce_partials(part, (int)grid, 1, 1, d_out, s);
 }
 
 int blas_multi_axpy(qcd_ctx* c, const double* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s) {
@@ -355,16 +351,15 @@ int blas_multi_axpy(qcd_ctx* c, const double* const* phi, int k, const double* d
   return QCD_OK;
 }
 
-int blas_norm2(qcd_ctx* c, const double* v, double* d_out, cudaStream_t s) {
+int blas_norm2(qcd_ctx* c, double* part, const double* v, double* d_out, cudaStream_t s) {
   const long long n = c->V * 12;
   const unsigned grid = blas_grid(n);
-  QCD_TRY(ensure_partials(c, (size_t)grid));
   {
     ProfScope ps(c, QCD_KERNEL_BLAS, s, 16.0 * n, 4.0 * n);
-    norm2_kernel<<<grid, kBlasThreads, 0, s>>>((const double2*)v, n, c->d_partials);
+    norm2_kernel<<<grid, kBlasThreads, 0, s>>>((const double2*)v, n, part);
     QCD_LAUNCHED();
   }
-  return reduce_partials(c->d_partials, (int)grid, 1, 1, d_out, s);
+  return reduce_partials(part, (int)grid, 1, 1, d_out, s);
 }
 
 int blas_gamma5(qcd_ctx* c, const double* x, double* y, int, cudaStream_t s) {

@@ -66,7 +66,7 @@ __device__ __forceinline__ Spinor<T> dirac_site(const Geom& g, const void* U, co
 }
 
 template <int P, int DAG>
-__global__ void __launch_bounds__(256) dirac_kernel(Geom g, const void* __restrict__ U, FieldPtr A, FieldPtr in,
+__global__ void __launch_bounds__(512) dirac_kernel(Geom g, const void* __restrict__ U, FieldPtr A, FieldPtr in,
                                                     FieldPtr out) {
   typedef typename Arith<P>::T T;
   long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -124,7 +124,7 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
   if (out.prec != prec || in.nreal != 24 || out.nreal != 24) return QCD_ERR_ARG;
   QCD_TRY(ensure_gauge(c, prec, s));
   QCD_TRY(ensure_clover(c, prec, s));
-  const int threads = c->dirac_threads;
+  const int threads = c->dirac_threads[prec];
   const unsigned grid = (unsigned)((c->V + threads - 1) / threads);
   const void* U = c->U[prec];
   FieldPtr A = c->A[prec].ptr();
@@ -146,19 +146,18 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
   return QCD_OK;
 }
 
-int residual64(qcd_ctx* c, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s) {
+int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s) {
   if (b.prec != P64 || x.prec != P64 || r.prec != P64) return QCD_ERR_ARG;
   QCD_TRY(ensure_gauge(c, P64, s));
   QCD_TRY(ensure_clover(c, P64, s));
   const unsigned grid = (unsigned)((c->V + 255) / 256);
-  QCD_TRY(ensure_partials(c, grid));
   {
     ProfScope ps(c, QCD_KERNEL_RESIDUAL, s, (bytes_per_site(P64) + 192) * (double)c->V, 1848.0 * (double)c->V);
     residual64_kernel<<<grid, 256, 0, s>>>(c->g, c->U[P64], c->A[P64].ptr(), b.ptr(), x.ptr(), r.ptr(),
-                                           c->d_partials);
+                                           part);
     QCD_LAUNCHED();
   }
-  return reduce_partials(c->d_partials, (int)grid, 1, 1, d_norm2, s);
+  return reduce_partials(part, (int)grid, 1, 1, d_norm2, s);
 }
 
 }  // namespace qcd

@@ -65,7 +65,9 @@ struct SapWork {
   int prec = -1;
 };
 
-// solver work fields (FP64 internal layout unless stated)
+// solver work fields of one right-hand side (FP64 internal layout unless
+// stated).  Every buffer a solve touches is allocated by ws_prepare, so the
+// iteration itself never allocates (and can be captured in a CUDA graph).
 struct Workspace {
   SapWork sap;
   int nkv = 0;
@@ -78,9 +80,12 @@ struct Workspace {
   double* d_rn = nullptr;  // [nkv + 8] residual norms
   double* d_gam = nullptr; // [nkv] complex
   double* d_gs = nullptr;  // [nkv][8] Gram-Schmidt norms and pass results
+  double* d_part = nullptr;  // reduction partial sums
   double* h_pin = nullptr; // pinned host mirror for scalars read back
+  // one captured CUDA graph per FGCR iteration index, valid for graph_key
+  std::vector<cudaGraphExec_t> graphs;
+  long long graph_key = -1;
 };
-
 }  // namespace qcd
 
 struct qcd_field {
@@ -100,16 +105,14 @@ struct qcd_ctx {
   qcd::Rec A[4];     // clover (4 + m0 + c_sw term), 72 reals per site
   qcd::Rec Ahat[4];  // SAP block clover: A on even sites, A^-1 on odd sites
   qcd::Workspace* ws = nullptr;
+  std::vector<qcd::Workspace*> batch_ws;  // extra right-hand sides of a multi-RHS solve
+  std::vector<cudaStream_t> streams;      // one stream per right-hand side of a batch
   // instrumentation
   bool prof = false;
   qcd::Timer timers[QCD_KERNEL_COUNT];
   std::vector<cudaEvent_t> event_pool;
   // launch shape chosen by the autotuner
-  int dirac_threads = 256;
-  int sap_threads_per_site = 1;
-  // reduction scratch (FP64 partial sums)
-  double* d_partials = nullptr;
-  size_t partials_len = 0;
+  int dirac_threads[4] = {256, 256, 256, 256};  // CTA size of the operator kernel per precision
   double* d_scalars = nullptr;  // small device array for coefficients
   double* h_scalars = nullptr;  // pinned host mirror
 };
@@ -129,7 +132,6 @@ struct ProfScope {
 // ---- memory helpers (api.cu)
 int rec_alloc(Rec& r, int prec, int nreal, long long V);
 void rec_free(Rec& r);
-int ensure_partials(qcd_ctx* c, size_t n);
 Workspace* ensure_ws(qcd_ctx* c);
 
 // ---- layout.cu
@@ -149,31 +151,32 @@ int ensure_clover(qcd_ctx* c, int prec, cudaStream_t s);
 // out = D in (dagger: D^+); fields in one precision
 int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s);
 // r = b - D x and |r|^2 partial sums (FP64); optional second output of D x
-int residual64(qcd_ctx* c, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s);
+int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s);
 
 // ---- sap.cu
-int sap_apply(qcd_ctx* c, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec, cudaStream_t s);
+int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s);
+int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec, cudaStream_t s);
 
 // ---- blas.cu (FP64 fields of the context, 24 reals per site)
 // Gram-Schmidt building blocks.  cond (optional) = {|chi|^2, |chi'|^2}: the
 // call is skipped unless |chi'|^2 < |chi|^2 / 2 (second pass, DGKS criterion).
 // d_out[j] = (v_j, w) for j < k (complex); d_norm (optional) = |w|^2
-int blas_multidot(qcd_ctx* c, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s,
+int blas_multidot(qcd_ctx* c, double* part, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s,
                   const double* cond = nullptr, double* d_norm = nullptr);
 // w -= sum_j coef[j] v_j (coef on device, complex); then d_out[j] = (v_j, w) for j < k
-int blas_axpy_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w,
+int blas_axpy_dot(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w,
                   double* d_out, cudaStream_t s);
 // w -= sum_j coef[j] v_j; d_out = {|w|^2, (w, rho)}
-int blas_axpy_norm_dot(qcd_ctx* c, const double* const* v, int k, const double* d_coef, double* w,
+int blas_axpy_norm_dot(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w,
                        const double* rho, double* d_out, cudaStream_t s, const double* cond = nullptr);
 // gs = {|chi|^2, pass-1 {|chi'|^2, (chi', rho)}, pass-2 {...}}: picks the final
 // coefficients into cr, chi /= |chi|, rho -= (chi, rho) chi, d_out = |rho|^2
-int blas_normalise_update(qcd_ctx* c, double* chi, double* rho, const double* d_gs, int two_pass, double* d_cr,
+int blas_normalise_update(qcd_ctx* c, double* part, double* chi, double* rho, const double* d_gs, int two_pass, double* d_cr,
                           double* d_out, cudaStream_t s);
 // x += sum_j gamma_j phi_j (gamma on device)
 int blas_multi_axpy(qcd_ctx* c, const double* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s);
 // norm2
-int blas_norm2(qcd_ctx* c, const double* v, double* d_out, cudaStream_t s);
+int blas_norm2(qcd_ctx* c, double* part, const double* v, double* d_out, cudaStream_t s);
 // y = g5 x (in place allowed)
 int blas_gamma5(qcd_ctx* c, const double* x, double* y, int nsites_layout, cudaStream_t s);
 // small dense solve of the FGCR triangular system on the device
@@ -183,6 +186,26 @@ int fgcr_backsub(const double* d_a1, const double* d_a2, const double* d_cr, int
 int reduce_partials(const double* partials, int nparts, int stride, int m, double* out, cudaStream_t s);
 
 // ---- solver.cu
+size_t partials_for(long long V);
+int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream_t s);
+void ws_release(Workspace& w);
+// one right-hand side of one lattice, solved in lock step with the others
+struct Problem {
+  qcd_ctx* c = nullptr;
+  Workspace* w = nullptr;
+  cudaStream_t s = nullptr;
+  Rec b, x;  // FP64 internal fields (b is read, x holds the guess / solution)
+  qcd_solve_info info{};
+  // driver state
+  double bn = 0, rn = 0;
+  int kused = 0, slow = 0;
+  bool active = true, cycle_done = false;
+  int status = QCD_OK;
+};
+// FGCR (Sec. 4) on all problems in lock step: each iteration is enqueued for
+// every active problem on its own stream (replayed from a CUDA graph when
+// use_graphs), then one host synchronisation checks every residual.
+int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool use_graphs);
 int solve_one(qcd_ctx* c, const Rec& b, const Rec& x, const qcd_solver_params& sp, qcd_solve_info* info,
               cudaStream_t s);
 void workspace_free(qcd_ctx* c);

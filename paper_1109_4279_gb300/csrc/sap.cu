@@ -3,8 +3,8 @@
 // simple iterative solver (MR) and Dirichlet boundary conditions"; Sec. 5 /
 // Table 1: even/odd preconditioning inside the block solver).
 //
-// One launch = one colour half-sweep: one CTA per block of that colour, one
-// thread per (even site, odd site) pair.  The block's links and clover blocks
+// One launch = one colour half-sweep: one CTA per block of that colour, two
+// threads per (even site, odd site) pair.  The block's links and clover blocks
 // are staged in shared memory, so the n_mr MR steps never touch HBM (Sec. 4:
 // "all the data necessary for a block solve fit the local store").  With
 // 16-bit block fields the staged copy keeps the storage format (two link rows,
@@ -265,39 +265,177 @@ __device__ __forceinline__ void s_spinor_store(T* base, int n, int i, const Spin
     }
 }
 
-// neighbour indices of one site packed two per int (16 bits each, 0xffff = outside)
-__device__ __forceinline__ int nb_get(const int* pk, int k) {
-  const int v = (pk[k >> 1] >> (16 * (k & 1))) & 0xffff;
-  return v == 0xffff ? -1 : v;
+// ------------------------------------------------------------------------
+// Pair split: the two threads of an (even site, odd site) pair share the work
+// of every site operation.  Thread half hf computes the hops in directions
+// mu = 2 hf and 2 hf + 1 (so no link is loaded twice) and owns spin
+// components 2 hf and 2 hf + 1 of every vector; the clover term, being block
+// diagonal in chirality, acts on the owned half alone.  Partial hop sums are
+// exchanged with one shuffle per real.
+// ------------------------------------------------------------------------
+
+// owned half (spins 2 hf, 2 hf + 1) of a spinor field stored [24][n] in shared memory
+template <typename T>
+__device__ __forceinline__ Half<T> s_half(const T* base, int n, int i, int hf) {
+  Half<T> h;
+  const T* p = base + (12 * hf) * n + i;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h.c[s][c] = {p[(6 * s + 2 * c) * n], p[(6 * s + 2 * c + 1) * n]};
+  return h;
 }
 
-// hops of D restricted to the block (Dirichlet: hops that leave the block are
-// dropped) at site r from a field v on the opposite parity stored at
-// src[index], index = neighbour site - off:
-//   -1/2 sum_mu [U_mu(r)(1 - g) v(r + mu) + U_mu(r - mu)^+ (1 + g) v(r - mu)]
-// One loop over mu (runtime spin phases): a single copy of the hop code.
+template <typename T>
+__device__ __forceinline__ void s_half_store(T* base, int n, int i, int hf, const Half<T>& h) {
+  T* p = base + (12 * hf) * n + i;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      p[(6 * s + 2 * c) * n] = h.c[s][c].re;
+      p[(6 * s + 2 * c + 1) * n] = h.c[s][c].im;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ Half<T> half_of(const Spinor<T>& v, int hf) {
+  Half<T> h;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h.c[s][c] = hf ? v.c[2 + s][c] : v.c[s][c];
+  return h;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_pair(T v) {
+  return __shfl_xor_sync(0xffffffffu, v, 1);
+}
+
+// own half of the pair's summed partial spinors
+template <typename T>
+__device__ __forceinline__ Half<T> pair_reduce(const Spinor<T>& acc, int hf) {
+  Half<T> mine = half_of(acc, hf);
+  const Half<T> theirs = half_of(acc, 1 - hf);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      mine.c[s][c].re += shfl_pair(theirs.c[s][c].re);
+      mine.c[s][c].im += shfl_pair(theirs.c[s][c].im);
+    }
+  return mine;
+}
+
+// full spinor from the two owned halves of a pair
+template <typename T>
+__device__ __forceinline__ Spinor<T> pair_full(const Half<T>& own, int hf) {
+  Spinor<T> v;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cpx<T> o = {shfl_pair(own.c[s][c].re), shfl_pair(own.c[s][c].im)};
+      v.c[s][c] = hf ? o : own.c[s][c];
+      v.c[2 + s][c] = hf ? own.c[s][c] : o;
+    }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ Half<T> half_axpy(const Half<T>& a, const Half<T>& b, T s) {  // a + s b
+  Half<T> o;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o.c[i][c] = a.c[i][c] + s * b.c[i][c];
+  return o;
+}
+
+// clover chiral block hf applied to an owned half
+template <typename T>
+__device__ __forceinline__ Half<T> clover_half_apply(const T* c36, const Half<T>& in) {
+  cpx<T> i6[6], o6[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) i6[k] = in.c[k / 3][k % 3];
+  clover_block_apply(c36, i6, o6);
+  Half<T> o;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) o.c[k / 3][k % 3] = o6[k];
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ Half<T> clover_half(const ExpandedStage<T>& st, int r, int hf, const Half<T>& in) {
+  T c[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) c[k] = st.A[(36 * hf + k) * st.Vb + r];
+  return clover_half_apply(c, in);
+}
+
+template <int P>
+__device__ __forceinline__ Half<float> clover_half(const HalfStage<P>& st, int r, int hf, const Half<float>& in) {
+  typedef typename HalfStage<P>::hr hr;
+  const uint4* A = (const uint4*)(st.base + 96 * st.Vb);
+  float h40[40];  // chunks 4 hf .. 4 hf + 4 hold this chiral block's 36 values at offset 4 hf
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const uint4 v = A[(4 * hf + k) * st.Vb + r];
+    const hr* h = reinterpret_cast<const hr*>(&v);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) h40[8 * k + e] = to_f<P>(h[e]);
+  }
+  float c[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) c[k] = hf ? h40[k + 4] : h40[k];
+  Half<float> o = clover_half_apply(c, in);
+  const float s = ((const float*)(st.base + 240 * st.Vb))[r];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) o.c[a][b] = s * o.c[a][b];
+  return o;
+}
+
+// partial hops of the block operator at site r over directions mu = 2 hf + m:
+//   sum_mu [U_mu(r)(1 - g) v(r + mu) + U_mu(r - mu)^+ (1 + g) v(r - mu)]
+// (Dirichlet: hops leaving the block are absent); v lives on the opposite
+// parity at src[site - off]; pk[m] = forward | backward << 16 indices into
+// src, 0xffff when the neighbour is outside the block.
 template <typename T, typename ST>
-__device__ __forceinline__ Spinor<T> hops(const ST& st, int n, int r, const T* src, const int* pk, int off) {
+__device__ __forceinline__ Spinor<T> hops_pair(const ST& st, int n, int r, const T* src, const int pk[2], int off,
+                                               int hf) {
   Spinor<T> acc;
   zero(acc);
 #pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {
+  for (int m = 0; m < 2; ++m) {
+    const int mu = 2 * hf + m;
     const SpinDir<T> d = spin_dir<T>(mu);
-    const int kf = nb_get(pk, 2 * mu), kb = nb_get(pk, 2 * mu + 1);
-    if (kf >= 0) {
+    const int pm = m ? pk[1] : pk[0];
+    const int kf = pm & 0xffff, kb = (pm >> 16) & 0xffff;
+    if (kf != 0xffff) {
       const Half<T> h = project_rt<-1>(s_spinor(src, n, kf), d);
       expand_add_rt<-1>(acc, umul(st.link(r, mu), h), T(1), d);
     }
-    if (kb >= 0) {
+    if (kb != 0xffff) {
       const Half<T> h = project_rt<+1>(s_spinor(src, n, kb), d);
       expand_add_rt<+1>(acc, udmul(st.link(kb + off, mu), h), T(1), d);
     }
   }
-#pragma unroll
-  for (int s = 0; s < 4; ++s)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) acc.c[s][c] = T(-0.5) * acc.c[s][c];
   return acc;
+}
+
+// owned half of -1/2 (sum of hops) at site r
+template <typename T, typename ST>
+__device__ __forceinline__ Half<T> block_hops(const ST& st, int n, int r, const T* src, const int pk[2], int off,
+                                              int hf) {
+  Half<T> h = pair_reduce(hops_pair<T>(st, n, r, src, pk, off, hf), hf);
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h.c[s][c] = T(-0.5) * h.c[s][c];
+  return h;
 }
 
 // deterministic CTA-wide sum of 3 values; every thread gets the totals
@@ -325,14 +463,6 @@ __device__ __forceinline__ void cta_sum3(T& a, T& b, T& c, T* red) {
   __syncthreads();
 }
 
-template <typename T>
-__device__ __forceinline__ void add_spinor(Spinor<T>& a, const Spinor<T>& b, T s) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) a.c[i][c] = a.c[i][c] + s * b.c[i][c];
-}
-
 // psi storage precision of the SAP accumulator
 template <int P>
 struct PsiPrec {
@@ -343,37 +473,88 @@ struct PsiPrec<P64> {
   static constexpr int value = P64;
 };
 
-// receive the face contributions of the other colour at site (blk, r)
-template <typename T, typename ST>
-__device__ __forceinline__ void receive_faces(const SapArgs& a, const ST& st, int blk, int r, const int y[4],
-                                              const int n[4], Spinor<T>& rho) {
-  const Geom& g = a.g;
-#pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {
-    const SpinDir<T> d = spin_dir<T>(mu);
-    if (y[mu] == g.b[mu] - 1) {  // from block + mu: U_mu(y) (1 - g) part, projected by the sender
-      const int nbk = n[mu] + 1 < g.nb[mu] ? blk + g.bstr[mu] : blk - (g.nb[mu] - 1) * g.bstr[mu];
-      const Half<T> h = face_load<T>(a, nbk, 2 * mu, face_index(g, y, mu));
-      expand_add_rt<-1>(rho, umul(st.link(r, mu), h), T(1), d);
+// owned half of an FP32 / FP64 spinor field in global memory (spins 2 hf, 2 hf + 1
+// are reals 12 hf .. 12 hf + 11: float4 chunks 3 hf .. 3 hf + 2, or double2 chunks 6 hf ..)
+template <int PS, typename T>
+__device__ __forceinline__ Half<T> g_half(const FieldPtr& f, int Vb, int blk, int r, int hf) {
+  Half<T> h;
+  if constexpr (PS == P64) {
+    const double2* d = (const double2*)f.data + ((long long)blk * 12 + 6 * hf) * Vb + r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double2 v = d[(long long)k * Vb];
+      h.c[k / 3][k % 3] = {(T)v.x, (T)v.y};
     }
-    if (y[mu] == 0) {  // from block - mu: U^+ (1 + g) part, multiplied by the sender
-      const int nbk = n[mu] > 0 ? blk - g.bstr[mu] : blk + (g.nb[mu] - 1) * g.bstr[mu];
-      const Half<T> w = face_load<T>(a, nbk, 2 * mu + 1, face_index(g, y, mu));
-      expand_add_rt<+1>(rho, w, T(1), d);
+  } else {
+    const float4* d = (const float4*)f.data + ((long long)blk * 6 + 3 * hf) * Vb + r;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 v = d[(long long)k * Vb];
+      h.c[(2 * k) / 3][(2 * k) % 3] = {(T)v.x, (T)v.y};
+      h.c[(2 * k + 1) / 3][(2 * k + 1) % 3] = {(T)v.z, (T)v.w};
+    }
+  }
+  return h;
+}
+
+template <int PS, typename T>
+__device__ __forceinline__ void g_half_store(const FieldPtr& f, int Vb, int blk, int r, int hf, const Half<T>& h) {
+  if constexpr (PS == P64) {
+    double2* d = (double2*)f.data + ((long long)blk * 12 + 6 * hf) * Vb + r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) d[(long long)k * Vb] = make_double2((double)h.c[k / 3][k % 3].re, (double)h.c[k / 3][k % 3].im);
+  } else {
+    float4* d = (float4*)f.data + ((long long)blk * 6 + 3 * hf) * Vb + r;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const cpx<T> a = h.c[(2 * k) / 3][(2 * k) % 3], b = h.c[(2 * k + 1) / 3][(2 * k + 1) % 3];
+      d[(long long)k * Vb] = make_float4((float)a.re, (float)a.im, (float)b.re, (float)b.im);
     }
   }
 }
 
-// write the face contributions of the correction chi at site (blk, r)
+// receive the other colour's face contributions at site (blk, r) for the
+// directions of this thread; returns a partial full spinor
+template <typename T, typename ST>
+__device__ __forceinline__ Spinor<T> receive_faces(const SapArgs& a, const ST& st, int blk, int r, const int y[4],
+                                                   const int n[4], int hf) {
+  const Geom& g = a.g;
+  Spinor<T> acc;
+  zero(acc);
+#pragma unroll 1
+  for (int m = 0; m < 2; ++m) {
+    const int mu = 2 * hf + m;
+    const SpinDir<T> d = spin_dir<T>(mu);
+    const int ymu = mu == 0 ? y[0] : (mu == 1 ? y[1] : (mu == 2 ? y[2] : y[3]));
+    const int nmu = mu == 0 ? n[0] : (mu == 1 ? n[1] : (mu == 2 ? n[2] : n[3]));
+    if (ymu == g.b[mu] - 1) {  // from block + mu: U_mu(y) (1 - g) part, projected by the sender
+      const int nbk = nmu + 1 < g.nb[mu] ? blk + g.bstr[mu] : blk - (g.nb[mu] - 1) * g.bstr[mu];
+      const Half<T> h = face_load<T>(a, nbk, 2 * mu, face_index(g, y, mu));
+      expand_add_rt<-1>(acc, umul(st.link(r, mu), h), T(1), d);
+    }
+    if (ymu == 0) {  // from block - mu: U^+ (1 + g) part, multiplied by the sender
+      const int nbk = nmu > 0 ? blk - g.bstr[mu] : blk + (g.nb[mu] - 1) * g.bstr[mu];
+      const Half<T> w = face_load<T>(a, nbk, 2 * mu + 1, face_index(g, y, mu));
+      expand_add_rt<+1>(acc, w, T(1), d);
+    }
+  }
+  return acc;
+}
+
+// write the face contributions of the correction chi at site (blk, r) for the
+// directions of this thread
 template <typename T, typename ST>
 __device__ __forceinline__ void send_faces(const SapArgs& a, const ST& st, int blk, int r, const int y[4],
-                                           const int n[4], const Spinor<T>& chi) {
+                                           const int n[4], const Spinor<T>& chi, int hf) {
   const Geom& g = a.g;
 #pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {
+  for (int m = 0; m < 2; ++m) {
+    const int mu = 2 * hf + m;
     const SpinDir<T> d = spin_dir<T>(mu);
-    if (y[mu] == 0) {  // to y = x - mu: 1/2 eta_mu(y) (1 - g) chi, projected
-      const T f = T(0.5) * ((n[mu] == 0) ? (T)g.bc[mu] : T(1));
+    const int ymu = mu == 0 ? y[0] : (mu == 1 ? y[1] : (mu == 2 ? y[2] : y[3]));
+    const int nmu = mu == 0 ? n[0] : (mu == 1 ? n[1] : (mu == 2 ? n[2] : n[3]));
+    if (ymu == 0) {  // to y = x - mu: 1/2 eta_mu(y) (1 - g) chi, projected
+      const T f = T(0.5) * ((nmu == 0) ? (T)g.bc[mu] : T(1));
       Half<T> h = project_rt<-1>(chi, d);
 #pragma unroll
       for (int s = 0; s < 2; ++s)
@@ -381,8 +562,8 @@ __device__ __forceinline__ void send_faces(const SapArgs& a, const ST& st, int b
         for (int c = 0; c < 3; ++c) h.c[s][c] = f * h.c[s][c];
       face_store<T>(a, blk, 2 * mu, face_index(g, y, mu), h);
     }
-    if (y[mu] == g.b[mu] - 1) {  // to y = x + mu: 1/2 eta_mu(x) U_mu(x)^+ (1 + g) chi, projected
-      const T f = T(0.5) * ((n[mu] == g.nb[mu] - 1) ? (T)g.bc[mu] : T(1));
+    if (ymu == g.b[mu] - 1) {  // to y = x + mu: 1/2 eta_mu(x) U_mu(x)^+ (1 + g) chi, projected
+      const T f = T(0.5) * ((nmu == g.nb[mu] - 1) ? (T)g.bc[mu] : T(1));
       Half<T> w = udmul(st.link(r, mu), project_rt<+1>(chi, d));
 #pragma unroll
       for (int s = 0; s < 2; ++s)
@@ -407,7 +588,7 @@ struct StageFor<P64> {
 };
 
 template <int P, typename T>
-__global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
+__global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   typedef typename StageFor<P>::type ST;
   constexpr bool kHalf = (P == P16 || P == PB16);
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -466,13 +647,15 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
     }
   }
 
-  // thread i owns even site i and odd site Vbh + i; threads i >= Vbh (only
-  // when a block has fewer than 64 sites) take part in barriers and sums only
-  const int i = threadIdx.x;
+  // thread pair i owns even site i and odd site Vbh + i, half hf of their
+  // spin components and the hops in directions 2 hf, 2 hf + 1.  Pairs with
+  // i >= Vbh (only for blocks of fewer than 32 sites) compute on site 0 and
+  // store nothing, so that every lane takes part in the shuffles.
+  const int i = threadIdx.x >> 1, hf = threadIdx.x & 1;
   const bool act = i < Vbh;
-  const int re = act ? i : 0, ro = act ? Vbh + i : Vbh;
+  const int re = act ? i : 0, ro = Vbh + re;
 
-  // ---- in-block neighbour tables of the two owned sites (while the copies fly)
+  // ---- in-block neighbour tables of the two sites, own directions only
   int ye[4], yo[4];
   {
     const int pe = __ldg(g.r2y + re), po = __ldg(g.r2y + ro);
@@ -482,11 +665,11 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
       yo[mu] = ycoord(po, mu);
     }
   }
-  // even site: indices into the odd vector t (site - Vbh); odd site: into r (= site)
-  int pke[4], pko[4];
+  int pkE[2], pkO[2];  // even site: indices into t (site - Vbh); odd site: into r (= site)
   {
     const int je = ye[0] * g.ystr[0] + ye[1] * g.ystr[1] + ye[2] * g.ystr[2] + ye[3] * g.ystr[3];
     const int jo = yo[0] * g.ystr[0] + yo[1] * g.ystr[1] + yo[2] * g.ystr[2] + yo[3] * g.ystr[3];
+    int pke[4], pko[4];
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       const int ef = ye[mu] + 1 < g.b[mu] ? __ldg(g.j2r + je + g.ystr[mu]) - Vbh : 0xffff;
@@ -496,28 +679,32 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
       pke[mu] = ef | (eb << 16);
       pko[mu] = of | (ob << 16);
     }
+    pkE[0] = hf ? pke[2] : pke[0];
+    pkE[1] = hf ? pke[3] : pke[1];
+    pkO[0] = hf ? pko[2] : pko[0];
+    pkO[1] = hf ? pko[3] : pko[1];
   }
 
-  // ---- residual of the two sites
-  Spinor<T> rho_e, rho_o;
-  zero(rho_e);
-  zero(rho_o);
-  if (act) {
+  // ---- residual of the two sites (own halves)
+  Half<T> rho_e, rho_o;
+  {
+    Spinor<T> fe, fo;
     if (a.read_eta) {
-      Spinor<double> d = load_spinor<P64, double>(a.eta, Vb, blk, re);
+      const Spinor<double> de = load_spinor<P64, double>(a.eta, Vb, blk, re);
+      const Spinor<double> dd = load_spinor<P64, double>(a.eta, Vb, blk, ro);
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) rho_e.c[s][c] = {(T)d.c[s][c].re, (T)d.c[s][c].im};
-      d = load_spinor<P64, double>(a.eta, Vb, blk, ro);
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) rho_o.c[s][c] = {(T)d.c[s][c].re, (T)d.c[s][c].im};
+        for (int c = 0; c < 3; ++c) {
+          fe.c[s][c] = {(T)de.c[s][c].re, (T)de.c[s][c].im};
+          fo.c[s][c] = {(T)dd.c[s][c].re, (T)dd.c[s][c].im};
+        }
     } else {
-      rho_e = load_spinor<P, T>(a.rho, Vb, blk, re);
-      rho_o = load_spinor<P, T>(a.rho, Vb, blk, ro);
+      fe = load_spinor<P, T>(a.rho, Vb, blk, re);
+      fo = load_spinor<P, T>(a.rho, Vb, blk, ro);
     }
+    rho_e = half_of(fe, hf);
+    rho_o = half_of(fo, hf);
   }
   if constexpr (kHalf) {
     // every thread waits (bounded) for the staging copies; a time-out is made
@@ -531,27 +718,23 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
   } else {
     __syncthreads();
   }
+  if (a.faces_in) {
+    rho_e = half_axpy(rho_e, pair_reduce(receive_faces<T>(a, st, blk, re, ye, n, hf), hf), T(1));
+    rho_o = half_axpy(rho_o, pair_reduce(receive_faces<T>(a, st, blk, ro, yo, n, hf), hf), T(1));
+  }
   if (act) {
-    if (a.faces_in) {
-      receive_faces<T>(a, st, blk, re, ye, n, rho_e);
-      receive_faces<T>(a, st, blk, ro, yo, n, rho_o);
-    }
-    s_spinor_store(s_rho_o, Vbh, i, rho_o);
+    s_half_store(s_rho_o, Vbh, i, hf, rho_o);
     // etahat = rho_e - D_eo A_oo^-1 rho_o: first t = A_oo^-1 rho_o
-    s_spinor_store(s_t, Vbh, i, st.clover(ro, rho_o));
+    s_half_store(s_t, Vbh, i, hf, clover_half(st, ro, hf, rho_o));
   }
   __syncthreads();
-  Spinor<T> r, x;
-  zero(r);
-  zero(x);
-  if (act) {
-    const Spinor<T> q = hops<T>(st, Vbh, re, s_t, pke, Vbh);
+  Half<T> r = half_axpy(rho_e, block_hops<T>(st, Vbh, re, s_t, pkE, Vbh, hf), T(-1));
+  Half<T> x;
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+  for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) r.c[s][c] = rho_e.c[s][c] - q.c[s][c];
-    s_spinor_store(s_r, Vbh, i, r);
-  }
+    for (int c = 0; c < 3; ++c) x.c[s][c] = {T(0), T(0)};
+  if (act) s_half_store(s_r, Vbh, i, hf, r);
   __syncthreads();
 
   // ---- MR on Dhat = A_ee - D_eo A_oo^-1 D_oe, x_e = 0, r = etahat.  Each
@@ -560,101 +743,83 @@ __global__ void __launch_bounds__(256) sap_sweep_kernel(SapArgs a) {
 #pragma unroll 1
   for (int step = 0; step < 2 * a.nmr; ++step) {
     const int ph = step & 1;
-    Spinor<T> p;
-    zero(p);
-    if (act) {
-      const Spinor<T> hq = ph ? hops<T>(st, Vbh, re, s_t, pke, Vbh) : hops<T>(st, Vbh, ro, s_r, pko, 0);
-      const Spinor<T> cl = st.clover(ph ? re : ro, ph ? r : hq);
-      if (ph == 0) {
-        s_spinor_store(s_t, Vbh, i, cl);
-      } else {
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) p.c[s][c] = cl.c[s][c] - hq.c[s][c];
-      }
-    }
+    const int pk2[2] = {ph ? pkE[0] : pkO[0], ph ? pkE[1] : pkO[1]};
+    const Half<T> hq = block_hops<T>(st, Vbh, ph ? re : ro, ph ? s_t : s_r, pk2, ph ? Vbh : 0, hf);
+    const Half<T> cl = clover_half(st, ph ? re : ro, hf, ph ? r : hq);
     if (ph == 0) {
+      if (act) s_half_store(s_t, Vbh, i, hf, cl);
       __syncthreads();
       continue;
     }
+    const Half<T> p = half_axpy(cl, hq, T(-1));
     T pr_re = 0, pr_im = 0, pp = 0;
+    if (act) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+      for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const cpx<T> v = p.c[s][c], w = r.c[s][c];
-        pr_re += v.re * w.re + v.im * w.im;
-        pr_im += v.re * w.im - v.im * w.re;
-        pp += v.re * v.re + v.im * v.im;
-      }
+        for (int c = 0; c < 3; ++c) {
+          const cpx<T> v = p.c[s][c], w = r.c[s][c];
+          pr_re += v.re * w.re + v.im * w.im;
+          pr_im += v.re * w.im - v.im * w.re;
+          pp += v.re * v.re + v.im * v.im;
+        }
+    }
     cta_sum3(pr_re, pr_im, pp, s_red);
     const T inv = pp > T(0) ? T(1) / pp : T(0);
     const cpx<T> alpha = {pr_re * inv, pr_im * inv};
-    if (act) {
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          x.c[s][c] = cmadd(alpha, r.c[s][c], x.c[s][c]);
-          r.c[s][c] = r.c[s][c] - cmul(alpha, p.c[s][c]);
-        }
-      s_spinor_store(s_r, Vbh, i, r);
-    }
+      for (int c = 0; c < 3; ++c) {
+        x.c[s][c] = cmadd(alpha, r.c[s][c], x.c[s][c]);
+        r.c[s][c] = r.c[s][c] - cmul(alpha, p.c[s][c]);
+      }
+    if (act) s_half_store(s_r, Vbh, i, hf, r);
     __syncthreads();
   }
 
   // ---- chi_o = A_oo^-1 (rho_o - D_oe chi_e)
-  if (act) s_spinor_store(s_r, Vbh, i, x);
+  if (act) s_half_store(s_r, Vbh, i, hf, x);
   __syncthreads();
-  if (!act) return;
-  Spinor<T> chi_o;
-  {
-    Spinor<T> u = hops<T>(st, Vbh, ro, s_r, pko, 0);
-    const Spinor<T> src = s_spinor(s_rho_o, Vbh, i);
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) u.c[s][c] = src.c[s][c] - u.c[s][c];
-    chi_o = st.clover(ro, u);
-  }
+  const Half<T> chi_o = clover_half(st, ro, hf, half_axpy(rho_o, block_hops<T>(st, Vbh, ro, s_r, pkO, 0, hf), T(-1)));
 
   // ---- outputs: solution, block residual (r on even, 0 on odd), faces
   constexpr int PS = PsiPrec<P>::value;
   typedef typename std::conditional<PS == P64, double, float>::type TS;
+  const Spinor<T> x_full = pair_full(x, hf);
+  const Spinor<T> chio_full = pair_full(chi_o, hf);
+  const Spinor<T> r_full = pair_full(r, hf);
+  if (!act) return;
 #pragma unroll 1
   for (int half = 0; half < 2; ++half) {
     const int rs = half ? ro : re;
-    const Spinor<T>& chi = half ? chi_o : x;
-    Spinor<TS> v;
+    const Half<T>& chi = half ? chi_o : x;
+    Half<TS> v;
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < 2; ++s)
 #pragma unroll
       for (int c = 0; c < 3; ++c) v.c[s][c] = {(TS)chi.c[s][c].re, (TS)chi.c[s][c].im};
-    if (a.psi_mode == 1 || a.psi_mode == 3) {
-      Spinor<TS> old = load_spinor<PS, TS>(a.psi, Vb, blk, rs);
-      add_spinor(v, old, TS(1));
-    }
+    if (a.psi_mode == 1 || a.psi_mode == 3) v = half_axpy(v, g_half<PS, TS>(a.psi, Vb, blk, rs, hf), TS(1));
     if (a.psi_mode <= 1) {
-      store_spinor<PS, TS>(a.psi, Vb, blk, rs, v);
+      g_half_store<PS, TS>(a.psi, Vb, blk, rs, hf, v);
     } else {
-      Spinor<double> dv;
+      Half<double> dv;
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+      for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) dv.c[s][c] = {(double)v.c[s][c].re, (double)v.c[s][c].im};
-      store_spinor<P64, double>(a.out, Vb, blk, rs, dv);
+      g_half_store<P64, double>(a.out, Vb, blk, rs, hf, dv);
     }
   }
-  if (a.write_rho) {
-    store_spinor<P, T>(a.rho, Vb, blk, re, r);
+  if (a.write_rho && hf == 0) {
+    store_spinor<P, T>(a.rho, Vb, blk, re, r_full);
     Spinor<T> z;
     zero(z);
     store_spinor<P, T>(a.rho, Vb, blk, ro, z);
   }
   if (a.faces_out) {
-    send_faces<T>(a, st, blk, re, ye, n, x);
-    send_faces<T>(a, st, blk, ro, yo, n, chi_o);
+    send_faces<T>(a, st, blk, re, ye, n, x_full, hf);
+    send_faces<T>(a, st, blk, ro, yo, n, chio_full, hf);
   }
 }
 
@@ -665,43 +830,59 @@ static size_t sap_smem_bytes(const Geom& g) {
 }
 
 template <int P, typename T>
-static int launch_sweep(const SapArgs& a, unsigned grid, int threads, cudaStream_t s, int maxsm) {
-  const size_t smem = sap_smem_bytes<P, T>(a.g);
+static int set_smem_attr(const Geom& g, int maxsm) {
+  const size_t smem = sap_smem_bytes<P, T>(g);
   if (smem > (size_t)maxsm) return QCD_ERR_UNSUPPORTED;
   QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sap_sweep_kernel<P, T><<<grid, threads, smem, s>>>(a);
   return QCD_OK;
 }
 
-static int sap_apply_impl(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec,
-                          cudaStream_t s) {
+// allocate the SAP work fields and set the kernel's shared-memory limit for
+// this geometry (outside any stream capture)
+int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s) {
   const Geom& g = c->g;
-  if (eta64.prec != P64 || psi64.prec != P64) return QCD_ERR_ARG;
-  if (ncy < 1 || nmr < 0) return QCD_ERR_ARG;
+  if (prec < P64 || prec > PB16) return QCD_ERR_ARG;
   if (g.Vbh > 256) return QCD_ERR_UNSUPPORTED;
   QCD_TRY(ensure_gauge(c, prec, s));
   QCD_TRY(ensure_clover(c, prec, s));
-  const bool dbl = prec == P64;
   int dev = 0, maxsm = 0;
   QCD_CUDA(cudaGetDevice(&dev));
   QCD_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // work fields
-  if (w.prec != prec) {
-    rec_free(w.rho);
-    rec_free(w.psi);
-    if (w.faces) cudaFree(w.faces);
-    w.faces = nullptr;
-    QCD_TRY(rec_alloc(w.rho, prec, 24, c->V));
-    QCD_TRY(rec_alloc(w.psi, dbl ? P64 : P32, 24, c->V));
-    int F = 0;
-    for (int mu = 0; mu < 4; ++mu) F += 2 * (g.Vb / g.b[mu]);
-    w.faces_bytes = (size_t)c->nblk * F * 12 * (dbl ? 8 : 4);
-    if (cudaMalloc(&w.faces, w.faces_bytes) != cudaSuccess) {
-      w.faces = nullptr;
-      return QCD_ERR_NOMEM;
-    }
-    w.prec = prec;
+  switch (prec) {
+    case P64: QCD_TRY((set_smem_attr<P64, double>(g, maxsm))); break;
+    case P32: QCD_TRY((set_smem_attr<P32, float>(g, maxsm))); break;
+    case P16: QCD_TRY((set_smem_attr<P16, float>(g, maxsm))); break;
+    default: QCD_TRY((set_smem_attr<PB16, float>(g, maxsm))); break;
   }
+  if (w.prec == prec) return QCD_OK;
+  const bool dbl = prec == P64;
+  rec_free(w.rho);
+  rec_free(w.psi);
+  if (w.faces) cudaFree(w.faces);
+  w.faces = nullptr;
+  w.prec = -1;
+  QCD_TRY(rec_alloc(w.rho, prec, 24, c->V));
+  QCD_TRY(rec_alloc(w.psi, dbl ? P64 : P32, 24, c->V));
+  int F = 0;
+  for (int mu = 0; mu < 4; ++mu) F += 2 * (g.Vb / g.b[mu]);
+  w.faces_bytes = (size_t)c->nblk * F * 12 * (dbl ? 8 : 4);
+  if (cudaMalloc(&w.faces, w.faces_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    w.faces = nullptr;
+    return QCD_ERR_NOMEM;
+  }
+  w.prec = prec;
+  return QCD_OK;
+}
+
+// psi64 = M_SAP eta64; allocates nothing once sap_prepare ran for prec
+int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec,
+              cudaStream_t s) {
+  const Geom& g = c->g;
+  if (eta64.prec != P64 || psi64.prec != P64) return QCD_ERR_ARG;
+  if (ncy < 1 || nmr < 0) return QCD_ERR_ARG;
+  if (w.prec != prec) QCD_TRY(sap_prepare(c, w, prec, s));
+  const bool dbl = prec == P64;
   SapArgs a;
   a.g = g;
   a.nmr = nmr;
@@ -722,7 +903,7 @@ static int sap_apply_impl(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& p
   }
   a.F = off;
   const unsigned grid = (unsigned)(c->nblk / 2);
-  const int threads = g.Vbh < 32 ? 32 : ((g.Vbh + 31) / 32) * 32;
+  const int threads = 2 * g.Vbh < 32 ? 32 : ((2 * g.Vbh + 31) / 32) * 32;  // two threads per site pair
   // flops (the 1320 + 504 convention): per solved site the Schur operator
   // costs about one D per MR step, plus about one more D for the source and
   // the back-substitution
@@ -740,24 +921,16 @@ static int sap_apply_impl(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& p
       a.write_rho = !last;
       a.psi_mode = last ? (cy == 0 ? 2 : 3) : (cy == 0 ? 0 : 1);
       ProfScope ps(c, QCD_KERNEL_SAP, s, bytes, flops);
-      int st;
       switch (prec) {
-        case P64: st = launch_sweep<P64, double>(a, grid, threads, s, maxsm); break;
-        case P32: st = launch_sweep<P32, float>(a, grid, threads, s, maxsm); break;
-        case P16: st = launch_sweep<P16, float>(a, grid, threads, s, maxsm); break;
-        case PB16: st = launch_sweep<PB16, float>(a, grid, threads, s, maxsm); break;
+        case P64: sap_sweep_kernel<P64, double><<<grid, threads, sap_smem_bytes<P64, double>(g), s>>>(a); break;
+        case P32: sap_sweep_kernel<P32, float><<<grid, threads, sap_smem_bytes<P32, float>(g), s>>>(a); break;
+        case P16: sap_sweep_kernel<P16, float><<<grid, threads, sap_smem_bytes<P16, float>(g), s>>>(a); break;
+        case PB16: sap_sweep_kernel<PB16, float><<<grid, threads, sap_smem_bytes<PB16, float>(g), s>>>(a); break;
         default: return QCD_ERR_ARG;
       }
-      if (st != QCD_OK) return st;
       QCD_LAUNCHED();
     }
   return QCD_OK;
-}
-
-int sap_apply(qcd_ctx* c, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec, cudaStream_t s) {
-  Workspace* ws = ensure_ws(c);
-  if (!ws) return QCD_ERR_NOMEM;
-  return sap_apply_impl(c, ws->sap, eta64, psi64, ncy, nmr, prec, s);
 }
 
 }  // namespace qcd

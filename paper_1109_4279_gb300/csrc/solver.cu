@@ -12,6 +12,13 @@
 // the device, x += sum_k gamma_k phi_k, and r = b - D x is recomputed in FP64
 // ("only when the FGCR recursion is restarted, the residue is computed in
 // full double precision", Sec. 4).
+//
+// Many right-hand sides or lattices (Sec. 4: flexibility in the lattice
+// sizes) are solved in lock step: every iteration is enqueued for all active
+// problems, each on its own stream and workspace, so their kernels run
+// concurrently, and one host synchronisation per iteration reads all the
+// recursive residuals.  With use_graphs each problem's iteration k is captured
+// once as a CUDA graph and replayed (one launch instead of ~20).
 #include <cmath>
 #include <cstring>
 
@@ -19,9 +26,23 @@
 
 namespace qcd {
 
-static int ws_reserve(qcd_ctx* c, Workspace& w, int nkv) {
+size_t partials_for(long long V) {
+  const size_t blas = (size_t)152 * 8 * 65;     // largest BLAS grid x widest record
+  const size_t resid = (size_t)(V + 255) / 256;  // one partial per residual CTA
+  return blas > resid ? blas : resid;
+}
+
+int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream_t s) {
+  const int nkv = sp.nkv;
   for (Rec* f : {&w.b, &w.x, &w.r, &w.rho})
     if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
+  if (!w.d_part) {
+    if (cudaMalloc(&w.d_part, sizeof(double) * partials_for(c->V)) != cudaSuccess) {
+      cudaGetLastError();
+      w.d_part = nullptr;
+      return QCD_ERR_NOMEM;
+    }
+  }
   if (nkv > w.nkv) {
     for (int k = w.nkv; k < nkv; ++k) {
       w.phi.emplace_back();
@@ -35,7 +56,8 @@ static int ws_reserve(qcd_ctx* c, Workspace& w, int nkv) {
     cudaFree(w.d_rn);
     cudaFree(w.d_gam);
     cudaFree(w.d_gs);
-    cudaFreeHost(w.h_pin);
+    if (w.h_pin) cudaFreeHost(w.h_pin);
+    w.d_a1 = w.d_a2 = w.d_cr = w.d_rn = w.d_gam = w.d_gs = w.h_pin = nullptr;
     QCD_CUDA(cudaMalloc(&w.d_a1, sizeof(double) * 2 * nkv * nkv));
     QCD_CUDA(cudaMalloc(&w.d_a2, sizeof(double) * 2 * nkv * nkv));
     QCD_CUDA(cudaMalloc(&w.d_cr, sizeof(double) * 3 * nkv));
@@ -45,160 +67,335 @@ static int ws_reserve(qcd_ctx* c, Workspace& w, int nkv) {
     QCD_CUDA(cudaMallocHost(&w.h_pin, sizeof(double) * (nkv + 8)));
     w.nkv = nkv;
   }
+  QCD_TRY(ensure_gauge(c, P64, s));
+  QCD_TRY(ensure_clover(c, P64, s));
+  if (sp.outer_prec != P64) {
+    QCD_TRY(ensure_gauge(c, sp.outer_prec, s));
+    QCD_TRY(ensure_clover(c, sp.outer_prec, s));
+    if (w.lo_in.prec != sp.outer_prec) {
+      rec_free(w.lo_in);
+      rec_free(w.lo_out);
+      QCD_TRY(rec_alloc(w.lo_in, sp.outer_prec, 24, c->V));
+      QCD_TRY(rec_alloc(w.lo_out, sp.outer_prec, 24, c->V));
+    }
+  }
+  if (sp.precond == QCD_PRECOND_SAP) QCD_TRY(sap_prepare(c, w.sap, sp.sap_prec, s));
   return QCD_OK;
 }
 
-// read one device double back (synchronises the stream)
-static int read_scalar(Workspace& w, const double* d, double* h, cudaStream_t s) {
-  QCD_CUDA(cudaMemcpyAsync(w.h_pin, d, sizeof(double), cudaMemcpyDeviceToHost, s));
-  QCD_CUDA(cudaStreamSynchronize(s));
-  *h = w.h_pin[0];
-  return QCD_OK;
+static void graphs_clear(Workspace& w) {
+  for (auto g : w.graphs)
+    if (g) cudaGraphExecDestroy(g);
+  w.graphs.clear();
+  w.graph_key = -1;
+}
+
+void ws_release(Workspace& w) {
+  graphs_clear(w);
+  rec_free(w.sap.rho);
+  rec_free(w.sap.psi);
+  if (w.sap.faces) cudaFree(w.sap.faces);
+  w.sap.faces = nullptr;
+  w.sap.prec = -1;
+  for (Rec* f : {&w.b, &w.x, &w.r, &w.rho, &w.tmp64, &w.lo_in, &w.lo_out}) rec_free(*f);
+  for (auto& r : w.phi) rec_free(r);
+  for (auto& r : w.chi) rec_free(r);
+  w.phi.clear();
+  w.chi.clear();
+  for (double** p : {&w.d_a1, &w.d_a2, &w.d_cr, &w.d_rn, &w.d_gam, &w.d_gs, &w.d_part}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  if (w.h_pin) cudaFreeHost(w.h_pin);
+  w.h_pin = nullptr;
+  w.nkv = 0;
 }
 
 // chi = D phi in the requested outer precision (FP64 default)
 static int outer_apply(qcd_ctx* c, Workspace& w, const Rec& phi, const Rec& chi, int prec, cudaStream_t s) {
   if (prec == P64) return dirac_apply(c, phi, chi, 0, s);
-  if (w.lo_in.prec != prec) {
-    rec_free(w.lo_in);
-    rec_free(w.lo_out);
-    QCD_TRY(rec_alloc(w.lo_in, prec, 24, c->V));
-    QCD_TRY(rec_alloc(w.lo_out, prec, 24, c->V));
-  }
   QCD_TRY(convert_rec(c, phi, w.lo_in, s));
   QCD_TRY(dirac_apply(c, w.lo_in, w.lo_out, 0, s));
   return convert_rec(c, w.lo_out, chi, s);
 }
 
+// enqueue FGCR iteration k of one problem; ends with a copy of |rho_{k+1}|^2
+// to w.h_pin[k] (pinned host memory)
+static int enqueue_iteration(Problem& p, const qcd_solver_params& sp, int k) {
+  qcd_ctx* c = p.c;
+  Workspace& w = *p.w;
+  cudaStream_t s = p.s;
+  const size_t bytes = (size_t)c->V * 24 * sizeof(double);
+  if (sp.precond == QCD_PRECOND_SAP) {
+    QCD_TRY(sap_apply(c, w.sap, w.rho, w.phi[k], sp.ncy, sp.nmr, sp.sap_prec, s));
+  } else {
+    QCD_CUDA(cudaMemcpyAsync(w.phi[k].data, w.rho.data, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  QCD_TRY(outer_apply(c, w, w.phi[k], w.chi[k], sp.outer_prec, s));
+  const double* chi_p[64];
+  for (int j = 0; j < k; ++j) chi_p[j] = (const double*)w.chi[j].data;
+  double* chik = (double*)w.chi[k].data;
+  double* a1 = w.d_a1 + 2 * (size_t)k * sp.nkv;
+  double* a2 = w.d_a2 + 2 * (size_t)k * sp.nkv;
+  // classical Gram-Schmidt; the second pass runs (decided on the device) only
+  // if the first one cancelled more than half of the squared norm
+  double* gs = w.d_gs + 8 * (size_t)k;
+  const double* rho_p = (const double*)w.rho.data;
+  QCD_TRY(blas_multidot(c, w.d_part, chi_p, k, chik, a1, s, nullptr, gs));
+  QCD_TRY(blas_axpy_norm_dot(c, w.d_part, chi_p, k, a1, chik, rho_p, gs + 1, s));
+  if (k > 0) {
+    QCD_TRY(blas_multidot(c, w.d_part, chi_p, k, chik, a2, s, gs));
+    QCD_TRY(blas_axpy_norm_dot(c, w.d_part, chi_p, k, a2, chik, rho_p, gs + 4, s, gs));
+  }
+  QCD_TRY(blas_normalise_update(c, w.d_part, chik, (double*)w.rho.data, gs, k > 0, w.d_cr + 3 * k, w.d_rn + k, s));
+  QCD_CUDA(cudaMemcpyAsync(w.h_pin + k, w.d_rn + k, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return QCD_OK;
+}
+
+static long long graph_key(const qcd_solver_params& sp) {
+  return ((((long long)sp.nkv * 8 + sp.precond) * 64 + sp.ncy) * 64 + sp.nmr) * 16 + sp.sap_prec * 4 + sp.outer_prec;
+}
+
+// enqueue iteration k, from a captured graph when requested
+static int launch_iteration(Problem& p, const qcd_solver_params& sp, int k, bool use_graphs) {
+  if (!use_graphs) return enqueue_iteration(p, sp, k);
+  Workspace& w = *p.w;
+  const long long key = graph_key(sp);
+  if (w.graph_key != key) {
+    graphs_clear(w);
+    w.graphs.assign(sp.nkv, nullptr);
+    w.graph_key = key;
+  }
+  if (!w.graphs[k]) {
+    cudaGraph_t g = nullptr;
+    QCD_CUDA(cudaStreamBeginCapture(p.s, cudaStreamCaptureModeThreadLocal));
+    int st = enqueue_iteration(p, sp, k);
+    cudaError_t e = cudaStreamEndCapture(p.s, &g);
+    if (st != QCD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&w.graphs[k], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      w.graphs[k] = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+  }
+  QCD_CUDA(cudaGraphLaunch(w.graphs[k], p.s));
+  return QCD_OK;
+}
+
+static int sync_all(std::vector<Problem>& probs) {
+  for (auto& p : probs)
+    if (p.active) QCD_CUDA(cudaStreamSynchronize(p.s));
+  return QCD_OK;
+}
+
+int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool use_graphs) {
+  if (sp.nkv < 1 || sp.nkv > 64 || !(sp.tol > 0) || sp.max_restarts < 1) return QCD_ERR_ARG;
+  if (sp.precond != QCD_PRECOND_NONE && sp.precond != QCD_PRECOND_SAP) return QCD_ERR_ARG;
+  if (sp.outer_prec != P64 && sp.outer_prec != P32) return QCD_ERR_ARG;
+  if (sp.precond == QCD_PRECOND_SAP && (sp.ncy < 1 || sp.nmr < 0 || sp.sap_prec < P64 || sp.sap_prec > PB16))
+    return QCD_ERR_ARG;
+  const size_t bytes_of = sizeof(double);
+  for (auto& p : probs) {
+    memset(&p.info, 0, sizeof(p.info));
+    p.active = true;
+    p.status = QCD_OK;
+    if (!p.c->clover_built) {
+      p.status = QCD_ERR_STATE;
+      p.active = false;
+      continue;
+    }
+    int st = ws_prepare(p.c, *p.w, sp, p.s);
+    // clear the SAP staging time-out flag of the context
+    if (st == QCD_OK && cudaMemsetAsync(p.c->d_scalars + 128, 0, sizeof(double), p.s) != cudaSuccess)
+      st = QCD_ERR_CUDA;
+    if (st != QCD_OK) {
+      p.status = st;
+      p.active = false;
+    }
+  }
+  // |b|, r = b - D x0
+  for (auto& p : probs) {
+    if (!p.active) continue;
+    Workspace& w = *p.w;
+    int st = blas_norm2(p.c, w.d_part, (const double*)p.b.data, w.d_rn + w.nkv, p.s);
+    if (st == QCD_OK) st = residual64(p.c, w.d_part, p.b, p.x, w.r, w.d_rn + w.nkv + 1, p.s);
+    if (st == QCD_OK && cudaMemcpyAsync(w.h_pin + w.nkv, w.d_rn + w.nkv, 2 * bytes_of, cudaMemcpyDeviceToHost,
+                                        p.s) != cudaSuccess)
+      st = QCD_ERR_CUDA;
+    if (st != QCD_OK) {
+      p.status = st;
+      p.active = false;
+    }
+  }
+  QCD_TRY(sync_all(probs));
+  for (auto& p : probs) {
+    if (!p.active) continue;
+    Workspace& w = *p.w;
+    const double bn2 = w.h_pin[w.nkv], rn2 = w.h_pin[w.nkv + 1];
+    if (!(bn2 == bn2) || std::isinf(bn2) || !(rn2 == rn2)) {
+      p.status = QCD_NAN;
+      p.active = false;
+      continue;
+    }
+    if (bn2 == 0.0) {  // b = 0: x = 0
+      if (cudaMemsetAsync(p.x.data, 0, (size_t)p.c->V * 24 * sizeof(double), p.s) != cudaSuccess)
+        p.status = QCD_ERR_CUDA;
+      p.active = false;
+      continue;
+    }
+    p.bn = std::sqrt(bn2);
+    p.rn = std::sqrt(rn2);
+    p.info.true_residual = p.rn / p.bn;
+    p.slow = 0;
+    if (p.rn <= sp.tol * p.bn) p.active = false;
+  }
+  // restart cycles
+  for (;;) {
+    bool any = false;
+    for (auto& p : probs) {
+      if (p.active && p.info.restarts >= sp.max_restarts) {
+        p.status = QCD_NOT_CONVERGED;
+        p.active = false;
+      }
+      any |= p.active;
+    }
+    if (!any) break;
+    for (auto& p : probs) {
+      if (!p.active) continue;
+      p.kused = 0;
+      p.cycle_done = false;
+      if (cudaMemcpyAsync(p.w->rho.data, p.w->r.data, (size_t)p.c->V * 24 * sizeof(double), cudaMemcpyDeviceToDevice,
+                          p.s) != cudaSuccess) {
+        p.status = QCD_ERR_CUDA;
+        p.active = false;
+      }
+    }
+    for (int k = 0; k < sp.nkv; ++k) {
+      bool launched = false;
+      for (auto& p : probs) {
+        if (!p.active || p.cycle_done) continue;
+        int st = launch_iteration(p, sp, k, use_graphs);
+        if (st != QCD_OK) {
+          p.status = st;
+          p.active = false;
+          continue;
+        }
+        launched = true;
+      }
+      if (!launched) break;
+      QCD_TRY(sync_all(probs));
+      for (auto& p : probs) {
+        if (!p.active || p.cycle_done) continue;
+        const double rk2 = p.w->h_pin[k];
+        ++p.info.iterations;
+        p.kused = k + 1;
+        if (!(rk2 == rk2)) {
+          p.status = QCD_NAN;
+          p.active = false;
+          continue;
+        }
+        if (std::sqrt(rk2) <= sp.tol * p.bn) p.cycle_done = true;
+      }
+    }
+    // x += sum gamma_k phi_k; r = b - D x (FP64)
+    for (auto& p : probs) {
+      if (!p.active || p.kused == 0) continue;
+      Workspace& w = *p.w;
+      const double* phi_p[64];
+      for (int j = 0; j < p.kused; ++j) phi_p[j] = (const double*)w.phi[j].data;
+      int st = fgcr_backsub(w.d_a1, w.d_a2, w.d_cr, p.kused, sp.nkv, w.d_gam, p.s);
+      if (st == QCD_OK) st = blas_multi_axpy(p.c, phi_p, p.kused, w.d_gam, (double*)p.x.data, p.s);
+      if (st == QCD_OK) st = residual64(p.c, w.d_part, p.b, p.x, w.r, w.d_rn + w.nkv + 2, p.s);
+      if (st == QCD_OK && cudaMemcpyAsync(w.h_pin + w.nkv + 2, w.d_rn + w.nkv + 2, bytes_of, cudaMemcpyDeviceToHost,
+                                          p.s) != cudaSuccess)
+        st = QCD_ERR_CUDA;
+      if (st == QCD_OK && cudaMemcpyAsync(w.h_pin + w.nkv + 3, (const double*)(p.c->d_scalars + 128), bytes_of,
+                                          cudaMemcpyDeviceToHost, p.s) != cudaSuccess)
+        st = QCD_ERR_CUDA;
+      if (st != QCD_OK) {
+        p.status = st;
+        p.active = false;
+      }
+    }
+    QCD_TRY(sync_all(probs));
+    for (auto& p : probs) {
+      if (!p.active) continue;
+      Workspace& w = *p.w;
+      ++p.info.restarts;
+      int sap_err = 0;
+      memcpy(&sap_err, w.h_pin + w.nkv + 3, sizeof(int));
+      if (sap_err) {
+        p.status = QCD_ERR_TIMEOUT;
+        p.active = false;
+        continue;
+      }
+      const double nrn = std::sqrt(w.h_pin[w.nkv + 2]);
+      if (!(nrn == nrn)) {
+        p.status = QCD_NAN;
+        p.active = false;
+        continue;
+      }
+      p.slow = nrn > 0.999 * p.rn ? p.slow + 1 : 0;
+      p.rn = nrn;
+      p.info.true_residual = nrn / p.bn;
+      if (nrn <= sp.tol * p.bn) {
+        p.active = false;
+      } else if (p.slow >= 3) {
+        p.status = QCD_STAGNATED;
+        p.active = false;
+      }
+    }
+  }
+  int first = QCD_OK;
+  for (auto& p : probs) {
+    p.info.status = p.status;
+    if (p.status != QCD_OK && first == QCD_OK) first = p.status;
+  }
+  return first;
+}
+
 int solve_one(qcd_ctx* c, const Rec& b, const Rec& x, const qcd_solver_params& sp, qcd_solve_info* info,
               cudaStream_t s) {
-  qcd_solve_info inf;
-  memset(&inf, 0, sizeof(inf));
-  auto finish = [&](int st) {
-    inf.status = st;
-    if (info) *info = inf;
-    return st;
-  };
-  if (!c->clover_built) return finish(QCD_ERR_STATE);
-  if (sp.nkv < 1 || sp.nkv > 64 || sp.tol <= 0 || sp.max_restarts < 1) return finish(QCD_ERR_ARG);
-  if (sp.precond != QCD_PRECOND_NONE && sp.precond != QCD_PRECOND_SAP) return finish(QCD_ERR_ARG);
-  if (sp.outer_prec != P64 && sp.outer_prec != P32) return finish(QCD_ERR_ARG);
-  Workspace* wp = ensure_ws(c);
-  if (!wp) return finish(QCD_ERR_NOMEM);
-  Workspace& w = *wp;
-  int st = ws_reserve(c, w, sp.nkv);
-  if (st) return finish(st);
-
+  Workspace* w = ensure_ws(c);
+  if (!w) return QCD_ERR_NOMEM;
+  std::vector<Problem> probs(1);
+  probs[0].c = c;
+  probs[0].w = w;
+  probs[0].s = s;
+  probs[0].b = b;
+  probs[0].x = x;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-
-  auto run = [&]() -> int {
-    const size_t bytes = (size_t)c->V * 24 * sizeof(double);
-    double bn2 = 0, rn2 = 0;
-    QCD_TRY(blas_norm2(c, (const double*)b.data, w.d_rn, s));
-    QCD_TRY(read_scalar(w, w.d_rn, &bn2, s));
-    if (!(bn2 == bn2) || std::isinf(bn2)) return QCD_NAN;
-    if (bn2 == 0.0) {
-      QCD_CUDA(cudaMemsetAsync(x.data, 0, bytes, s));
-      inf.true_residual = 0;
-      return QCD_OK;
-    }
-    const double bn = std::sqrt(bn2);
-    QCD_TRY(residual64(c, b, x, w.r, w.d_rn, s));
-    QCD_TRY(read_scalar(w, w.d_rn, &rn2, s));
-    double rn = std::sqrt(rn2);
-    inf.true_residual = rn / bn;
-    if (!(rn == rn)) return QCD_NAN;
-    int slow_cycles = 0;
-    std::vector<const double*> chi_p(sp.nkv), phi_p(sp.nkv);
-    for (int k = 0; k < sp.nkv; ++k) {
-      chi_p[k] = (const double*)w.chi[k].data;
-      phi_p[k] = (const double*)w.phi[k].data;
-    }
-    while (rn > sp.tol * bn && inf.restarts < sp.max_restarts) {
-      QCD_CUDA(cudaMemcpyAsync(w.rho.data, w.r.data, bytes, cudaMemcpyDeviceToDevice, s));
-      int kused = 0;
-      for (int k = 0; k < sp.nkv; ++k) {
-        if (sp.precond == QCD_PRECOND_SAP) {
-          QCD_TRY(sap_apply(c, w.rho, w.phi[k], sp.ncy, sp.nmr, sp.sap_prec, s));
-        } else {
-          QCD_CUDA(cudaMemcpyAsync(w.phi[k].data, w.rho.data, bytes, cudaMemcpyDeviceToDevice, s));
-        }
-        QCD_TRY(outer_apply(c, w, w.phi[k], w.chi[k], sp.outer_prec, s));
-        double* chik = (double*)w.chi[k].data;
-        double* a1 = w.d_a1 + 2 * (size_t)k * sp.nkv;
-        double* a2 = w.d_a2 + 2 * (size_t)k * sp.nkv;
-        // classical Gram-Schmidt; the second pass runs (decided on the device)
-        // only if the first one cancelled more than half of the squared norm
-        double* gs = w.d_gs + 8 * (size_t)k;
-        const double* rho_p = (const double*)w.rho.data;
-        QCD_TRY(blas_multidot(c, chi_p.data(), k, chik, a1, s, nullptr, gs));
-        QCD_TRY(blas_axpy_norm_dot(c, chi_p.data(), k, a1, chik, rho_p, gs + 1, s));
-        if (k > 0) {
-          QCD_TRY(blas_multidot(c, chi_p.data(), k, chik, a2, s, gs));
-          QCD_TRY(blas_axpy_norm_dot(c, chi_p.data(), k, a2, chik, rho_p, gs + 4, s, gs));
-        }
-        QCD_TRY(blas_normalise_update(c, chik, (double*)w.rho.data, gs, k > 0, w.d_cr + 3 * k, w.d_rn + k, s));
-        double rk2 = 0;
-        QCD_TRY(read_scalar(w, w.d_rn + k, &rk2, s));
-        ++inf.iterations;
-        kused = k + 1;
-        if (!(rk2 == rk2)) return QCD_NAN;
-        if (std::sqrt(rk2) <= sp.tol * bn) break;
-      }
-      if (kused == 0) break;
-      QCD_TRY(fgcr_backsub(w.d_a1, w.d_a2, w.d_cr, kused, sp.nkv, w.d_gam, s));
-      QCD_TRY(blas_multi_axpy(c, phi_p.data(), kused, w.d_gam, (double*)x.data, s));
-      QCD_TRY(residual64(c, b, x, w.r, w.d_rn + sp.nkv, s));
-      double nrn2 = 0;
-      QCD_TRY(read_scalar(w, w.d_rn + sp.nkv, &nrn2, s));
-      ++inf.restarts;
-      const double nrn = std::sqrt(nrn2);
-      if (!(nrn == nrn)) return QCD_NAN;
-      slow_cycles = nrn > 0.999 * rn ? slow_cycles + 1 : 0;
-      rn = nrn;
-      inf.true_residual = rn / bn;
-      if (slow_cycles >= 3 && rn > sp.tol * bn) return QCD_STAGNATED;
-    }
-    return rn <= sp.tol * bn ? QCD_OK : QCD_NOT_CONVERGED;
-  };
-  st = run();
+  int st = fgcr_batch(probs, sp, false);
   cudaEventRecord(e1, s);
   cudaEventSynchronize(e1);
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  inf.time_ms = ms;
-  return finish(st);
+  probs[0].info.time_ms = ms;
+  if (info) *info = probs[0].info;
+  return st;
 }
 
 void workspace_free(qcd_ctx* c) {
-  Workspace* w = c->ws;
-  if (!w) return;
-  rec_free(w->sap.rho);
-  rec_free(w->sap.psi);
-  if (w->sap.faces) cudaFree(w->sap.faces);
-  rec_free(w->b);
-  rec_free(w->x);
-  rec_free(w->r);
-  rec_free(w->rho);
-  rec_free(w->tmp64);
-  rec_free(w->lo_in);
-  rec_free(w->lo_out);
-  for (auto& r : w->phi) rec_free(r);
-  for (auto& r : w->chi) rec_free(r);
-  cudaFree(w->d_a1);
-  cudaFree(w->d_a2);
-  cudaFree(w->d_cr);
-  cudaFree(w->d_rn);
-  cudaFree(w->d_gam);
-  cudaFree(w->d_gs);
-  if (w->h_pin) cudaFreeHost(w->h_pin);
-  delete w;
-  c->ws = nullptr;
+  if (c->ws) {
+    ws_release(*c->ws);
+    delete c->ws;
+    c->ws = nullptr;
+  }
+  for (auto* w : c->batch_ws) {
+    ws_release(*w);
+    delete w;
+  }
+  c->batch_ws.clear();
 }
 
 }  // namespace qcd
