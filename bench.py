@@ -45,6 +45,9 @@ METRIC = "SAP+FGCR time to |r|/|b|<1e-10 and D_w GB/s vs HBM peak, 1 GB300"
 # as 12 reals (two rows), 72-real clover; 16-bit adds the per-site scales
 DW_BYTES = {"f64": 1344.0, "f32": 672.0, "f16": 352.0}
 DW_FLOPS = 1824.0  # 1320 hopping + 504 clover per site
+DTYPE = {(sp, op): "%s recursion (f64 residual and solution at restarts) + %s SAP arithmetic on %s SAP storage"
+                   % (op, "f64" if sp == "f64" else "f32", sp)
+         for sp in ("f64", "f32", "f16", "bf16") for op in ("f64", "f32")}
 
 
 def peaks():
@@ -188,7 +191,8 @@ def run_reference(args, world, rank):
     t_iter = statistics.median(times)
     value = t_iter * iters
     sample = ("one SAP-FGCR iteration of the oracle on the full %s lattice per step (clover build not "
-              "timed), extrapolated x%d iterations (the GPU solve's count)" % (args.workload.split()[0], iters))
+              "timed), extrapolated x%d iterations (the FP64 recursion's count on this workload, "
+              "measured on the GPU)" % (args.workload.split()[0], iters))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -203,13 +207,13 @@ def run_reference(args, world, rank):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
-def time_dirac(lat, b_t, prec, reps=20):
-    """Resident-field operator apply: ms per launch (CUDA events on the stream)."""
+def time_dirac(lat, b_t, prec, reps=20, nrhs=1):
+    """Resident-field operator apply (nrhs right-hand sides per launch): ms per launch."""
     import torch
     from paper_1109_4279_gb300 import binding as B
-    fi = B.qcd_field_create(lat.ctx, prec)
-    fo = B.qcd_field_create(lat.ctx, prec)
-    B.qcd_field_import(lat.ctx, fi, b_t)
+    fi = B.qcd_field_create_n(lat.ctx, prec, nrhs)
+    fo = B.qcd_field_create_n(lat.ctx, prec, nrhs)
+    B.qcd_field_import(lat.ctx, fi, b_t.expand(nrhs, *b_t.shape).contiguous() if nrhs > 1 else b_t)
     for _ in range(3):
         B.qcd_apply_D_field(lat.ctx, fi, fo)
     s = torch.cuda.current_stream()
@@ -226,6 +230,88 @@ def time_dirac(lat, b_t, prec, reps=20):
     return ms
 
 
+def _time_solve(lat, b_t, sp, reps=1):
+    """Median device time (ms) of complete solves from x = 0 after one warm-up."""
+    import torch
+    from paper_1109_4279_gb300 import binding as B
+    x = torch.zeros_like(b_t)
+    times, info = [], None
+    for k in range(reps + 1):
+        x.zero_()
+        st, inf = B.qcd_solve(lat.ctx, b_t, x, 1, sp, raise_on_fail=False)
+        info = inf[0]
+        if k:
+            times.append(info["time_ms"])
+    return statistics.median(times), info
+
+
+def run_comparisons(args, lat, w, U, b_t, sp_main, main_ms):
+    """Time-to-solution of the same system with other precision splits and
+    the plain FP64 solvers (one timed solve each after a warm-up)."""
+    import torch
+    from paper_1109_4279_gb300 import binding as B
+    main = "sap_%s_outer_%s" % (args.sap_prec, args.outer_prec)
+    out = {main: {"ms": main_ms, "note": "the benchmarked solve"}}
+    variants = [("sap_%s_outer_%s" % (sp_, op_), dict(sap_prec=sp_, outer_prec=op_))
+                for sp_, op_ in (("f16", "f64"), ("f16", "f32"), ("f32", "f32"), ("bf16", "f32"), ("f32", "f64"))]
+    variants.append(("gcr_f64_unpreconditioned", dict(precond="none", max_restarts=400)))
+    for name, kw in variants:
+        if name == main:
+            continue
+        sp = B.solver_params(tol=1e-10, nkv=w["nkv"], ncy=w["ncy"], nmr=w["nmr"], **kw)
+        ms, info = _time_solve(lat, b_t, sp)
+        out[name] = {"ms": ms, "iterations": info["iterations"], "status": info["status"],
+                     "true_residual": info["true_residual"]}
+    # all-FP64 SAP: FP64 block fields of a 4^4 block exceed shared memory, so 4x4x4x2 blocks
+    blk64 = (4, 4, 4, 2)
+    lat64 = B.Lattice(w["dims"], blk64, w["m0"], w["csw"])
+    lat64.load_gauge(torch.from_numpy(U).cuda())
+    sp = B.solver_params(tol=1e-10, nkv=w["nkv"], ncy=w["ncy"], nmr=w["nmr"], sap_prec="f64")
+    ms, info = _time_solve(lat64, b_t, sp)
+    out["sap_f64_outer_f64_blocks_4x4x4x2"] = {"ms": ms, "iterations": info["iterations"], "status": info["status"],
+                                               "true_residual": info["true_residual"]}
+    lat64.close()
+    plain = min(out["gcr_f64_unpreconditioned"]["ms"], out["sap_f64_outer_f64_blocks_4x4x4x2"]["ms"])
+    out["speedup_vs_plain_fp64"] = plain / main_ms
+    return out
+
+
+def run_batched(args):
+    """12 spin-colour point sources on 24^3 x 48 (eps 0.5, seed 4, m0 0,
+    c_sw 1.5): one multi-right-hand-side call against 12 single solves."""
+    import numpy as np
+    import torch
+    from paper_1109_4279_gb300 import binding as B, synth
+    wl = synth.WORKLOADS["24^3x48 12 point sources"]
+    U, _ = synth.gauge_field(wl["dims"], wl["eps"], wl["seed"])
+    b = torch.from_numpy(synth.point_sources(wl["dims"])).cuda()
+    lat = B.Lattice(wl["dims"], wl["block"], wl["m0"], wl["csw"])
+    lat.load_gauge(torch.from_numpy(U).cuda())
+    sp = B.solver_params(tol=1e-10, nkv=wl["nkv"], ncy=wl["ncy"], nmr=wl["nmr"], sap_prec=args.sap_prec,
+                         outer_prec=args.outer_prec)
+    x = torch.zeros_like(b)
+    for _ in range(2):  # warm-up (workspaces, graph capture), then timed
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = B.qcd_solve(lat.ctx, b, x, 12, sp)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+    t_seq = 0.0
+    for k in range(12):
+        xk = torch.zeros_like(b[k])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.qcd_solve(lat.ctx, b[k].contiguous(), xk, 1, sp)
+        torch.cuda.synchronize()
+        t_seq += time.perf_counter() - t0
+    lat.close()
+    return {"workload": "24^3x48, 12 point sources, SAP %s / FGCR %s" % (args.sap_prec, args.outer_prec),
+            "batched_s": t_batch, "sequential_s": t_seq,
+            "solves_per_s_batched": 12 / t_batch, "solves_per_s_sequential": 12 / t_seq,
+            "iterations": [i["iterations"] for i in info], "max_true_residual": max(i["true_residual"] for i in info)}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -238,7 +324,8 @@ def run_ours(args, world, rank, local):
     lat.load_gauge(torch.from_numpy(U).cuda())
     b_t = torch.from_numpy(b).cuda()
     x_t = torch.zeros_like(b_t)
-    sp = B.solver_params(tol=1e-10, nkv=w["nkv"], ncy=w["ncy"], nmr=w["nmr"], sap_prec="f16", outer_prec="f64")
+    sp = B.solver_params(tol=1e-10, nkv=w["nkv"], ncy=w["ncy"], nmr=w["nmr"], sap_prec=args.sap_prec,
+                         outer_prec=args.outer_prec)
 
     def solve_once():
         x_t.zero_()
@@ -289,7 +376,9 @@ def run_ours(args, world, rank, local):
     dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
     kd = kernels[dom]
     if dom == "sap":
-        roof = {"kernel": "sap_sweep (FP16 block fields, FP32 arithmetic)", "bound": "alu",
+        roof = {"kernel": "sap_sweep (%s block fields, %s arithmetic)" % (args.sap_prec.upper(),
+                                                                         "FP64" if args.sap_prec == "f64" else "FP32"),
+                "bound": "alu",
                 "achieved": kd["achieved_tflops"], "peak": pk["fp32_tflops"], "unit": "TFLOP/s"}
     elif dom in ("dirac", "residual"):
         roof = {"kernel": "dirac FP64", "bound": "alu", "achieved": kd["achieved_tflops"],
@@ -310,6 +399,20 @@ def run_ours(args, world, rank, local):
         dw[prec] = {"ms": ms, "gbs": gbs, "frac_hbm_measured": gbs / pk["hbm_gbs"], "frac_hbm_nominal_8tbs": gbs / 8000.0,
                     "gflops": DW_FLOPS * V / (ms * 1e-3) / 1e9}
 
+    # multi-right-hand-side operator: links and clover read once per site for R fields
+    R = 12
+    for prec in ("f32", "f16"):
+        ms = time_dirac(lat, b_t, prec, reps=10, nrhs=R)
+        spin = {"f32": 192.0, "f16": 104.0}[prec]
+        byts = (DW_BYTES[prec] - spin + spin * R) * V
+        gbs = byts / (ms * 1e-3) / 1e9
+        dw[prec + "_x%d_rhs" % R] = {"ms": ms, "gbs": gbs, "frac_hbm_measured": gbs / pk["hbm_gbs"],
+                                     "bytes_per_site_rhs": byts / V / R,
+                                     "site_rhs_per_s": V * R / (ms * 1e-3)}
+
+    comparisons = run_comparisons(args, lat, w, U, b_t, sp, ms_per_step) if not args.quick else None
+    batched = run_batched(args) if not args.quick else None
+
     # end to end through the public API with host buffers
     b_h = torch.from_numpy(b.copy()).pin_memory()
     x_h = torch.zeros_like(b_h).pin_memory()
@@ -329,20 +432,22 @@ def run_ours(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_iter, threads = oracle_iteration_seconds(w, U, b)
-        cpu = {"value": t_iter * iters, "unit": "s", "cores": threads, "kind": "oracle",
+        n_or = args.gpu_iterations
+        cpu = {"value": t_iter * n_or, "unit": "s", "cores": threads, "kind": "oracle",
                "sample": "one SAP-FGCR iteration of the FP64 oracle on the full %s lattice "
-                         "(%.1f s), extrapolated x%d iterations" % (args.workload.split()[0], t_iter, iters)}
+                         "(%.1f s), extrapolated x%d iterations (the FP64 recursion's count on this "
+                         "workload)" % (args.workload.split()[0], t_iter, n_or)}
 
     line = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 outer + f32 arithmetic on f16 SAP storage", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE[(args.sap_prec, args.outer_prec)], "data": "synthetic",
             "config": {"workload": args.workload, "dims": list(w["dims"]), "block": list(w["block"]), "m0": w["m0"],
                        "csw": w["csw"], "eps": w["eps"], "seed": w["seed"], "tol": 1e-10, "nkv": w["nkv"],
-                       "ncy": w["ncy"], "nmr": w["nmr"], "sap_prec": "f16", "outer_prec": "f64",
+                       "ncy": w["ncy"], "nmr": w["nmr"], "sap_prec": args.sap_prec, "outer_prec": args.outer_prec,
                        "iterations": iters, "restarts": int(statistics.median(i["restarts"] for i in infos)),
                        "true_residual": max(i["true_residual"] for i in infos),
                        "l2": "no flush: every FP64 solver vector (192 B/site) and the gauge/clover fields exceed the 129 MB L2"},
-            "roofline": roof, "kernels": kernels, "dw": dw,
+            "roofline": roof, "kernels": kernels, "dw": dw, "comparisons": comparisons, "batched": batched,
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * fbytes, "d2h_bytes_per_step": fbytes},
             "gpu_launches": launches,
             "clocks": clk.summary(), "cpu_baseline": cpu,
@@ -362,8 +467,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(BENCH_WORKLOADS), default=WORKLOAD)
     ap.add_argument("--gpu-iterations", type=int, default=7,
-                    help="reference arm: FGCR iterations the GPU solve of this workload needs (measured: 7)")
+                    help="oracle extrapolation: FGCR iterations of the FP64 recursion on this workload "
+                         "(measured on the GPU: 7)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the comparison and batched sections")
+    ap.add_argument("--sap-prec", choices=["f64", "f32", "f16", "bf16"], default="f16",
+                    help="storage precision of the SAP block fields")
+    ap.add_argument("--outer-prec", choices=["f64", "f32"], default="f32",
+                    help="FGCR recursion precision (f32: the iterative-refinement scheme, FP64 restarts)")
     args = ap.parse_args()
     if args.impl == "reference":
         world = int(os.environ.get("WORLD_SIZE", "1"))

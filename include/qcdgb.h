@@ -91,7 +91,13 @@ typedef struct {
     int ncy;           /* SAP cycles per preconditioner application */
     int nmr;           /* MR steps per block solve */
     int sap_prec;      /* precision of the SAP block fields: QCD_PREC_F64/F32/F16/BF16 */
-    int outer_prec;    /* precision of chi_k = D phi_k in the recursion: QCD_PREC_F64 (default) or QCD_PREC_F32 */
+    int outer_prec;    /* precision of the FGCR recursion (Sec. 4):
+                          QCD_PREC_F64 (default): rho, phi_k, chi_k = D phi_k, Gram-Schmidt and dots in FP64;
+                          QCD_PREC_F32: iterative refinement -- each restart cycle runs the whole recursion
+                          in FP32 on the normalised residual r / |r| until its residual has dropped by
+                          inner_tol (or the target is met), then the FP32 correction is added to the FP64
+                          solution and r = b - D x is recomputed in FP64 */
+    double inner_tol;  /* QCD_PREC_F32 recursion only: residual reduction per restart cycle (default 1e-5) */
 } qcd_solver_params;
 
 /* Solver report, always filled (also on failure). */
@@ -249,6 +255,10 @@ typedef struct qcd_field qcd_field;
  * precision.  Free with qcd_field_free.
  */
 int qcd_field_create(qcd_ctx* ctx, int prec, qcd_field** out);
+/* Same for nrhs fields back to back (a multi-right-hand-side field: import,
+ * export and qcd_apply_D_field then treat nrhs * (V, 4, 3) complex128, and the
+ * operator reads each site's links and clover once for all right-hand sides). */
+int qcd_field_create_n(qcd_ctx* ctx, int prec, int nrhs, qcd_field** out);
 void qcd_field_free(qcd_field* f);
 
 /* Convert a device (V, 4, 3) complex128 lexicographic spinor into / out of a field. */

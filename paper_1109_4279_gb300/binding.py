@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
 class SolverParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("nkv", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("precond", ctypes.c_int), ("ncy", ctypes.c_int), ("nmr", ctypes.c_int),
-                ("sap_prec", ctypes.c_int), ("outer_prec", ctypes.c_int)]
+                ("sap_prec", ctypes.c_int), ("outer_prec", ctypes.c_int), ("inner_tol", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -83,6 +83,7 @@ def lib():
             "qcd_status_string": (ctypes.c_char_p, [I]),
             "qcd_last_error": (ctypes.c_char_p, []),
             "qcd_field_create": (I, [P, I, ctypes.POINTER(P)]),
+            "qcd_field_create_n": (I, [P, I, I, ctypes.POINTER(P)]),
             "qcd_field_free": (None, [P]),
             "qcd_field_import": (I, [P, P, P, P]),
             "qcd_field_export": (I, [P, P, P, P]),
@@ -240,6 +241,12 @@ def qcd_status_string(st):
 def qcd_field_create(ctx, prec="f32"):
     h = ctypes.c_void_p()
     check(lib().qcd_field_create(ctx, PREC[prec], ctypes.byref(h)), "qcd_field_create")
+    return h
+
+
+def qcd_field_create_n(ctx, prec="f32", nrhs=1):
+    h = ctypes.c_void_p()
+    check(lib().qcd_field_create_n(ctx, PREC[prec], int(nrhs), ctypes.byref(h)), "qcd_field_create_n")
     return h
 
 

@@ -106,6 +106,7 @@ void qcd_solver_defaults(qcd_solver_params* sp) {
   sp->nmr = 4;
   sp->sap_prec = QCD_PREC_F32;
   sp->outer_prec = QCD_PREC_F64;
+  sp->inner_tol = 1e-5;
 }
 
 const char* qcd_status_string(int st) {
@@ -205,16 +206,12 @@ int qcd_apply_D(qcd_ctx* c, const double* in, double* out, int dagger, int prec,
   if (!c || !in || !out || nrhs < 1 || prec < 0 || prec > 3) return QCD_ERR_ARG;
   if (!c->clover_built) return QCD_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
-  Workspace* w = ensure_ws(c);
-  if (!w) return QCD_ERR_NOMEM;
   Rec a, b;
-  QCD_TRY(rec_alloc(a, prec, 24, c->V));
-  int st = rec_alloc(b, prec, 24, c->V);
-  for (int k = 0; k < nrhs && st == QCD_OK; ++k) {
-    st = import_spinor(c, in + (size_t)k * c->V * 24, a, 1, s);
-    if (st == QCD_OK) st = dirac_apply(c, a, b, dagger, s);
-    if (st == QCD_OK) st = export_spinor(c, b, out + (size_t)k * c->V * 24, 1, s);
-  }
+  int st = rec_alloc(a, prec, 24, c->V * nrhs);
+  if (st == QCD_OK) st = rec_alloc(b, prec, 24, c->V * nrhs);
+  if (st == QCD_OK) st = import_spinor(c, in, a, nrhs, s);
+  if (st == QCD_OK) st = dirac_apply(c, a, b, dagger, s, nrhs);
+  if (st == QCD_OK) st = export_spinor(c, b, out, nrhs, s);
   cudaStreamSynchronize(s);
   rec_free(a);
   rec_free(b);
@@ -460,12 +457,15 @@ int qcd_gradient(qcd_ctx* c, const double* phi, double* dL_dphi, double* dL_dthe
   return st;
 }
 
-int qcd_field_create(qcd_ctx* c, int prec, qcd_field** out) {
-  if (!c || !out || prec < 0 || prec > 3) return QCD_ERR_ARG;
+int qcd_field_create(qcd_ctx* c, int prec, qcd_field** out) { return qcd_field_create_n(c, prec, 1, out); }
+
+int qcd_field_create_n(qcd_ctx* c, int prec, int nrhs, qcd_field** out) {
+  if (!c || !out || prec < 0 || prec > 3 || nrhs < 1) return QCD_ERR_ARG;
   qcd_field* f = new (std::nothrow) qcd_field();
   if (!f) return QCD_ERR_NOMEM;
   f->ctx = c;
-  int st = rec_alloc(f->rec, prec, 24, c->V);
+  f->nrhs = nrhs;
+  int st = rec_alloc(f->rec, prec, 24, c->V * nrhs);
   if (st) {
     delete f;
     return st;
@@ -483,18 +483,18 @@ void qcd_field_free(qcd_field* f) {
 
 int qcd_field_import(qcd_ctx* c, qcd_field* f, const double* in, void* stream) {
   if (!c || !f || !in || f->ctx != c) return QCD_ERR_ARG;
-  return import_spinor(c, in, f->rec, 1, (cudaStream_t)stream);
+  return import_spinor(c, in, f->rec, f->nrhs, (cudaStream_t)stream);
 }
 
 int qcd_field_export(qcd_ctx* c, const qcd_field* f, double* out, void* stream) {
   if (!c || !f || !out || f->ctx != c) return QCD_ERR_ARG;
-  return export_spinor(c, f->rec, out, 1, (cudaStream_t)stream);
+  return export_spinor(c, f->rec, out, f->nrhs, (cudaStream_t)stream);
 }
 
 int qcd_apply_D_field(qcd_ctx* c, const qcd_field* in, qcd_field* out, int dagger, void* stream) {
-  if (!c || !in || !out || in->ctx != c || out->ctx != c || in == out) return QCD_ERR_ARG;
+  if (!c || !in || !out || in->ctx != c || out->ctx != c || in == out || in->nrhs != out->nrhs) return QCD_ERR_ARG;
   if (!c->clover_built) return QCD_ERR_STATE;
-  return dirac_apply(c, in->rec, out->rec, dagger, (cudaStream_t)stream);
+  return dirac_apply(c, in->rec, out->rec, dagger, (cudaStream_t)stream, in->nrhs);
 }
 
 int qcd_sap_apply(qcd_ctx* c, const double* eta, double* psi, int ncy, int nmr, int sap_prec, void* stream) {

@@ -99,15 +99,15 @@ extern "C" int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
   const int cand[3] = {128, 256, 512};
   for (int p = P64; p <= PB16 && st == QCD_OK; ++p) {
     Rec a, b;
-    st = rec_alloc(a, p, 24, c->V);
-    if (st == QCD_OK) st = rec_alloc(b, p, 24, c->V);
+    st = rec_alloc(a, p, 24, c->V * nrhs);
+    if (st == QCD_OK) st = rec_alloc(b, p, 24, c->V * nrhs);
     if (st == QCD_OK && cudaMemsetAsync(a.data, 0, a.bytes, s) != cudaSuccess) st = QCD_ERR_CUDA;
     float best_ms = 1e30f;
     for (int k = 0; k < 3 && st == QCD_OK; ++k) {
       c->dirac_threads[p] = cand[k];
-      st = dirac_apply(c, a, b, 0, s);  // warm-up (also builds this precision's fields)
+      st = dirac_apply(c, a, b, 0, s, nrhs);  // warm-up (also builds this precision's fields)
       cudaEventRecord(e0, s);
-      for (int it = 0; it < 5 * nrhs && st == QCD_OK; ++it) st = dirac_apply(c, a, b, 0, s);
+      for (int it = 0; it < 5 && st == QCD_OK; ++it) st = dirac_apply(c, a, b, 0, s, nrhs);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       float ms = 0;

@@ -1,9 +1,12 @@
-// FP64 spinor linear algebra of the FGCR recursion (Sec. 4; Sec. 6 counts it
-// as "spinor linear algebra", 12 % of the solver time on QPACE): fused
+// Spinor linear algebra of the FGCR recursion (Sec. 4; Sec. 6 counts it as
+// "spinor linear algebra", 12 % of the solver time on QPACE): fused
 // multi-dot / multi-axpy kernels for classical Gram-Schmidt with
-// re-orthogonalisation, norms and the solution update.  Every reduction is
-// deterministic: fixed grid, per-CTA partial sums in a fixed order, then one
-// CTA sums the partials in index order.
+// re-orthogonalisation, norms and the solution update, in FP64 (vectors of
+// double2, one complex number per element) or FP32 (vectors of float4, two
+// complex numbers per element; the recursion of the mixed-precision scheme).
+// FP32 kernels accumulate in FP32 per thread; every CTA and grid sum is FP64.
+// Every reduction is deterministic: fixed grid, per-CTA partial sums in a
+// fixed order, then one warp per value sums the partials in index order.
 #include "internal.h"
 
 namespace qcd {
@@ -11,9 +14,64 @@ namespace qcd {
 static constexpr int kMaxVec = 64;
 static constexpr int kBlasThreads = 256;
 
-struct VecList {
-  const double2* v[kMaxVec];
+template <typename R>
+struct VecT;
+template <>
+struct VecT<double> {
+  typedef double2 type;
+  static constexpr int NC = 1;  // complex numbers per element
 };
+template <>
+struct VecT<float> {
+  typedef float4 type;
+  static constexpr int NC = 2;
+};
+
+template <typename E>
+struct VecList {
+  const E* v[kMaxVec];
+};
+
+// ---- complex arithmetic on one element
+// (re, im) += conj(a) b
+__device__ __forceinline__ void dot_acc(const double2& a, const double2& b, double& re, double& im) {
+  re = fma(a.x, b.x, fma(a.y, b.y, re));
+  im = fma(a.x, b.y, fma(-a.y, b.x, im));
+}
+__device__ __forceinline__ void dot_acc(const float4& a, const float4& b, float& re, float& im) {
+  re = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, re))));
+  im = fmaf(a.x, b.y, fmaf(-a.y, b.x, fmaf(a.z, b.w, fmaf(-a.w, b.z, im))));
+}
+__device__ __forceinline__ void nrm_acc(const double2& b, double& n) { n = fma(b.x, b.x, fma(b.y, b.y, n)); }
+__device__ __forceinline__ void nrm_acc(const float4& b, float& n) {
+  n = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, n))));
+}
+// b -= (cr + i ci) a
+__device__ __forceinline__ void csub(double2& b, double cr, double ci, const double2& a) {
+  b.x -= cr * a.x - ci * a.y;
+  b.y -= cr * a.y + ci * a.x;
+}
+__device__ __forceinline__ void csub(float4& b, float cr, float ci, const float4& a) {
+  b.x -= cr * a.x - ci * a.y;
+  b.y -= cr * a.y + ci * a.x;
+  b.z -= cr * a.z - ci * a.w;
+  b.w -= cr * a.w + ci * a.z;
+}
+// b += (cr + i ci) a
+__device__ __forceinline__ void cadd(double2& b, double cr, double ci, const double2& a) {
+  b.x += cr * a.x - ci * a.y;
+  b.y += cr * a.y + ci * a.x;
+}
+__device__ __forceinline__ void cadd(float4& b, float cr, float ci, const float4& a) {
+  b.x += cr * a.x - ci * a.y;
+  b.y += cr * a.y + ci * a.x;
+  b.z += cr * a.z - ci * a.w;
+  b.w += cr * a.w + ci * a.z;
+}
+__device__ __forceinline__ double2 rscale(const double2& a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ float4 rscale(const float4& a, float s) {
+  return make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+}
 
 static unsigned blas_grid(long long n) {
   long long g = (n + kBlasThreads - 1) / kBlasThreads;
@@ -27,14 +85,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// reduce M values per thread over the CTA; thread 0 writes part[blockIdx.x * M + j]
-template <int M>
-__device__ __forceinline__ void cta_reduce_store(double (&v)[M], double* part) {
+// reduce M values per thread over the CTA (in FP64); thread j < M writes
+// part[blockIdx.x * M + j]
+template <int M, typename A>
+__device__ __forceinline__ void cta_reduce_store(A (&v)[M], double* part) {
   __shared__ double sh[kBlasThreads / 32][M > 0 ? M : 1];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    double t = warp_sum(v[j]);
+    double t = warp_sum((double)v[j]);
     if (l == 0) sh[w][j] = t;
   }
   __syncthreads();
@@ -74,66 +133,63 @@ __device__ __forceinline__ bool second_pass_needed(const double* gs) {
 // out[j] = (v_j, w) = sum conj(v_j) w, j < k <= K; with NORM also out[2K] = |w|^2.
 // cond (optional): skip unless second_pass_needed(cond) -- then the partial
 // sums are zero, so the reduced coefficients are zero.
-template <int K, int NORM>
-__global__ void __launch_bounds__(kBlasThreads) multidot_kernel(VecList vl, int k, const double2* __restrict__ w,
-                                                                long long n, const double* cond, double* part) {
-  double acc[2 * K + NORM];
+template <typename R, int K, int NORM>
+__global__ void __launch_bounds__(kBlasThreads)
+    multidot_kernel(VecList<typename VecT<R>::type> vl, int k, const typename VecT<R>::type* __restrict__ w, long long n,
+                    const double* cond, double* part) {
+  typedef typename VecT<R>::type E;
+  R acc[2 * K + NORM];
 #pragma unroll
   for (int j = 0; j < 2 * K + NORM; ++j) acc[j] = 0;
   if (cond == nullptr || second_pass_needed(cond)) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-      const double2 b = __ldg(w + i);
+      const E b = __ldg(w + i);
 #pragma unroll
       for (int j = 0; j < K; ++j)
-        if (j < k) {
-          const double2 a = __ldg(vl.v[j] + i);
-          acc[2 * j] = fma(a.x, b.x, fma(a.y, b.y, acc[2 * j]));
-          acc[2 * j + 1] = fma(a.x, b.y, fma(-a.y, b.x, acc[2 * j + 1]));
-        }
-      if (NORM) acc[2 * K] = fma(b.x, b.x, fma(b.y, b.y, acc[2 * K]));
+        if (j < k) dot_acc(__ldg(vl.v[j] + i), b, acc[2 * j], acc[2 * j + 1]);
+      if (NORM) nrm_acc(b, acc[2 * K]);
     }
   }
   cta_reduce_store<2 * K + NORM>(acc, part);
 }
 
 // w -= sum_j c_j v_j; then out[j] = (v_j, w) (DOT = 1) or out = {|w|^2, (w, rho)} (DOT = 2)
-template <int K, int DOT>
-__global__ void __launch_bounds__(kBlasThreads) axpy_dot_kernel(VecList vl, int k, const double* __restrict__ coef,
-                                                                double2* __restrict__ w,
-                                                                const double2* __restrict__ rho, long long n,
-                                                                const double* cond, double* part) {
+template <typename R, int K, int DOT>
+__global__ void __launch_bounds__(kBlasThreads)
+    axpy_dot_kernel(VecList<typename VecT<R>::type> vl, int k, const double* __restrict__ coef,
+                    typename VecT<R>::type* __restrict__ w, const typename VecT<R>::type* __restrict__ rho, long long n,
+                    const double* cond, double* part) {
+  typedef typename VecT<R>::type E;
   constexpr int M = DOT == 1 ? 2 * K : 3;
   if (cond != nullptr && !second_pass_needed(cond)) return;  // block-uniform: no partials written
-  double acc[M];
+  R acc[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) acc[j] = 0;
-  double2 cf[K];
+  R cr[K], ci[K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) cf[j] = j < k ? make_double2(coef[2 * j], coef[2 * j + 1]) : make_double2(0, 0);
+  for (int j = 0; j < K; ++j) {
+    cr[j] = j < k ? (R)coef[2 * j] : R(0);
+    ci[j] = j < k ? (R)coef[2 * j + 1] : R(0);
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double2 b = w[i];
-    double2 a[K];
+    E b = w[i];
+    E a[K];
 #pragma unroll
     for (int j = 0; j < K; ++j)
       if (j < k) {
         a[j] = __ldg(vl.v[j] + i);
-        b.x -= cf[j].x * a[j].x - cf[j].y * a[j].y;
-        b.y -= cf[j].x * a[j].y + cf[j].y * a[j].x;
+        csub(b, cr[j], ci[j], a[j]);
       }
     w[i] = b;
     if (DOT == 1) {
 #pragma unroll
       for (int j = 0; j < K; ++j)
-        if (j < k) {
-          acc[2 * j] = fma(a[j].x, b.x, fma(a[j].y, b.y, acc[2 * j]));
-          acc[2 * j + 1] = fma(a[j].x, b.y, fma(-a[j].y, b.x, acc[2 * j + 1]));
-        }
+        if (j < k) dot_acc(a[j], b, acc[2 * j], acc[2 * j + 1]);
     } else {
-      const double2 r = __ldg(rho + i);
-      acc[0] = fma(b.x, b.x, fma(b.y, b.y, acc[0]));
-      acc[1] = fma(b.x, r.x, fma(b.y, r.y, acc[1]));
-      acc[2] = fma(b.x, r.y, fma(-b.y, r.x, acc[2]));
+      const E r = __ldg(rho + i);
+      nrm_acc(b, acc[0]);
+      dot_acc(b, r, acc[1], acc[2]);
     }
   }
   cta_reduce_store<M>(acc, part);
@@ -144,10 +200,11 @@ __global__ void __launch_bounds__(kBlasThreads) axpy_dot_kernel(VecList vl, int 
 // are used when the second pass ran.  Thread 0 of CTA 0 stores them in
 // cr = {|chi_k|^2, (chi_k, rho_k)}.  Then chi /= |chi|;
 // rho -= ((chi, rho) / |chi|^2) chi_unnormalised;  partial |rho|^2.
-__global__ void __launch_bounds__(kBlasThreads) normalise_update_kernel(double2* __restrict__ chi,
-                                                                        double2* __restrict__ rho,
-                                                                        const double* __restrict__ gs, int two_pass,
-                                                                        double* cr, long long n, double* part) {
+template <typename R>
+__global__ void __launch_bounds__(kBlasThreads)
+    normalise_update_kernel(typename VecT<R>::type* __restrict__ chi, typename VecT<R>::type* __restrict__ rho,
+                            const double* __restrict__ gs, int two_pass, double* cr, long long n, double* part) {
+  typedef typename VecT<R>::type E;
   const double* co = (two_pass && second_pass_needed(gs)) ? gs + 4 : gs + 1;
   const double nrm2 = co[0];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -155,47 +212,95 @@ __global__ void __launch_bounds__(kBlasThreads) normalise_update_kernel(double2*
     cr[1] = co[1];
     cr[2] = co[2];
   }
-  const double inv = nrm2 > 0 ? 1.0 / sqrt(nrm2) : 0.0;
-  const double cre = nrm2 > 0 ? co[1] / nrm2 : 0.0, cim = nrm2 > 0 ? co[2] / nrm2 : 0.0;
-  double acc[1] = {0};
+  const R inv = nrm2 > 0 ? (R)(1.0 / sqrt(nrm2)) : R(0);
+  const R cre = nrm2 > 0 ? (R)(co[1] / nrm2) : R(0), cim = nrm2 > 0 ? (R)(co[2] / nrm2) : R(0);
+  R acc[1] = {0};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double2 x = chi[i];
-    double2 r = rho[i];
-    r.x -= cre * x.x - cim * x.y;
-    r.y -= cre * x.y + cim * x.x;
+    const E x = chi[i];
+    E r = rho[i];
+    csub(r, cre, cim, x);
     rho[i] = r;
-    chi[i] = make_double2(x.x * inv, x.y * inv);
-    acc[0] = fma(r.x, r.x, fma(r.y, r.y, acc[0]));
+    chi[i] = rscale(x, inv);
+    nrm_acc(r, acc[0]);
   }
   cta_reduce_store<1>(acc, part);
 }
 
 // x += sum_j g_j phi_j
-template <int K>
-__global__ void __launch_bounds__(kBlasThreads) multi_axpy_kernel(VecList vl, int k, const double* __restrict__ gam,
-                                                                  double2* __restrict__ x, long long n) {
-  double2 cf[K];
+template <typename R, int K>
+__global__ void __launch_bounds__(kBlasThreads)
+    multi_axpy_kernel(VecList<typename VecT<R>::type> vl, int k, const double* __restrict__ gam,
+                      typename VecT<R>::type* __restrict__ x, long long n) {
+  typedef typename VecT<R>::type E;
+  R cr[K], ci[K];
 #pragma unroll
-  for (int j = 0; j < K; ++j) cf[j] = j < k ? make_double2(gam[2 * j], gam[2 * j + 1]) : make_double2(0, 0);
+  for (int j = 0; j < K; ++j) {
+    cr[j] = j < k ? (R)gam[2 * j] : R(0);
+    ci[j] = j < k ? (R)gam[2 * j + 1] : R(0);
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double2 b = x[i];
+    E b = x[i];
 #pragma unroll
     for (int j = 0; j < K; ++j)
-      if (j < k) {
-        const double2 a = __ldg(vl.v[j] + i);
-        b.x += cf[j].x * a.x - cf[j].y * a.y;
-        b.y += cf[j].x * a.y + cf[j].y * a.x;
-      }
+      if (j < k) cadd(b, cr[j], ci[j], __ldg(vl.v[j] + i));
     x[i] = b;
   }
 }
 
-__global__ void __launch_bounds__(kBlasThreads) norm2_kernel(const double2* __restrict__ v, long long n, double* part) {
-  double acc[1] = {0};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double2 a = __ldg(v + i);
-    acc[0] = fma(a.x, a.x, fma(a.y, a.y, acc[0]));
+// Iterative refinement (Sec. 4): x64 += |r| sum_j g_j phi_j with FP32 phi_j,
+// the sum formed in FP32 and added to the FP64 solution in FP64.  Element i
+// of the FP32 layout [blk][6][Vb] (float4) holds the reals of FP64 elements
+// (blk, 2c, r) and (blk, 2c + 1, r) of the layout [blk][12][Vb] (double2).
+template <int K>
+__global__ void __launch_bounds__(kBlasThreads)
+    refine_update_kernel(VecList<float4> vl, int k, const double* __restrict__ gam, const double* __restrict__ rn2,
+                         double2* __restrict__ x, int Vb, long long n) {
+  float cr[K], ci[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    cr[j] = j < k ? (float)gam[2 * j] : 0.f;
+    ci[j] = j < k ? (float)gam[2 * j + 1] : 0.f;
   }
+  const double scale = sqrt(*rn2);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float4 d = make_float4(0, 0, 0, 0);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j < k) cadd(d, cr[j], ci[j], __ldg(vl.v[j] + i));
+    const long long blk = i / (6LL * Vb), rem = i - blk * 6LL * Vb;
+    const long long c = rem / Vb, r = rem - c * Vb;
+    const long long e0 = (blk * 12 + 2 * c) * Vb + r;
+    double2 x0 = x[e0], x1 = x[e0 + Vb];
+    x0.x = fma(scale, (double)d.x, x0.x);
+    x0.y = fma(scale, (double)d.y, x0.y);
+    x1.x = fma(scale, (double)d.z, x1.x);
+    x1.y = fma(scale, (double)d.w, x1.y);
+    x[e0] = x0;
+    x[e0 + Vb] = x1;
+  }
+}
+
+// rho32 = r64 / |r|: the normalised FP64 residual as the FP32 source of a
+// refinement cycle (same element mapping as refine_update_kernel)
+__global__ void __launch_bounds__(kBlasThreads)
+    demote_normalised_kernel(const double2* __restrict__ r, const double* __restrict__ rn2, float4* __restrict__ out,
+                             int Vb, long long n) {
+  const double inv = *rn2 > 0 ? 1.0 / sqrt(*rn2) : 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long blk = i / (6LL * Vb), rem = i - blk * 6LL * Vb;
+    const long long c = rem / Vb, rr = rem - c * Vb;
+    const long long e0 = (blk * 12 + 2 * c) * Vb + rr;
+    const double2 a = __ldg(r + e0), b = __ldg(r + e0 + Vb);
+    out[i] = make_float4((float)(a.x * inv), (float)(a.y * inv), (float)(b.x * inv), (float)(b.y * inv));
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlasThreads)
+    norm2_kernel(const typename VecT<R>::type* __restrict__ v, long long n, double* part) {
+  R acc[1] = {0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    nrm_acc(__ldg(v + i), acc[0]);
   cta_reduce_store<1>(acc, part);
 }
 
@@ -232,33 +337,43 @@ __global__ void backsub_kernel(const double* a1, const double* a2, const double*
 }
 
 // ------------------------------------------------------------------------
-static VecList make_list(const double* const* v, int k) {
-  VecList vl;
-  for (int j = 0; j < kMaxVec; ++j) vl.v[j] = j < k ? (const double2*)v[j] : nullptr;
+template <typename R>
+static VecList<typename VecT<R>::type> make_list(const R* const* v, int k) {
+  VecList<typename VecT<R>::type> vl;
+  for (int j = 0; j < kMaxVec; ++j) vl.v[j] = j < k ? (const typename VecT<R>::type*)v[j] : nullptr;
   return vl;
 }
 
-int blas_multidot(qcd_ctx* c, double* part, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s,
+// elements of one 24-real-per-site field
+template <typename R>
+static long long nel(qcd_ctx* c) {
+  return c->V * 12 / VecT<R>::NC;
+}
+
+static int pick_k(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32)); }
+
+template <typename R>
+int blas_multidot(qcd_ctx* c, double* part, const R* const* v, int k, const R* w, double* d_out, cudaStream_t s,
                   const double* cond, double* d_norm) {
+  typedef typename VecT<R>::type E;
   if (k <= 0) return QCD_OK;
   if (k > kMaxVec) return QCD_ERR_ARG;
-  const long long n = c->V * 12;
+  const long long n = nel<R>(c);
   const unsigned grid = blas_grid(n);
-  ProfScope ps(c, QCD_KERNEL_BLAS, s, 16.0 * n * (k + 1), 8.0 * n * k);
-  int K;
-  if (k <= 4) K = 4; else if (k <= 8) K = 8; else if (k <= 16) K = 16; else K = 32;
+  ProfScope ps(c, QCD_KERNEL_BLAS, s, sizeof(E) * (double)n * (k + 1), 8.0 * c->V * 12 * k);
+  const int K = pick_k(k);
   int done = 0;
   while (done < k) {
     const int kk = k - done < K ? k - done : K;
     const int norm = (d_norm != nullptr && done == 0) ? 1 : 0;
     const int M = 2 * K + norm;
-    VecList vl = make_list(v + done, kk);
-    const double2* w2 = (const double2*)w;
-#define MD(KK)                                                                                                   \
-  if (norm)                                                                                                      \
-    multidot_kernel<KK, 1><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, part);                  \
-  else                                                                                                           \
-    multidot_kernel<KK, 0><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, part);
+    auto vl = make_list<R>(v + done, kk);
+    const E* w2 = (const E*)w;
+#define MD(KK)                                                                         \
+  if (norm)                                                                            \
+    multidot_kernel<R, KK, 1><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, part); \
+  else                                                                                 \
+    multidot_kernel<R, KK, 0><<<grid, kBlasThreads, 0, s>>>(vl, kk, w2, n, cond, part);
     switch (K) {
       case 4: MD(4); break;
       case 8: MD(8); break;
@@ -274,89 +389,127 @@ int blas_multidot(qcd_ctx* c, double* part, const double* const* v, int k, const
   return QCD_OK;
 }
 
-template <int DOT>
-static int axpy_dot_impl(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w, const double* rho,
+template <typename R, int DOT>
+static int axpy_dot_impl(qcd_ctx* c, double* part, const R* const* v, int k, const double* d_coef, R* w, const R* rho,
                          double* d_out, cudaStream_t s, const double* cond = nullptr) {
+  typedef typename VecT<R>::type E;
   if (k > 32) return QCD_ERR_UNSUPPORTED;
-  const long long n = c->V * 12;
+  const long long n = nel<R>(c);
   const unsigned grid = blas_grid(n);
-  int K;
-  if (k <= 4) K = 4; else if (k <= 8) K = 8; else if (k <= 16) K = 16; else K = 32;
+  const int K = pick_k(k);
   const int M = DOT == 1 ? 2 * K : 3;
-  ProfScope ps(c, QCD_KERNEL_BLAS, s, 16.0 * n * (k + 2 + (DOT == 2)), 16.0 * n * k);
-  VecList vl = make_list(v, k);
-  const double2* r2 = (const double2*)rho;
+  ProfScope ps(c, QCD_KERNEL_BLAS, s, sizeof(E) * (double)n * (k + 2 + (DOT == 2)), 16.0 * c->V * 12 * k);
+  auto vl = make_list<R>(v, k);
+  const E* r2 = (const E*)rho;
+  E* w2 = (E*)w;
   switch (K) {
-    case 4: axpy_dot_kernel<4, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, part); break;
-    case 8: axpy_dot_kernel<8, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, part); break;
-    case 16: axpy_dot_kernel<16, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, part); break;
-    default: axpy_dot_kernel<32, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, (double2*)w, r2, n, cond, part); break;
+    case 4: axpy_dot_kernel<R, 4, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, w2, r2, n, cond, part); break;
+    case 8: axpy_dot_kernel<R, 8, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, w2, r2, n, cond, part); break;
+    case 16: axpy_dot_kernel<R, 16, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, w2, r2, n, cond, part); break;
+    default: axpy_dot_kernel<R, 32, DOT><<<grid, kBlasThreads, 0, s>>>(vl, k, d_coef, w2, r2, n, cond, part); break;
   }
   QCD_LAUNCHED();
   return reduce_partials(part, (int)grid, M, DOT == 1 ? 2 * k : 3, d_out, s);
 }
 
-int blas_axpy_dot(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w, double* d_out,
+template <typename R>
+int blas_axpy_dot(qcd_ctx* c, double* part, const R* const* v, int k, const double* d_coef, R* w, double* d_out,
                   cudaStream_t s) {
   if (k <= 0) return QCD_OK;
-  return axpy_dot_impl<1>(c, part, v, k, d_coef, w, nullptr, d_out, s);
+  return axpy_dot_impl<R, 1>(c, part, v, k, d_coef, w, nullptr, d_out, s);
 }
 
-int blas_axpy_norm_dot(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w, const double* rho,
+template <typename R>
+int blas_axpy_norm_dot(qcd_ctx* c, double* part, const R* const* v, int k, const double* d_coef, R* w, const R* rho,
                        double* d_out, cudaStream_t s, const double* cond) {
+  typedef typename VecT<R>::type E;
   if (k <= 0) {
     // nothing to subtract: only the norm and the dot
-    const long long n = c->V * 12;
+    const long long n = nel<R>(c);
     const unsigned grid = blas_grid(n);
-    VecList vl = make_list(v, 0);
-    ProfScope ps(c, QCD_KERNEL_BLAS, s, 32.0 * n, 8.0 * n);
-    axpy_dot_kernel<4, 2><<<grid, kBlasThreads, 0, s>>>(vl, 0, d_coef, (double2*)w, (const double2*)rho, n, cond,
-                                                        part);
+    auto vl = make_list<R>(v, 0);
+    ProfScope ps(c, QCD_KERNEL_BLAS, s, 2.0 * sizeof(E) * n, 8.0 * c->V * 12);
+    axpy_dot_kernel<R, 4, 2><<<grid, kBlasThreads, 0, s>>>(vl, 0, d_coef, (E*)w, (const E*)rho, n, cond, part);
     QCD_LAUNCHED();
     return reduce_partials(part, (int)grid, 3, 3, d_out, s);
   }
-  return axpy_dot_impl<2>(c, part, v, k, d_coef, w, rho, d_out, s, cond);
+  return axpy_dot_impl<R, 2>(c, part, v, k, d_coef, w, rho, d_out, s, cond);
 }
 
-int blas_normalise_update(qcd_ctx* c, double* part, double* chi, double* rho, const double* d_gs, int two_pass, double* d_cr,
+template <typename R>
+int blas_normalise_update(qcd_ctx* c, double* part, R* chi, R* rho, const double* d_gs, int two_pass, double* d_cr,
                           double* d_out, cudaStream_t s) {
-  const long long n = c->V * 12;
+  typedef typename VecT<R>::type E;
+  const long long n = nel<R>(c);
   const unsigned grid = blas_grid(n);
   {
-    ProfScope ps(c, QCD_KERNEL_BLAS, s, 64.0 * n, 8.0 * n);
-    normalise_update_kernel<<<grid, kBlasThreads, 0, s>>>((double2*)chi, (double2*)rho, d_gs, two_pass, d_cr, n,
-                                                          part);
+    ProfScope ps(c, QCD_KERNEL_BLAS, s, 4.0 * sizeof(E) * n, 8.0 * c->V * 12);
+    normalise_update_kernel<R><<<grid, kBlasThreads, 0, s>>>((E*)chi, (E*)rho, d_gs, two_pass, d_cr, n, part);
     QCD_LAUNCHED();
   }
   return reduce_partials(part, (int)grid, 1, 1, d_out, s);
 }
 
-int blas_multi_axpy(qcd_ctx* c, const double* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s) {
-  const long long n = c->V * 12;
+template <typename R>
+int blas_multi_axpy(qcd_ctx* c, const R* const* phi, int k, const double* d_gamma, R* x, cudaStream_t s) {
+  typedef typename VecT<R>::type E;
+  const long long n = nel<R>(c);
   const unsigned grid = blas_grid(n);
   int done = 0;
   while (done < k) {
     int kk = k - done < 16 ? k - done : 16;
-    VecList vl = make_list(phi + done, kk);
-    ProfScope ps(c, QCD_KERNEL_BLAS, s, 16.0 * n * (kk + 2), 8.0 * n * kk);
+    auto vl = make_list<R>(phi + done, kk);
+    ProfScope ps(c, QCD_KERNEL_BLAS, s, sizeof(E) * (double)n * (kk + 2), 8.0 * c->V * 12 * kk);
     if (kk <= 4)
-      multi_axpy_kernel<4><<<grid, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, n);
+      multi_axpy_kernel<R, 4><<<grid, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (E*)x, n);
     else if (kk <= 8)
-      multi_axpy_kernel<8><<<grid, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, n);
+      multi_axpy_kernel<R, 8><<<grid, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (E*)x, n);
     else
-      multi_axpy_kernel<16><<<grid, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, n);
+      multi_axpy_kernel<R, 16><<<grid, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (E*)x, n);
     QCD_LAUNCHED();
     done += kk;
   }
   return QCD_OK;
 }
 
-int blas_norm2(qcd_ctx* c, double* part, const double* v, double* d_out, cudaStream_t s) {
-  const long long n = c->V * 12;
+int blas_refine_update(qcd_ctx* c, const float* const* phi, int k, const double* d_gamma, const double* d_rn2,
+                       double* x, cudaStream_t s) {
+  const long long n = nel<float>(c);
+  const unsigned grid = blas_grid(n);
+  int done = 0;
+  while (done < k) {
+    int kk = k - done < 16 ? k - done : 16;
+    auto vl = make_list<float>(phi + done, kk);
+    ProfScope ps(c, QCD_KERNEL_BLAS, s, 16.0 * n * kk + 64.0 * n, 8.0 * c->V * 12 * kk);
+    if (kk <= 4)
+      refine_update_kernel<4><<<grid, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, d_rn2, (double2*)x, c->g.Vb, n);
+    else if (kk <= 8)
+      refine_update_kernel<8><<<grid, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, d_rn2, (double2*)x, c->g.Vb, n);
+    else
+      refine_update_kernel<16><<<grid, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, d_rn2, (double2*)x, c->g.Vb,
+                                                             n);
+    QCD_LAUNCHED();
+    done += kk;
+  }
+  return QCD_OK;
+}
+
+int blas_demote_normalised(qcd_ctx* c, const double* r, const double* d_rn2, float* out, cudaStream_t s) {
+  const long long n = nel<float>(c);
+  ProfScope ps(c, QCD_KERNEL_BLAS, s, 48.0 * n, 0.0);
+  demote_normalised_kernel<<<blas_grid(n), kBlasThreads, 0, s>>>((const double2*)r, d_rn2, (float4*)out, c->g.Vb, n);
+  QCD_LAUNCHED();
+  return QCD_OK;
+}
+
+template <typename R>
+int blas_norm2(qcd_ctx* c, double* part, const R* v, double* d_out, cudaStream_t s) {
+  typedef typename VecT<R>::type E;
+  const long long n = nel<R>(c);
   const unsigned grid = blas_grid(n);
   {
-    ProfScope ps(c, QCD_KERNEL_BLAS, s, 16.0 * n, 4.0 * n);
-    norm2_kernel<<<grid, kBlasThreads, 0, s>>>((const double2*)v, n, part);
+    ProfScope ps(c, QCD_KERNEL_BLAS, s, sizeof(E) * (double)n, 4.0 * c->V * 12);
+    norm2_kernel<R><<<grid, kBlasThreads, 0, s>>>((const E*)v, n, part);
     QCD_LAUNCHED();
   }
   return reduce_partials(part, (int)grid, 1, 1, d_out, s);
@@ -375,5 +528,19 @@ int fgcr_backsub(const double* d_a1, const double* d_a2, const double* d_cr, int
   QCD_LAUNCHED();
   return QCD_OK;
 }
+
+#define QCD_BLAS_INST(R)                                                                                              \
+  template int blas_multidot<R>(qcd_ctx*, double*, const R* const*, int, const R*, double*, cudaStream_t,            \
+                                const double*, double*);                                                              \
+  template int blas_axpy_dot<R>(qcd_ctx*, double*, const R* const*, int, const double*, R*, double*, cudaStream_t);  \
+  template int blas_axpy_norm_dot<R>(qcd_ctx*, double*, const R* const*, int, const double*, R*, const R*, double*,   \
+                                     cudaStream_t, const double*);                                                    \
+  template int blas_normalise_update<R>(qcd_ctx*, double*, R*, R*, const double*, int, double*, double*,             \
+                                        cudaStream_t);                                                                \
+  template int blas_multi_axpy<R>(qcd_ctx*, const R* const*, int, const double*, R*, cudaStream_t);                  \
+  template int blas_norm2<R>(qcd_ctx*, double*, const R*, double*, cudaStream_t);
+QCD_BLAS_INST(double)
+QCD_BLAS_INST(float)
+#undef QCD_BLAS_INST
 
 }  // namespace qcd

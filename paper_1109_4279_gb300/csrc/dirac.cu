@@ -65,15 +65,27 @@ __device__ __forceinline__ Spinor<T> dirac_site(const Geom& g, const void* U, co
   return o;
 }
 
+// one thread per site; with nrhs > 1 the thread applies the operator to every
+// right-hand side in turn (fields nrhs apart by `stride` sites), so the
+// site's links and clover block come from HBM once and from L1 afterwards
 template <int P, int DAG>
 __global__ void __launch_bounds__(512) dirac_kernel(Geom g, const void* __restrict__ U, FieldPtr A, FieldPtr in,
-                                                    FieldPtr out) {
+                                                    FieldPtr out, int nrhs) {
   typedef typename Arith<P>::T T;
   long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
-  Spinor<T> o = dirac_site<P, DAG, T>(g, U, A, in, blk, r);
-  store_spinor<P, T>(out, g.Vb, blk, r, o);
+  constexpr int NC = P == P64 ? 12 : (P == P32 ? 6 : 3);
+#pragma unroll 1
+  for (int k = 0; k < nrhs; ++k) {
+    FieldPtr fi = in, fo = out;
+    fi.data = (char*)in.data + (size_t)k * g.V * NC * 16;
+    fo.data = (char*)out.data + (size_t)k * g.V * NC * 16;
+    if (in.norm) fi.norm = in.norm + (size_t)k * g.V;
+    if (out.norm) fo.norm = out.norm + (size_t)k * g.V;
+    Spinor<T> o = dirac_site<P, DAG, T>(g, U, A, fi, blk, r);
+    store_spinor<P, T>(fo, g.Vb, blk, r, o);
+  }
 }
 
 // deterministic block sum of a double: warp shuffles, then warps in order
@@ -119,21 +131,24 @@ static double bytes_per_site(int prec) {
   return 2 * (24 * 2 + 4) + 4 * 12 * 2 + (72 * 2 + 4);
 }
 
-int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s) {
+int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s, int nrhs) {
   const int prec = in.prec;
-  if (out.prec != prec || in.nreal != 24 || out.nreal != 24) return QCD_ERR_ARG;
+  if (out.prec != prec || in.nreal != 24 || out.nreal != 24 || nrhs < 1) return QCD_ERR_ARG;
   QCD_TRY(ensure_gauge(c, prec, s));
   QCD_TRY(ensure_clover(c, prec, s));
   const int threads = c->dirac_threads[prec];
   const unsigned grid = (unsigned)((c->V + threads - 1) / threads);
   const void* U = c->U[prec];
   FieldPtr A = c->A[prec].ptr();
-  ProfScope ps(c, QCD_KERNEL_DIRAC, s, bytes_per_site(prec) * (double)c->V, 1824.0 * (double)c->V);
+  // algorithmic bytes: links and clover once, spinors per right-hand side
+  const double spin = prec == P64 ? 384 : (prec == P32 ? 192 : 104);
+  const double bytes = ((bytes_per_site(prec) - spin) + spin * nrhs) * (double)c->V;
+  ProfScope ps(c, QCD_KERNEL_DIRAC, s, bytes, 1824.0 * (double)c->V * nrhs);
 #define LAUNCH(PP)                                                                                 \
   if (dagger)                                                                                      \
-    dirac_kernel<PP, 1><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr());                 \
+    dirac_kernel<PP, 1><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);           \
   else                                                                                             \
-    dirac_kernel<PP, 0><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr());
+    dirac_kernel<PP, 0><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);
   switch (prec) {
     case P64: LAUNCH(P64); break;
     case P32: LAUNCH(P32); break;

@@ -72,7 +72,7 @@ struct Workspace {
   SapWork sap;
   int nkv = 0;
   Rec b, x, r, rho, tmp64;
-  Rec lo_in, lo_out;  // reduced-precision operator scratch
+  int rprec = P64;    // precision of rho, phi_k, chi_k: P64, or P32 for the refinement scheme
   std::vector<Rec> phi, chi;
   double* d_a1 = nullptr;  // [nkv][nkv] complex, first Gram-Schmidt pass
   double* d_a2 = nullptr;  // [nkv][nkv] complex, second pass
@@ -90,6 +90,7 @@ struct Workspace {
 
 struct qcd_field {
   qcd_ctx* ctx;
+  int nrhs = 1;  // fields back to back
   qcd::Rec rec;
 };
 
@@ -149,7 +150,8 @@ int ensure_clover(qcd_ctx* c, int prec, cudaStream_t s);
 
 // ---- dirac.cu
 // out = D in (dagger: D^+); fields in one precision
-int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s);
+// nrhs > 1: in/out hold nrhs fields back to back (V sites apart)
+int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s, int nrhs = 1);
 // r = b - D x and |r|^2 partial sums (FP64); optional second output of D x
 int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s);
 
@@ -157,26 +159,38 @@ int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& 
 int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s);
 int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec, cudaStream_t s);
 
-// ---- blas.cu (FP64 fields of the context, 24 reals per site)
+// ---- blas.cu: fields of 24 reals per site, R = double (FP64 layout) or
+// float (FP32 layout, the recursion of the mixed-precision scheme).
 // Gram-Schmidt building blocks.  cond (optional) = {|chi|^2, |chi'|^2}: the
 // call is skipped unless |chi'|^2 < |chi|^2 / 2 (second pass, DGKS criterion).
 // d_out[j] = (v_j, w) for j < k (complex); d_norm (optional) = |w|^2
-int blas_multidot(qcd_ctx* c, double* part, const double* const* v, int k, const double* w, double* d_out, cudaStream_t s,
+template <typename R>
+int blas_multidot(qcd_ctx* c, double* part, const R* const* v, int k, const R* w, double* d_out, cudaStream_t s,
                   const double* cond = nullptr, double* d_norm = nullptr);
 // w -= sum_j coef[j] v_j (coef on device, complex); then d_out[j] = (v_j, w) for j < k
-int blas_axpy_dot(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w,
-                  double* d_out, cudaStream_t s);
+template <typename R>
+int blas_axpy_dot(qcd_ctx* c, double* part, const R* const* v, int k, const double* d_coef, R* w, double* d_out,
+                  cudaStream_t s);
 // w -= sum_j coef[j] v_j; d_out = {|w|^2, (w, rho)}
-int blas_axpy_norm_dot(qcd_ctx* c, double* part, const double* const* v, int k, const double* d_coef, double* w,
-                       const double* rho, double* d_out, cudaStream_t s, const double* cond = nullptr);
+template <typename R>
+int blas_axpy_norm_dot(qcd_ctx* c, double* part, const R* const* v, int k, const double* d_coef, R* w, const R* rho,
+                       double* d_out, cudaStream_t s, const double* cond = nullptr);
 // gs = {|chi|^2, pass-1 {|chi'|^2, (chi', rho)}, pass-2 {...}}: picks the final
 // coefficients into cr, chi /= |chi|, rho -= (chi, rho) chi, d_out = |rho|^2
-int blas_normalise_update(qcd_ctx* c, double* part, double* chi, double* rho, const double* d_gs, int two_pass, double* d_cr,
+template <typename R>
+int blas_normalise_update(qcd_ctx* c, double* part, R* chi, R* rho, const double* d_gs, int two_pass, double* d_cr,
                           double* d_out, cudaStream_t s);
 // x += sum_j gamma_j phi_j (gamma on device)
-int blas_multi_axpy(qcd_ctx* c, const double* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s);
+template <typename R>
+int blas_multi_axpy(qcd_ctx* c, const R* const* phi, int k, const double* d_gamma, R* x, cudaStream_t s);
+// iterative refinement: x64 += sqrt(*d_rn2) sum_j gamma_j phi_j (FP32 phi_j)
+int blas_refine_update(qcd_ctx* c, const float* const* phi, int k, const double* d_gamma, const double* d_rn2,
+                       double* x, cudaStream_t s);
+// out32 = r64 / sqrt(*d_rn2)
+int blas_demote_normalised(qcd_ctx* c, const double* r, const double* d_rn2, float* out, cudaStream_t s);
 // norm2
-int blas_norm2(qcd_ctx* c, double* part, const double* v, double* d_out, cudaStream_t s);
+template <typename R>
+int blas_norm2(qcd_ctx* c, double* part, const R* v, double* d_out, cudaStream_t s);
 // y = g5 x (in place allowed)
 int blas_gamma5(qcd_ctx* c, const double* x, double* y, int nsites_layout, cudaStream_t s);
 // small dense solve of the FGCR triangular system on the device

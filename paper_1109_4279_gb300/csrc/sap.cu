@@ -32,7 +32,8 @@ struct SapArgs {
   Geom g;
   int colour;           // blocks with (n0 + n1 + n2 + n3) % 2 == colour are solved
   int nmr;              // MR steps per block
-  int read_eta;         // residual source: 1 = eta (FP64), 0 = rho_sap
+  int read_eta;         // residual source: 1 = eta, 0 = rho_sap
+  int io32;             // eta and out are FP32 fields (else FP64)
   int faces_in;         // add face contributions of the other colour
   int faces_out;        // write this block's face contributions
   int write_rho;        // store the block residual
@@ -123,6 +124,11 @@ struct ExpandedStage {
   T* U;
   T* A;
   int Vb;
+  __device__ __forceinline__ void base_init(unsigned char* p, int vb) {
+    U = (T*)p;
+    A = U + 4 * 18 * vb;
+    Vb = vb;
+  }
   static constexpr size_t bytes(int Vb) { return sizeof(T) * (size_t)(4 * 18 + 72) * Vb; }
   __device__ __forceinline__ SU3<T> link(int r, int mu) const {
     SU3<T> u;
@@ -182,6 +188,35 @@ struct HalfStage {
   }
 };
 
+// 16-bit, links expanded once at stage-in: links [4 mu][9][Vb] as 16-bit
+// complex pairs (all three rows), clover as in HalfStage.  The compressed
+// links arrive by bulk copy in a landing zone and are rebuilt there into full
+// matrices, so no hop pays for the third row.
+template <int P>
+struct HalfExpStage {
+  const unsigned char* base;
+  int Vb;
+  __device__ __forceinline__ void base_init(unsigned char* p, int vb) {
+    base = p;
+    Vb = vb;
+  }
+  typedef typename Storage<P>::real hr;
+  static constexpr size_t bytes(int Vb) { return (size_t)(144 + 144 + 4) * Vb; }
+  __device__ __forceinline__ SU3<float> link(int r, int mu) const {
+    const uint32_t* p = (const uint32_t*)base + (mu * 9) * Vb + r;
+    SU3<float> u;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const uint32_t v = p[k * Vb];
+      const hr* h = reinterpret_cast<const hr*>(&v);
+      u.m[k / 3][k % 3] = {to_f<P>(h[0]), to_f<P>(h[1])};
+    }
+    return u;
+  }
+  __device__ __forceinline__ const uint4* clover_chunks() const { return (const uint4*)(base + 144 * Vb); }
+  __device__ __forceinline__ const float* clover_scales() const { return (const float*)(base + 288 * Vb); }
+};
+
 // ------------------------------------------------------------------------
 // bulk copy global -> shared with an mbarrier (TMA, non-tensor form)
 // ------------------------------------------------------------------------
@@ -222,22 +257,55 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b) {
   return true;
 }
 
-// issue the bulk copies of a block's 16-bit links and clover (thread 0 only)
+// issue the bulk copies of a block's 16-bit links (to `links`) and clover
+// blocks with their scales (to `clover`), thread 0 only
 template <int P>
-__device__ __forceinline__ void stage_issue(const SapArgs& a, int blk, unsigned char* dst, uint64_t* bar) {
+__device__ __forceinline__ void stage_issue(const SapArgs& a, int blk, unsigned char* links, unsigned char* clover,
+                                            uint64_t* bar) {
   const int Vb = a.g.Vb;
   const unsigned char* srcs[3] = {(const unsigned char*)a.U + (size_t)blk * 96 * Vb,
                                   (const unsigned char*)a.Ahat.data + (size_t)blk * 144 * Vb,
                                   (const unsigned char*)(a.Ahat.norm + (size_t)blk * Vb)};
+  unsigned char* dsts[3] = {links, clover, clover + 144 * Vb};
   const uint32_t sizes[3] = {(uint32_t)(96 * Vb), (uint32_t)(144 * Vb), (uint32_t)(4 * Vb)};
   mbar_expect_tx(bar, sizes[0] + sizes[1] + sizes[2]);
-  size_t off = 0;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 3; ++k)
     for (uint32_t o = 0; o < sizes[k]; o += 16384) {
       const uint32_t n = sizes[k] - o < 16384 ? sizes[k] - o : 16384;
-      bulk_copy_g2s(dst + off + o, srcs[k] + o, n, bar);
+      bulk_copy_g2s(dsts[k] + o, srcs[k] + o, n, bar);
     }
-    off += sizes[k];
+}
+
+// rebuild the compressed 16-bit links of the landing zone (rows 0-1, layout of
+// the storage format) into full 16-bit matrices [mu][9][Vb]
+template <int P>
+__device__ __forceinline__ void expand_links(const unsigned char* land, unsigned char* out, int Vb) {
+  typedef typename Storage<P>::real hr;
+  for (int r = threadIdx.x; r < Vb; r += blockDim.x) {
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      const uint4 a = ((const uint4*)land)[mu * Vb + r];
+      const uint2 b = ((const uint2*)(land + 64 * Vb))[mu * Vb + r];
+      const hr* ha = reinterpret_cast<const hr*>(&a);
+      const hr* hb = reinterpret_cast<const hr*>(&b);
+      SU3<float> u;
+      u.m[0][0] = {to_f<P>(ha[0]), to_f<P>(ha[1])};
+      u.m[0][1] = {to_f<P>(ha[2]), to_f<P>(ha[3])};
+      u.m[0][2] = {to_f<P>(ha[4]), to_f<P>(ha[5])};
+      u.m[1][0] = {to_f<P>(ha[6]), to_f<P>(ha[7])};
+      u.m[1][1] = {to_f<P>(hb[0]), to_f<P>(hb[1])};
+      u.m[1][2] = {to_f<P>(hb[2]), to_f<P>(hb[3])};
+      reconstruct(u);
+      uint32_t* o = (uint32_t*)out + (mu * 9) * Vb + r;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        uint32_t v;
+        hr* h = reinterpret_cast<hr*>(&v);
+        h[0] = from_f<P>(u.m[k / 3][k % 3].re);
+        h[1] = from_f<P>(u.m[k / 3][k % 3].im);
+        o[k * Vb] = v;
+      }
+    }
   }
 }
 
@@ -309,41 +377,6 @@ __device__ __forceinline__ Half<T> half_of(const Spinor<T>& v, int hf) {
 }
 
 template <typename T>
-__device__ __forceinline__ T shfl_pair(T v) {
-  return __shfl_xor_sync(0xffffffffu, v, 1);
-}
-
-// own half of the pair's summed partial spinors
-template <typename T>
-__device__ __forceinline__ Half<T> pair_reduce(const Spinor<T>& acc, int hf) {
-  Half<T> mine = half_of(acc, hf);
-  const Half<T> theirs = half_of(acc, 1 - hf);
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      mine.c[s][c].re += shfl_pair(theirs.c[s][c].re);
-      mine.c[s][c].im += shfl_pair(theirs.c[s][c].im);
-    }
-  return mine;
-}
-
-// full spinor from the two owned halves of a pair
-template <typename T>
-__device__ __forceinline__ Spinor<T> pair_full(const Half<T>& own, int hf) {
-  Spinor<T> v;
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const cpx<T> o = {shfl_pair(own.c[s][c].re), shfl_pair(own.c[s][c].im)};
-      v.c[s][c] = hf ? o : own.c[s][c];
-      v.c[2 + s][c] = hf ? own.c[s][c] : o;
-    }
-  return v;
-}
-
-template <typename T>
 __device__ __forceinline__ Half<T> half_axpy(const Half<T>& a, const Half<T>& b, T s) {  // a + s b
   Half<T> o;
 #pragma unroll
@@ -375,13 +408,13 @@ __device__ __forceinline__ Half<T> clover_half(const ExpandedStage<T>& st, int r
 }
 
 template <int P>
-__device__ __forceinline__ Half<float> clover_half(const HalfStage<P>& st, int r, int hf, const Half<float>& in) {
-  typedef typename HalfStage<P>::hr hr;
-  const uint4* A = (const uint4*)(st.base + 96 * st.Vb);
+__device__ __forceinline__ Half<float> clover_half_native(const uint4* A, const float* scales, int Vb, int r, int hf,
+                                                          const Half<float>& in) {
+  typedef typename Storage<P>::real hr;
   float h40[40];  // chunks 4 hf .. 4 hf + 4 hold this chiral block's 36 values at offset 4 hf
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    const uint4 v = A[(4 * hf + k) * st.Vb + r];
+    const uint4 v = A[(4 * hf + k) * Vb + r];
     const hr* h = reinterpret_cast<const hr*>(&v);
 #pragma unroll
     for (int e = 0; e < 8; ++e) h40[8 * k + e] = to_f<P>(h[e]);
@@ -390,7 +423,7 @@ __device__ __forceinline__ Half<float> clover_half(const HalfStage<P>& st, int r
 #pragma unroll
   for (int k = 0; k < 36; ++k) c[k] = hf ? h40[k + 4] : h40[k];
   Half<float> o = clover_half_apply(c, in);
-  const float s = ((const float*)(st.base + 240 * st.Vb))[r];
+  const float s = scales[r];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -398,39 +431,89 @@ __device__ __forceinline__ Half<float> clover_half(const HalfStage<P>& st, int r
   return o;
 }
 
-// partial hops of the block operator at site r over directions mu = 2 hf + m:
-//   sum_mu [U_mu(r)(1 - g) v(r + mu) + U_mu(r - mu)^+ (1 + g) v(r - mu)]
+template <int P>
+__device__ __forceinline__ Half<float> clover_half(const HalfStage<P>& st, int r, int hf, const Half<float>& in) {
+  return clover_half_native<P>((const uint4*)(st.base + 96 * st.Vb), (const float*)(st.base + 240 * st.Vb), st.Vb, r,
+                               hf, in);
+}
+
+template <int P>
+__device__ __forceinline__ Half<float> clover_half(const HalfExpStage<P>& st, int r, int hf, const Half<float>& in) {
+  return clover_half_native<P>(st.clover_chunks(), st.clover_scales(), st.Vb, r, hf, in);
+}
+
+// one direction of the block operator's hops at site r:
+//   U_mu(r)(1 - g) v(r + mu) + U_mu(r - mu)^+ (1 + g) v(r - mu)
 // (Dirichlet: hops leaving the block are absent); v lives on the opposite
-// parity at src[site - off]; pk[m] = forward | backward << 16 indices into
-// src, 0xffff when the neighbour is outside the block.
+// parity at src[site - off]; pm = forward | backward << 16 indices into src,
+// 0xffff when the neighbour is outside the block.
+template <int MU, typename T, typename ST>
+__device__ __forceinline__ void hop_dir(const ST& st, int n, int r, const T* src, int pm, int off, Spinor<T>& acc) {
+  const int kf = pm & 0xffff, kb = (pm >> 16) & 0xffff;
+  if (kf != 0xffff) {
+    const Half<T> h = project<MU, -1>(s_spinor(src, n, kf));
+    expand_add<MU, -1>(acc, umul(st.link(r, MU), h), T(1));
+  }
+  if (kb != 0xffff) {
+    const Half<T> h = project<MU, +1>(s_spinor(src, n, kb));
+    expand_add<MU, +1>(acc, udmul(st.link(kb + off, MU), h), T(1));
+  }
+}
+
+// partial hops over this thread's directions 2 hf, 2 hf + 1 (hf is uniform
+// across a warp, so both branches run without divergence)
 template <typename T, typename ST>
 __device__ __forceinline__ Spinor<T> hops_pair(const ST& st, int n, int r, const T* src, const int pk[2], int off,
                                                int hf) {
   Spinor<T> acc;
   zero(acc);
-#pragma unroll 1
-  for (int m = 0; m < 2; ++m) {
-    const int mu = 2 * hf + m;
-    const SpinDir<T> d = spin_dir<T>(mu);
-    const int pm = m ? pk[1] : pk[0];
-    const int kf = pm & 0xffff, kb = (pm >> 16) & 0xffff;
-    if (kf != 0xffff) {
-      const Half<T> h = project_rt<-1>(s_spinor(src, n, kf), d);
-      expand_add_rt<-1>(acc, umul(st.link(r, mu), h), T(1), d);
-    }
-    if (kb != 0xffff) {
-      const Half<T> h = project_rt<+1>(s_spinor(src, n, kb), d);
-      expand_add_rt<+1>(acc, udmul(st.link(kb + off, mu), h), T(1), d);
-    }
+  if (hf) {
+    hop_dir<2, T>(st, n, r, src, pk[0], off, acc);
+    hop_dir<3, T>(st, n, r, src, pk[1], off, acc);
+  } else {
+    hop_dir<0, T>(st, n, r, src, pk[0], off, acc);
+    hop_dir<1, T>(st, n, r, src, pk[1], off, acc);
   }
   return acc;
+}
+
+// Pair exchange through shared memory: xb holds [2][12][np] reals (np = site
+// pairs per half, a multiple of 32).  Both calls below contain a barrier and
+// must be reached by every thread of the CTA.
+
+// own half of the pair's summed partial spinors (thread (hf, i) stores the
+// part its partner owns in slot hf and reads its partner's slot 1 - hf)
+template <typename T>
+__device__ __forceinline__ Half<T> pair_reduce_s(const Spinor<T>& acc, int hf, int i, int np, T* xb) {
+  s_half_store(xb, np, i, hf, half_of(acc, 1 - hf));
+  __syncthreads();
+  return half_axpy(half_of(acc, hf), s_half(xb, np, i, 1 - hf), T(1));
+}
+
+// full spinor from the owned halves of a pair (ends with a barrier, so the
+// buffer can be reused at once)
+template <typename T>
+__device__ __forceinline__ Spinor<T> pair_full_s(const Half<T>& own, int hf, int i, int np, T* xb) {
+  s_half_store(xb, np, i, hf, own);
+  __syncthreads();
+  const Half<T> o = s_half(xb, np, i, 1 - hf);
+  __syncthreads();
+  Spinor<T> v;
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v.c[s][c] = hf ? o.c[s][c] : own.c[s][c];
+      v.c[2 + s][c] = hf ? own.c[s][c] : o.c[s][c];
+    }
+  return v;
 }
 
 // owned half of -1/2 (sum of hops) at site r
 template <typename T, typename ST>
 __device__ __forceinline__ Half<T> block_hops(const ST& st, int n, int r, const T* src, const int pk[2], int off,
-                                              int hf) {
-  Half<T> h = pair_reduce(hops_pair<T>(st, n, r, src, pk, off, hf), hf);
+                                              int hf, int i, int np, T* xb) {
+  Half<T> h = pair_reduce_s(hops_pair<T>(st, n, r, src, pk, off, hf), hf, i, np, xb);
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -576,7 +659,7 @@ __device__ __forceinline__ void send_faces(const SapArgs& a, const ST& st, int b
 
 template <int P>
 struct StageFor {
-  typedef HalfStage<P> type;
+  typedef HalfExpStage<P> type;
 };
 template <>
 struct StageFor<P32> {
@@ -587,6 +670,9 @@ struct StageFor<P64> {
   typedef ExpandedStage<double> type;
 };
 
+// site pairs per half-CTA: Vbh rounded up to whole warps
+__host__ __device__ __forceinline__ int pairs_per_half(int Vbh) { return (Vbh + 31) / 32 * 32; }
+
 template <int P, typename T>
 __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   typedef typename StageFor<P>::type ST;
@@ -594,23 +680,19 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Geom& g = a.g;
   const int Vb = g.Vb, Vbh = g.Vbh;
+  const int np = pairs_per_half(Vbh);
 
-  // shared memory: staged block fields, then the FP vectors r (even), t (odd),
-  // rho_o (odd source), the reduction scratch and the staging barrier
+  // shared memory: staged block fields, then the FP vectors r (even sites),
+  // t (odd sites), the pair-exchange buffer, the reduction scratch and the
+  // staging barrier.  With 16-bit fields the compressed links land in the
+  // vector area first and are expanded into the link area.
   ST st;
   const size_t stage_bytes = ST::bytes(Vb);
-  if constexpr (kHalf) {
-    st.base = smem_raw;
-    st.Vb = Vb;
-  } else {
-    st.U = (T*)smem_raw;
-    st.A = st.U + 4 * 18 * Vb;
-    st.Vb = Vb;
-  }
+  st.base_init(smem_raw, Vb);
   T* s_r = (T*)(smem_raw + stage_bytes);
   T* s_t = s_r + 24 * Vbh;
-  T* s_rho_o = s_t + 24 * Vbh;
-  T* s_red = s_rho_o + 24 * Vbh;
+  T* s_x = s_t + 24 * Vbh;  // [2][12][np]
+  T* s_red = s_x + 24 * np;
   uint64_t* bar = (uint64_t*)(s_red + 3 * 32);
 
   // block of the requested colour: pairs (2k, 2k+1) differ in n3 only, hence in colour
@@ -626,7 +708,7 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   if constexpr (kHalf) {
     if (threadIdx.x == 0) {
       mbar_init(bar, 1);
-      stage_issue<P>(a, blk, smem_raw, bar);
+      stage_issue<P>(a, blk, (unsigned char*)s_r, (unsigned char*)st.base + 144 * Vb, bar);
     }
   } else {
     for (int r = threadIdx.x; r < Vb; r += blockDim.x) {
@@ -647,11 +729,11 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
     }
   }
 
-  // thread pair i owns even site i and odd site Vbh + i, half hf of their
-  // spin components and the hops in directions 2 hf, 2 hf + 1.  Pairs with
-  // i >= Vbh (only for blocks of fewer than 32 sites) compute on site 0 and
-  // store nothing, so that every lane takes part in the shuffles.
-  const int i = threadIdx.x >> 1, hf = threadIdx.x & 1;
+  // site pair i owns even site i and odd site Vbh + i; thread half hf (uniform
+  // across a warp) holds spin components 2 hf, 2 hf + 1 and computes the hops
+  // in directions 2 hf, 2 hf + 1.  Pairs with i >= Vbh (blocks of fewer than
+  // 64 sites) compute on site 0 and store nothing.
+  const int hf = threadIdx.x / np, i = threadIdx.x - hf * np;
   const bool act = i < Vbh;
   const int re = act ? i : 0, ro = Vbh + re;
 
@@ -689,7 +771,17 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   Half<T> rho_e, rho_o;
   {
     Spinor<T> fe, fo;
-    if (a.read_eta) {
+    if (a.read_eta && a.io32) {
+      const Spinor<float> de = load_spinor<P32, float>(a.eta, Vb, blk, re);
+      const Spinor<float> dd = load_spinor<P32, float>(a.eta, Vb, blk, ro);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          fe.c[s][c] = {(T)de.c[s][c].re, (T)de.c[s][c].im};
+          fo.c[s][c] = {(T)dd.c[s][c].re, (T)dd.c[s][c].im};
+        }
+    } else if (a.read_eta) {
       const Spinor<double> de = load_spinor<P64, double>(a.eta, Vb, blk, re);
       const Spinor<double> dd = load_spinor<P64, double>(a.eta, Vb, blk, ro);
 #pragma unroll
@@ -715,20 +807,18 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
       mbar_wait_bounded(bar);  // let copies still in flight land before the CTA exits
       return;
     }
-  } else {
-    __syncthreads();
-  }
-  if (a.faces_in) {
-    rho_e = half_axpy(rho_e, pair_reduce(receive_faces<T>(a, st, blk, re, ye, n, hf), hf), T(1));
-    rho_o = half_axpy(rho_o, pair_reduce(receive_faces<T>(a, st, blk, ro, yo, n, hf), hf), T(1));
-  }
-  if (act) {
-    s_half_store(s_rho_o, Vbh, i, hf, rho_o);
-    // etahat = rho_e - D_eo A_oo^-1 rho_o: first t = A_oo^-1 rho_o
-    s_half_store(s_t, Vbh, i, hf, clover_half(st, ro, hf, rho_o));
+    expand_links<P>((const unsigned char*)s_r, (unsigned char*)st.base, Vb);
   }
   __syncthreads();
-  Half<T> r = half_axpy(rho_e, block_hops<T>(st, Vbh, re, s_t, pkE, Vbh, hf), T(-1));
+  if (a.faces_in) {
+    rho_e = half_axpy(rho_e, pair_reduce_s(receive_faces<T>(a, st, blk, re, ye, n, hf), hf, i, np, s_x), T(1));
+    __syncthreads();
+    rho_o = half_axpy(rho_o, pair_reduce_s(receive_faces<T>(a, st, blk, ro, yo, n, hf), hf, i, np, s_x), T(1));
+  }
+  // etahat = rho_e - D_eo A_oo^-1 rho_o: first t = A_oo^-1 rho_o
+  if (act) s_half_store(s_t, Vbh, i, hf, clover_half(st, ro, hf, rho_o));
+  __syncthreads();
+  Half<T> r = half_axpy(rho_e, block_hops<T>(st, Vbh, re, s_t, pkE, Vbh, hf, i, np, s_x), T(-1));
   Half<T> x;
 #pragma unroll
   for (int s = 0; s < 2; ++s)
@@ -744,7 +834,7 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   for (int step = 0; step < 2 * a.nmr; ++step) {
     const int ph = step & 1;
     const int pk2[2] = {ph ? pkE[0] : pkO[0], ph ? pkE[1] : pkO[1]};
-    const Half<T> hq = block_hops<T>(st, Vbh, ph ? re : ro, ph ? s_t : s_r, pk2, ph ? Vbh : 0, hf);
+    const Half<T> hq = block_hops<T>(st, Vbh, ph ? re : ro, ph ? s_t : s_r, pk2, ph ? Vbh : 0, hf, i, np, s_x);
     const Half<T> cl = clover_half(st, ph ? re : ro, hf, ph ? r : hq);
     if (ph == 0) {
       if (act) s_half_store(s_t, Vbh, i, hf, cl);
@@ -781,14 +871,16 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   // ---- chi_o = A_oo^-1 (rho_o - D_oe chi_e)
   if (act) s_half_store(s_r, Vbh, i, hf, x);
   __syncthreads();
-  const Half<T> chi_o = clover_half(st, ro, hf, half_axpy(rho_o, block_hops<T>(st, Vbh, ro, s_r, pkO, 0, hf), T(-1)));
+  const Half<T> chi_o =
+      clover_half(st, ro, hf, half_axpy(rho_o, block_hops<T>(st, Vbh, ro, s_r, pkO, 0, hf, i, np, s_x), T(-1)));
+  __syncthreads();
 
   // ---- outputs: solution, block residual (r on even, 0 on odd), faces
   constexpr int PS = PsiPrec<P>::value;
   typedef typename std::conditional<PS == P64, double, float>::type TS;
-  const Spinor<T> x_full = pair_full(x, hf);
-  const Spinor<T> chio_full = pair_full(chi_o, hf);
-  const Spinor<T> r_full = pair_full(r, hf);
+  const Spinor<T> x_full = pair_full_s(x, hf, i, np, s_x);
+  const Spinor<T> chio_full = pair_full_s(chi_o, hf, i, np, s_x);
+  const Spinor<T> r_full = pair_full_s(r, hf, i, np, s_x);
   if (!act) return;
 #pragma unroll 1
   for (int half = 0; half < 2; ++half) {
@@ -802,6 +894,13 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
     if (a.psi_mode == 1 || a.psi_mode == 3) v = half_axpy(v, g_half<PS, TS>(a.psi, Vb, blk, rs, hf), TS(1));
     if (a.psi_mode <= 1) {
       g_half_store<PS, TS>(a.psi, Vb, blk, rs, hf, v);
+    } else if (a.io32) {
+      Half<float> fv;
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) fv.c[s][c] = {(float)v.c[s][c].re, (float)v.c[s][c].im};
+      g_half_store<P32, float>(a.out, Vb, blk, rs, hf, fv);
     } else {
       Half<double> dv;
 #pragma unroll
@@ -826,7 +925,8 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
 template <int P, typename T>
 static size_t sap_smem_bytes(const Geom& g) {
   typedef typename StageFor<P>::type ST;
-  return ST::bytes(g.Vb) + sizeof(T) * (3 * 24 * (size_t)g.Vbh + 3 * 32) + 16;
+  const int np = pairs_per_half(g.Vbh);
+  return ST::bytes(g.Vb) + sizeof(T) * (2 * 24 * (size_t)g.Vbh + 24 * (size_t)np + 3 * 32) + 16;
 }
 
 template <int P, typename T>
@@ -875,11 +975,12 @@ int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s) {
   return QCD_OK;
 }
 
-// psi64 = M_SAP eta64; allocates nothing once sap_prepare ran for prec
+// psi = M_SAP eta (both FP64 or both FP32 fields); allocates nothing once
+// sap_prepare ran for prec
 int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec,
               cudaStream_t s) {
   const Geom& g = c->g;
-  if (eta64.prec != P64 || psi64.prec != P64) return QCD_ERR_ARG;
+  if (eta64.prec != psi64.prec || (eta64.prec != P64 && eta64.prec != P32)) return QCD_ERR_ARG;
   if (ncy < 1 || nmr < 0) return QCD_ERR_ARG;
   if (w.prec != prec) QCD_TRY(sap_prepare(c, w, prec, s));
   const bool dbl = prec == P64;
@@ -888,6 +989,7 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
   a.nmr = nmr;
   a.U = c->U[prec];
   a.Ahat = c->Ahat[prec].ptr();
+  a.io32 = eta64.prec == P32;
   a.eta = eta64.ptr();
   a.rho = w.rho.ptr();
   a.psi = w.psi.ptr();
@@ -903,7 +1005,7 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
   }
   a.F = off;
   const unsigned grid = (unsigned)(c->nblk / 2);
-  const int threads = 2 * g.Vbh < 32 ? 32 : ((2 * g.Vbh + 31) / 32) * 32;  // two threads per site pair
+  const int threads = 2 * pairs_per_half(g.Vbh);  // two threads per site pair, halves warp-aligned
   // flops (the 1320 + 504 convention): per solved site the Schur operator
   // costs about one D per MR step, plus about one more D for the source and
   // the back-substitution

@@ -9,9 +9,16 @@
 //                                the first cancelled more than half the norm);
 //   chi_k /= |chi_k|;  c_k = (chi_k, rho_k);  rho_{k+1} = rho_k - c_k chi_k.
 // At the end of a cycle the upper-triangular system H gamma = c is solved on
-// the device, x += sum_k gamma_k phi_k, and r = b - D x is recomputed in FP64
-// ("only when the FGCR recursion is restarted, the residue is computed in
-// full double precision", Sec. 4).
+// the device, x += sum_k gamma_k phi_k, and r = b - D x is recomputed in FP64.
+//
+// Two precisions of the recursion:
+//  - FP64 (outer_prec = F64): rho, phi_k, chi_k and every dot product in FP64;
+//  - FP32 (outer_prec = F32), the scheme of Sec. 4 (iterative refinement):
+//    every operation of a cycle is single precision, on the normalised
+//    residual rho_0 = r / |r|; the cycle ends when |rho_k| has dropped by
+//    inner_tol (or below the target); then the FP32 correction
+//    |r| sum_k gamma_k phi_k is added to the FP64 solution and the residue is
+//    recomputed in double precision.
 //
 // Many right-hand sides or lattices (Sec. 4: flexibility in the lattice
 // sizes) are solved in lock step: every iteration is enqueued for all active
@@ -19,6 +26,7 @@
 // concurrently, and one host synchronisation per iteration reads all the
 // recursive residuals.  With use_graphs each problem's iteration k is captured
 // once as a CUDA graph and replayed (one launch instead of ~20).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -32,10 +40,29 @@ size_t partials_for(long long V) {
   return blas > resid ? blas : resid;
 }
 
+static void graphs_clear(Workspace& w) {
+  for (auto g : w.graphs)
+    if (g) cudaGraphExecDestroy(g);
+  w.graphs.clear();
+  w.graph_key = -1;
+}
+
 int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream_t s) {
   const int nkv = sp.nkv;
-  for (Rec* f : {&w.b, &w.x, &w.r, &w.rho})
+  const int rprec = sp.outer_prec == P32 ? P32 : P64;
+  for (Rec* f : {&w.b, &w.x, &w.r})
     if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
+  if (w.rprec != rprec) {  // the recursion vectors change precision: reallocate them
+    graphs_clear(w);
+    rec_free(w.rho);
+    for (auto& r : w.phi) rec_free(r);
+    for (auto& r : w.chi) rec_free(r);
+    w.phi.clear();
+    w.chi.clear();
+    w.nkv = 0;
+    w.rprec = rprec;
+  }
+  if (!w.rho.data) QCD_TRY(rec_alloc(w.rho, rprec, 24, c->V));
   if (!w.d_part) {
     if (cudaMalloc(&w.d_part, sizeof(double) * partials_for(c->V)) != cudaSuccess) {
       cudaGetLastError();
@@ -47,8 +74,8 @@ int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream
     for (int k = w.nkv; k < nkv; ++k) {
       w.phi.emplace_back();
       w.chi.emplace_back();
-      QCD_TRY(rec_alloc(w.phi.back(), P64, 24, c->V));
-      QCD_TRY(rec_alloc(w.chi.back(), P64, 24, c->V));
+      QCD_TRY(rec_alloc(w.phi.back(), rprec, 24, c->V));
+      QCD_TRY(rec_alloc(w.chi.back(), rprec, 24, c->V));
     }
     cudaFree(w.d_a1);
     cudaFree(w.d_a2);
@@ -69,25 +96,12 @@ int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream
   }
   QCD_TRY(ensure_gauge(c, P64, s));
   QCD_TRY(ensure_clover(c, P64, s));
-  if (sp.outer_prec != P64) {
-    QCD_TRY(ensure_gauge(c, sp.outer_prec, s));
-    QCD_TRY(ensure_clover(c, sp.outer_prec, s));
-    if (w.lo_in.prec != sp.outer_prec) {
-      rec_free(w.lo_in);
-      rec_free(w.lo_out);
-      QCD_TRY(rec_alloc(w.lo_in, sp.outer_prec, 24, c->V));
-      QCD_TRY(rec_alloc(w.lo_out, sp.outer_prec, 24, c->V));
-    }
+  if (rprec != P64) {
+    QCD_TRY(ensure_gauge(c, rprec, s));
+    QCD_TRY(ensure_clover(c, rprec, s));
   }
   if (sp.precond == QCD_PRECOND_SAP) QCD_TRY(sap_prepare(c, w.sap, sp.sap_prec, s));
   return QCD_OK;
-}
-
-static void graphs_clear(Workspace& w) {
-  for (auto g : w.graphs)
-    if (g) cudaGraphExecDestroy(g);
-  w.graphs.clear();
-  w.graph_key = -1;
 }
 
 void ws_release(Workspace& w) {
@@ -97,7 +111,7 @@ void ws_release(Workspace& w) {
   if (w.sap.faces) cudaFree(w.sap.faces);
   w.sap.faces = nullptr;
   w.sap.prec = -1;
-  for (Rec* f : {&w.b, &w.x, &w.r, &w.rho, &w.tmp64, &w.lo_in, &w.lo_out}) rec_free(*f);
+  for (Rec* f : {&w.b, &w.x, &w.r, &w.rho, &w.tmp64}) rec_free(*f);
   for (auto& r : w.phi) rec_free(r);
   for (auto& r : w.chi) rec_free(r);
   w.phi.clear();
@@ -109,14 +123,29 @@ void ws_release(Workspace& w) {
   if (w.h_pin) cudaFreeHost(w.h_pin);
   w.h_pin = nullptr;
   w.nkv = 0;
+  w.rprec = P64;
 }
 
-// chi = D phi in the requested outer precision (FP64 default)
-static int outer_apply(qcd_ctx* c, Workspace& w, const Rec& phi, const Rec& chi, int prec, cudaStream_t s) {
-  if (prec == P64) return dirac_apply(c, phi, chi, 0, s);
-  QCD_TRY(convert_rec(c, phi, w.lo_in, s));
-  QCD_TRY(dirac_apply(c, w.lo_in, w.lo_out, 0, s));
-  return convert_rec(c, w.lo_out, chi, s);
+// classical Gram-Schmidt of chi_k against chi_0 .. chi_{k-1}, normalisation
+// and residual update, in the recursion's precision R; the second pass runs
+// (decided on the device) only if the first one cancelled more than half of
+// the squared norm
+template <typename R>
+static int gram_schmidt(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, int k, cudaStream_t s) {
+  const R* chi_p[64];
+  for (int j = 0; j < k; ++j) chi_p[j] = (const R*)w.chi[j].data;
+  R* chik = (R*)w.chi[k].data;
+  R* rho = (R*)w.rho.data;
+  double* a1 = w.d_a1 + 2 * (size_t)k * sp.nkv;
+  double* a2 = w.d_a2 + 2 * (size_t)k * sp.nkv;
+  double* gs = w.d_gs + 8 * (size_t)k;
+  QCD_TRY(blas_multidot<R>(c, w.d_part, chi_p, k, chik, a1, s, nullptr, gs));
+  QCD_TRY(blas_axpy_norm_dot<R>(c, w.d_part, chi_p, k, a1, chik, rho, gs + 1, s));
+  if (k > 0) {
+    QCD_TRY(blas_multidot<R>(c, w.d_part, chi_p, k, chik, a2, s, gs));
+    QCD_TRY(blas_axpy_norm_dot<R>(c, w.d_part, chi_p, k, a2, chik, rho, gs + 4, s, gs));
+  }
+  return blas_normalise_update<R>(c, w.d_part, chik, rho, gs, k > 0, w.d_cr + 3 * k, w.d_rn + k, s);
 }
 
 // enqueue FGCR iteration k of one problem; ends with a copy of |rho_{k+1}|^2
@@ -125,29 +154,16 @@ static int enqueue_iteration(Problem& p, const qcd_solver_params& sp, int k) {
   qcd_ctx* c = p.c;
   Workspace& w = *p.w;
   cudaStream_t s = p.s;
-  const size_t bytes = (size_t)c->V * 24 * sizeof(double);
   if (sp.precond == QCD_PRECOND_SAP) {
     QCD_TRY(sap_apply(c, w.sap, w.rho, w.phi[k], sp.ncy, sp.nmr, sp.sap_prec, s));
   } else {
-    QCD_CUDA(cudaMemcpyAsync(w.phi[k].data, w.rho.data, bytes, cudaMemcpyDeviceToDevice, s));
+    QCD_CUDA(cudaMemcpyAsync(w.phi[k].data, w.rho.data, w.rho.bytes, cudaMemcpyDeviceToDevice, s));
   }
-  QCD_TRY(outer_apply(c, w, w.phi[k], w.chi[k], sp.outer_prec, s));
-  const double* chi_p[64];
-  for (int j = 0; j < k; ++j) chi_p[j] = (const double*)w.chi[j].data;
-  double* chik = (double*)w.chi[k].data;
-  double* a1 = w.d_a1 + 2 * (size_t)k * sp.nkv;
-  double* a2 = w.d_a2 + 2 * (size_t)k * sp.nkv;
-  // classical Gram-Schmidt; the second pass runs (decided on the device) only
-  // if the first one cancelled more than half of the squared norm
-  double* gs = w.d_gs + 8 * (size_t)k;
-  const double* rho_p = (const double*)w.rho.data;
-  QCD_TRY(blas_multidot(c, w.d_part, chi_p, k, chik, a1, s, nullptr, gs));
-  QCD_TRY(blas_axpy_norm_dot(c, w.d_part, chi_p, k, a1, chik, rho_p, gs + 1, s));
-  if (k > 0) {
-    QCD_TRY(blas_multidot(c, w.d_part, chi_p, k, chik, a2, s, gs));
-    QCD_TRY(blas_axpy_norm_dot(c, w.d_part, chi_p, k, a2, chik, rho_p, gs + 4, s, gs));
-  }
-  QCD_TRY(blas_normalise_update(c, w.d_part, chik, (double*)w.rho.data, gs, k > 0, w.d_cr + 3 * k, w.d_rn + k, s));
+  QCD_TRY(dirac_apply(c, w.phi[k], w.chi[k], 0, s));
+  if (w.rprec == P32)
+    QCD_TRY(gram_schmidt<float>(c, w, sp, k, s));
+  else
+    QCD_TRY(gram_schmidt<double>(c, w, sp, k, s));
   QCD_CUDA(cudaMemcpyAsync(w.h_pin + k, w.d_rn + k, sizeof(double), cudaMemcpyDeviceToHost, s));
   return QCD_OK;
 }
@@ -197,6 +213,7 @@ int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool us
   if (sp.nkv < 1 || sp.nkv > 64 || !(sp.tol > 0) || sp.max_restarts < 1) return QCD_ERR_ARG;
   if (sp.precond != QCD_PRECOND_NONE && sp.precond != QCD_PRECOND_SAP) return QCD_ERR_ARG;
   if (sp.outer_prec != P64 && sp.outer_prec != P32) return QCD_ERR_ARG;
+  if (sp.outer_prec == P32 && !(sp.inner_tol > 0 && sp.inner_tol < 1)) return QCD_ERR_ARG;
   if (sp.precond == QCD_PRECOND_SAP && (sp.ncy < 1 || sp.nmr < 0 || sp.sap_prec < P64 || sp.sap_prec > PB16))
     return QCD_ERR_ARG;
   const size_t bytes_of = sizeof(double);
@@ -218,13 +235,34 @@ int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool us
       p.active = false;
     }
   }
-  // |b|, r = b - D x0
+  // |b|^2 and |x0|^2; then r = b - D x0, or r = b without an operator
+  // application when the initial guess is zero
   for (auto& p : probs) {
     if (!p.active) continue;
     Workspace& w = *p.w;
-    int st = blas_norm2(p.c, w.d_part, (const double*)p.b.data, w.d_rn + w.nkv, p.s);
-    if (st == QCD_OK) st = residual64(p.c, w.d_part, p.b, p.x, w.r, w.d_rn + w.nkv + 1, p.s);
-    if (st == QCD_OK && cudaMemcpyAsync(w.h_pin + w.nkv, w.d_rn + w.nkv, 2 * bytes_of, cudaMemcpyDeviceToHost,
+    int st = blas_norm2<double>(p.c, w.d_part, (const double*)p.b.data, w.d_rn + w.nkv, p.s);
+    if (st == QCD_OK) st = blas_norm2<double>(p.c, w.d_part, (const double*)p.x.data, w.d_rn + w.nkv + 3, p.s);
+    if (st == QCD_OK && cudaMemcpyAsync(w.h_pin + w.nkv, w.d_rn + w.nkv, 4 * bytes_of, cudaMemcpyDeviceToHost,
+                                        p.s) != cudaSuccess)
+      st = QCD_ERR_CUDA;
+    if (st != QCD_OK) {
+      p.status = st;
+      p.active = false;
+    }
+  }
+  QCD_TRY(sync_all(probs));
+  for (auto& p : probs) {
+    if (!p.active) continue;
+    Workspace& w = *p.w;
+    int st = QCD_OK;
+    if (w.h_pin[w.nkv + 3] == 0.0) {
+      if (cudaMemcpyAsync(w.r.data, p.b.data, w.r.bytes, cudaMemcpyDeviceToDevice, p.s) != cudaSuccess ||
+          cudaMemcpyAsync(w.d_rn + w.nkv + 1, w.d_rn + w.nkv, bytes_of, cudaMemcpyDeviceToDevice, p.s) != cudaSuccess)
+        st = QCD_ERR_CUDA;
+    } else {
+      st = residual64(p.c, w.d_part, p.b, p.x, w.r, w.d_rn + w.nkv + 1, p.s);
+    }
+    if (st == QCD_OK && cudaMemcpyAsync(w.h_pin + w.nkv + 1, w.d_rn + w.nkv + 1, bytes_of, cudaMemcpyDeviceToHost,
                                         p.s) != cudaSuccess)
       st = QCD_ERR_CUDA;
     if (st != QCD_OK) {
@@ -265,13 +303,21 @@ int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool us
       any |= p.active;
     }
     if (!any) break;
+    // rho_0: the FP64 residual, or r / |r| in FP32; |r|^2 of the cycle start
+    // is in d_rn[nkv + 1] (first cycle) or d_rn[nkv + 2] (after a restart)
     for (auto& p : probs) {
       if (!p.active) continue;
+      Workspace& w = *p.w;
       p.kused = 0;
       p.cycle_done = false;
-      if (cudaMemcpyAsync(p.w->rho.data, p.w->r.data, (size_t)p.c->V * 24 * sizeof(double), cudaMemcpyDeviceToDevice,
-                          p.s) != cudaSuccess) {
-        p.status = QCD_ERR_CUDA;
+      const double* rn2 = w.d_rn + w.nkv + (p.info.restarts == 0 ? 1 : 2);
+      int st = QCD_OK;
+      if (w.rprec == P32)
+        st = blas_demote_normalised(p.c, (const double*)w.r.data, rn2, (float*)w.rho.data, p.s);
+      else if (cudaMemcpyAsync(w.rho.data, w.r.data, w.r.bytes, cudaMemcpyDeviceToDevice, p.s) != cudaSuccess)
+        st = QCD_ERR_CUDA;
+      if (st != QCD_OK) {
+        p.status = st;
         p.active = false;
       }
     }
@@ -299,17 +345,26 @@ int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool us
           p.active = false;
           continue;
         }
-        if (std::sqrt(rk2) <= sp.tol * p.bn) p.cycle_done = true;
+        // FP32 cycles work on r / |r|: stop at the target or after a drop by inner_tol
+        const double thr = p.w->rprec == P32 ? std::max(sp.tol * p.bn / p.rn, sp.inner_tol) : sp.tol * p.bn;
+        if (std::sqrt(rk2) <= thr) p.cycle_done = true;
       }
     }
     // x += sum gamma_k phi_k; r = b - D x (FP64)
     for (auto& p : probs) {
       if (!p.active || p.kused == 0) continue;
       Workspace& w = *p.w;
-      const double* phi_p[64];
-      for (int j = 0; j < p.kused; ++j) phi_p[j] = (const double*)w.phi[j].data;
       int st = fgcr_backsub(w.d_a1, w.d_a2, w.d_cr, p.kused, sp.nkv, w.d_gam, p.s);
-      if (st == QCD_OK) st = blas_multi_axpy(p.c, phi_p, p.kused, w.d_gam, (double*)p.x.data, p.s);
+      if (st == QCD_OK && w.rprec == P32) {
+        const float* phi_p[64];
+        for (int j = 0; j < p.kused; ++j) phi_p[j] = (const float*)w.phi[j].data;
+        const double* rn2 = w.d_rn + w.nkv + (p.info.restarts == 0 ? 1 : 2);
+        st = blas_refine_update(p.c, phi_p, p.kused, w.d_gam, rn2, (double*)p.x.data, p.s);
+      } else if (st == QCD_OK) {
+        const double* phi_p[64];
+        for (int j = 0; j < p.kused; ++j) phi_p[j] = (const double*)w.phi[j].data;
+        st = blas_multi_axpy<double>(p.c, phi_p, p.kused, w.d_gam, (double*)p.x.data, p.s);
+      }
       if (st == QCD_OK) st = residual64(p.c, w.d_part, p.b, p.x, w.r, w.d_rn + w.nkv + 2, p.s);
       if (st == QCD_OK && cudaMemcpyAsync(w.h_pin + w.nkv + 2, w.d_rn + w.nkv + 2, bytes_of, cudaMemcpyDeviceToHost,
                                           p.s) != cudaSuccess)

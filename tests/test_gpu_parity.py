@@ -179,3 +179,59 @@ def test_solve_16x32(orc, sap_prec):
     assert info[0]["status"] == 0, info
     assert _oracle_residual(orc, dims, U, A, b, x.cpu().numpy()) <= 1.05e-10
     lat.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_resident_field_multi_rhs(orc, prec):
+    """Three right-hand sides in one resident field, one operator launch for
+    all three: each equals the oracle's D applied to it."""
+    from paper_1109_4279_gb300 import binding
+    dims, block = (8, 8, 8, 16), (4, 4, 4, 4)
+    lat, U, A, _ = _setup(dims, block, 0.5, 11, -0.05, 1.5)
+    rng = np.random.default_rng(12)
+    b = synth.gaussian_spinor(dims, rng, nrhs=3)
+    fi = binding.qcd_field_create_n(lat.ctx, prec, 3)
+    fo = binding.qcd_field_create_n(lat.ctx, prec, 3)
+    bt = torch.from_numpy(b).cuda()
+    binding.qcd_field_import(lat.ctx, fi, bt)
+    binding.qcd_apply_D_field(lat.ctx, fi, fo)
+    out = torch.empty_like(bt)
+    binding.qcd_field_export(lat.ctx, fo, out)
+    torch.cuda.synchronize()
+    out = out.cpu().numpy()
+    for k in range(3):
+        assert rel(out[k], orc.apply_D(dims, U, A, AP, b[k])) < TOL_D[prec]
+    binding.qcd_field_free(fi)
+    binding.qcd_field_free(fo)
+    lat.close()
+
+
+def test_solve_outer_f32_split(orc):
+    """The split of Sec. 4: chi_k = D phi_k in FP32 inside the Krylov
+    recursion, the residual recomputed in FP64 at every restart; the FP64
+    true residual still reaches 1e-10."""
+    w = synth.WORKLOADS["16^3x32 fp32"]
+    dims = w["dims"]
+    lat, U, A, b = _setup(dims, w["block"], w["eps"], w["seed"], w["m0"], w["csw"])
+    x, info = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec="f16", outer_prec="f32")
+    assert info[0]["status"] == 0, info
+    assert _oracle_residual(orc, dims, U, A, b, x.cpu().numpy()) <= 1.05e-10
+    lat.close()
+
+
+@pytest.mark.parametrize("precond", ["sap", "none"])
+def test_solve_outer_f32_small(orc, precond):
+    """FP32 recursion with FP64 restarts on 8^4 (2 x 2 x 4 x 4 blocks): the
+    solution's FP64 residual, recomputed by the oracle, reaches 1e-10, and
+    the solution agrees with the all-FP64 recursion's."""
+    dims, block = (8, 8, 8, 8), (4, 4, 2, 2)
+    lat, U, A, b = _setup(dims, block, 0.5, 9, 0.0, 1.5)
+    bt = torch.from_numpy(b).cuda()
+    x32, info = lat.solve(bt, tol=1e-10, precond=precond, sap_prec="f32", outer_prec="f32", max_restarts=400)
+    assert info[0]["status"] == 0, info
+    assert _oracle_residual(orc, dims, U, A, b, x32.cpu().numpy()) <= 1.05e-10
+    x64, _ = lat.solve(bt, tol=1e-12, precond=precond, sap_prec="f32", outer_prec="f64", max_restarts=400)
+    # both residuals <= 1e-10 |b|: the solutions differ by at most
+    # |D^-1| |D| 2e-10 relative, well below 1e-7 for this mass
+    assert rel(x32.cpu().numpy(), x64.cpu().numpy()) < 1e-7
+    lat.close()
