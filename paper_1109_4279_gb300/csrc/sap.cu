@@ -312,25 +312,67 @@ __device__ __forceinline__ void expand_links(const unsigned char* land, unsigned
 // ------------------------------------------------------------------------
 // block operator pieces
 // ------------------------------------------------------------------------
+// Spinor fields in shared memory are stored as 16-byte chunks [24 / R][n]
+// (R = 4 FP32 or 2 FP64 reals per chunk; real 6 a + 2 b (+1) is spin a,
+// colour b), so a site's spinor is 6 (FP32) or 12 (FP64) vector loads.
+template <typename T>
+struct Chunk;
+template <>
+struct Chunk<float> {
+  typedef float4 type;
+  static constexpr int R = 4;
+};
+template <>
+struct Chunk<double> {
+  typedef double2 type;
+  static constexpr int R = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void chunk_get(const typename Chunk<T>::type& c, T* v);
+template <>
+__device__ __forceinline__ void chunk_get<float>(const float4& c, float* v) {
+  v[0] = c.x;
+  v[1] = c.y;
+  v[2] = c.z;
+  v[3] = c.w;
+}
+template <>
+__device__ __forceinline__ void chunk_get<double>(const double2& c, double* v) {
+  v[0] = c.x;
+  v[1] = c.y;
+}
+__device__ __forceinline__ float4 chunk_make(const float* v) { return make_float4(v[0], v[1], v[2], v[3]); }
+__device__ __forceinline__ double2 chunk_make(const double* v) { return make_double2(v[0], v[1]); }
+
+// reals [k0, k0 + N) of site i of a chunked field with stride n
+template <typename T, int N>
+__device__ __forceinline__ void s_load(const T* base, int n, int i, int k0, T* v) {
+  typedef typename Chunk<T>::type C;
+  constexpr int R = Chunk<T>::R;
+  const C* p = (const C*)base + (k0 / R) * n + i;
+#pragma unroll
+  for (int k = 0; k < N / R; ++k) chunk_get<T>(p[k * n], v + R * k);
+}
+template <typename T, int N>
+__device__ __forceinline__ void s_store(T* base, int n, int i, int k0, const T* v) {
+  typedef typename Chunk<T>::type C;
+  constexpr int R = Chunk<T>::R;
+  C* p = (C*)base + (k0 / R) * n + i;
+#pragma unroll
+  for (int k = 0; k < N / R; ++k) p[k * n] = chunk_make(v + R * k);
+}
+
 template <typename T>
 __device__ __forceinline__ Spinor<T> s_spinor(const T* base, int n, int i) {
+  T v[24];
+  s_load<T, 24>(base, n, i, 0, v);
   Spinor<T> s;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) s.c[a][b] = {base[(6 * a + 2 * b) * n + i], base[(6 * a + 2 * b + 1) * n + i]};
+    for (int b = 0; b < 3; ++b) s.c[a][b] = {v[6 * a + 2 * b], v[6 * a + 2 * b + 1]};
   return s;
-}
-
-template <typename T>
-__device__ __forceinline__ void s_spinor_store(T* base, int n, int i, const Spinor<T>& s) {
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      base[(6 * a + 2 * b) * n + i] = s.c[a][b].re;
-      base[(6 * a + 2 * b + 1) * n + i] = s.c[a][b].im;
-    }
 }
 
 // ------------------------------------------------------------------------
@@ -342,28 +384,31 @@ __device__ __forceinline__ void s_spinor_store(T* base, int n, int i, const Spin
 // exchanged with one shuffle per real.
 // ------------------------------------------------------------------------
 
-// owned half (spins 2 hf, 2 hf + 1) of a spinor field stored [24][n] in shared memory
+// owned half (spins 2 hf, 2 hf + 1: reals 12 hf .. 12 hf + 11) of a chunked
+// spinor field in shared memory
 template <typename T>
 __device__ __forceinline__ Half<T> s_half(const T* base, int n, int i, int hf) {
+  T v[12];
+  s_load<T, 12>(base, n, i, 12 * hf, v);
   Half<T> h;
-  const T* p = base + (12 * hf) * n + i;
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) h.c[s][c] = {p[(6 * s + 2 * c) * n], p[(6 * s + 2 * c + 1) * n]};
+    for (int c = 0; c < 3; ++c) h.c[s][c] = {v[6 * s + 2 * c], v[6 * s + 2 * c + 1]};
   return h;
 }
 
 template <typename T>
 __device__ __forceinline__ void s_half_store(T* base, int n, int i, int hf, const Half<T>& h) {
-  T* p = base + (12 * hf) * n + i;
+  T v[12];
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      p[(6 * s + 2 * c) * n] = h.c[s][c].re;
-      p[(6 * s + 2 * c + 1) * n] = h.c[s][c].im;
+      v[6 * s + 2 * c] = h.c[s][c].re;
+      v[6 * s + 2 * c + 1] = h.c[s][c].im;
     }
+  s_store<T, 12>(base, n, i, 12 * hf, v);
 }
 
 template <typename T>
@@ -445,19 +490,18 @@ __device__ __forceinline__ Half<float> clover_half(const HalfExpStage<P>& st, in
 // one direction of the block operator's hops at site r:
 //   U_mu(r)(1 - g) v(r + mu) + U_mu(r - mu)^+ (1 + g) v(r - mu)
 // (Dirichlet: hops leaving the block are absent); v lives on the opposite
-// parity at src[site - off]; pm = forward | backward << 16 indices into src,
-// 0xffff when the neighbour is outside the block.
+// parity at src[site - off] (chunked, stride n); pm = forward | backward << 16
+// indices into src.  A neighbour outside the block is the zero slot n - 1,
+// so the hop adds nothing and the code has no data-dependent branch (its
+// link is then the site's own, any valid link).
 template <int MU, typename T, typename ST>
 __device__ __forceinline__ void hop_dir(const ST& st, int n, int r, const T* src, int pm, int off, Spinor<T>& acc) {
   const int kf = pm & 0xffff, kb = (pm >> 16) & 0xffff;
-  if (kf != 0xffff) {
-    const Half<T> h = project<MU, -1>(s_spinor(src, n, kf));
-    expand_add<MU, -1>(acc, umul(st.link(r, MU), h), T(1));
-  }
-  if (kb != 0xffff) {
-    const Half<T> h = project<MU, +1>(s_spinor(src, n, kb));
-    expand_add<MU, +1>(acc, udmul(st.link(kb + off, MU), h), T(1));
-  }
+  const int lb = kb == n - 1 ? r : kb + off;
+  const Half<T> h0 = project<MU, -1>(s_spinor(src, n, kf));
+  expand_add<MU, -1>(acc, umul(st.link(r, MU), h0), T(1));
+  const Half<T> h1 = project<MU, +1>(s_spinor(src, n, kb));
+  expand_add<MU, +1>(acc, udmul(st.link(lb, MU), h1), T(1));
 }
 
 // partial hops over this thread's directions 2 hf, 2 hf + 1 (hf is uniform
@@ -521,7 +565,8 @@ __device__ __forceinline__ Half<T> block_hops(const ST& st, int n, int r, const 
   return h;
 }
 
-// deterministic CTA-wide sum of 3 values; every thread gets the totals
+// deterministic CTA-wide sum of 3 values; every thread gets the totals.  The
+// caller must pass another barrier before the next call.
 template <typename T>
 __device__ __forceinline__ void cta_sum3(T& a, T& b, T& c, T* red) {
 #pragma unroll
@@ -543,7 +588,7 @@ __device__ __forceinline__ void cta_sum3(T& a, T& b, T& c, T* red) {
     b += red[3 * k + 1];
     c += red[3 * k + 2];
   }
-  __syncthreads();
+  // no closing barrier: red is written again only after later barriers
 }
 
 // psi storage precision of the SAP accumulator
@@ -689,9 +734,10 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   ST st;
   const size_t stage_bytes = ST::bytes(Vb);
   st.base_init(smem_raw, Vb);
+  const int ns = Vbh + 1;  // stride of the chunked fields r and t; slot Vbh is a zero site
   T* s_r = (T*)(smem_raw + stage_bytes);
-  T* s_t = s_r + 24 * Vbh;
-  T* s_x = s_t + 24 * Vbh;  // [2][12][np]
+  T* s_t = s_r + 24 * ns;
+  T* s_x = s_t + 24 * ns;  // pair exchange: 24 reals x np, chunked
   T* s_red = s_x + 24 * np;
   uint64_t* bar = (uint64_t*)(s_red + 3 * 32);
 
@@ -747,17 +793,17 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
       yo[mu] = ycoord(po, mu);
     }
   }
-  int pkE[2], pkO[2];  // even site: indices into t (site - Vbh); odd site: into r (= site)
+  int pkE[2], pkO[2];  // even site: indices into t (site - Vbh); odd site: into r (= site); Vbh = absent
   {
     const int je = ye[0] * g.ystr[0] + ye[1] * g.ystr[1] + ye[2] * g.ystr[2] + ye[3] * g.ystr[3];
     const int jo = yo[0] * g.ystr[0] + yo[1] * g.ystr[1] + yo[2] * g.ystr[2] + yo[3] * g.ystr[3];
     int pke[4], pko[4];
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-      const int ef = ye[mu] + 1 < g.b[mu] ? __ldg(g.j2r + je + g.ystr[mu]) - Vbh : 0xffff;
-      const int eb = ye[mu] > 0 ? __ldg(g.j2r + je - g.ystr[mu]) - Vbh : 0xffff;
-      const int of = yo[mu] + 1 < g.b[mu] ? __ldg(g.j2r + jo + g.ystr[mu]) : 0xffff;
-      const int ob = yo[mu] > 0 ? __ldg(g.j2r + jo - g.ystr[mu]) : 0xffff;
+      const int ef = ye[mu] + 1 < g.b[mu] ? __ldg(g.j2r + je + g.ystr[mu]) - Vbh : Vbh;
+      const int eb = ye[mu] > 0 ? __ldg(g.j2r + je - g.ystr[mu]) - Vbh : Vbh;
+      const int of = yo[mu] + 1 < g.b[mu] ? __ldg(g.j2r + jo + g.ystr[mu]) : Vbh;
+      const int ob = yo[mu] > 0 ? __ldg(g.j2r + jo - g.ystr[mu]) : Vbh;
       pke[mu] = ef | (eb << 16);
       pko[mu] = of | (ob << 16);
     }
@@ -810,21 +856,30 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
     expand_links<P>((const unsigned char*)s_r, (unsigned char*)st.base, Vb);
   }
   __syncthreads();
+  {  // zero sites of r and t (the 16-bit links' landing zone is consumed by now)
+    typedef typename Chunk<T>::type C;
+    constexpr int NCH = 24 / Chunk<T>::R;
+    if (threadIdx.x < 2 * NCH) {
+      const T z[Chunk<T>::R] = {};
+      C* base = (C*)(threadIdx.x < NCH ? s_r : s_t);
+      base[(threadIdx.x % NCH) * ns + Vbh] = chunk_make(z);
+    }
+  }
   if (a.faces_in) {
     rho_e = half_axpy(rho_e, pair_reduce_s(receive_faces<T>(a, st, blk, re, ye, n, hf), hf, i, np, s_x), T(1));
     __syncthreads();
     rho_o = half_axpy(rho_o, pair_reduce_s(receive_faces<T>(a, st, blk, ro, yo, n, hf), hf, i, np, s_x), T(1));
   }
   // etahat = rho_e - D_eo A_oo^-1 rho_o: first t = A_oo^-1 rho_o
-  if (act) s_half_store(s_t, Vbh, i, hf, clover_half(st, ro, hf, rho_o));
+  if (act) s_half_store(s_t, ns, i, hf, clover_half(st, ro, hf, rho_o));
   __syncthreads();
-  Half<T> r = half_axpy(rho_e, block_hops<T>(st, Vbh, re, s_t, pkE, Vbh, hf, i, np, s_x), T(-1));
+  Half<T> r = half_axpy(rho_e, block_hops<T>(st, ns, re, s_t, pkE, Vbh, hf, i, np, s_x), T(-1));
   Half<T> x;
 #pragma unroll
   for (int s = 0; s < 2; ++s)
 #pragma unroll
     for (int c = 0; c < 3; ++c) x.c[s][c] = {T(0), T(0)};
-  if (act) s_half_store(s_r, Vbh, i, hf, r);
+  if (act) s_half_store(s_r, ns, i, hf, r);
   __syncthreads();
 
   // ---- MR on Dhat = A_ee - D_eo A_oo^-1 D_oe, x_e = 0, r = etahat.  Each
@@ -834,10 +889,10 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   for (int step = 0; step < 2 * a.nmr; ++step) {
     const int ph = step & 1;
     const int pk2[2] = {ph ? pkE[0] : pkO[0], ph ? pkE[1] : pkO[1]};
-    const Half<T> hq = block_hops<T>(st, Vbh, ph ? re : ro, ph ? s_t : s_r, pk2, ph ? Vbh : 0, hf, i, np, s_x);
+    const Half<T> hq = block_hops<T>(st, ns, ph ? re : ro, ph ? s_t : s_r, pk2, ph ? Vbh : 0, hf, i, np, s_x);
     const Half<T> cl = clover_half(st, ph ? re : ro, hf, ph ? r : hq);
     if (ph == 0) {
-      if (act) s_half_store(s_t, Vbh, i, hf, cl);
+      if (act) s_half_store(s_t, ns, i, hf, cl);
       __syncthreads();
       continue;
     }
@@ -864,15 +919,15 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
         x.c[s][c] = cmadd(alpha, r.c[s][c], x.c[s][c]);
         r.c[s][c] = r.c[s][c] - cmul(alpha, p.c[s][c]);
       }
-    if (act) s_half_store(s_r, Vbh, i, hf, r);
+    if (act) s_half_store(s_r, ns, i, hf, r);
     __syncthreads();
   }
 
   // ---- chi_o = A_oo^-1 (rho_o - D_oe chi_e)
-  if (act) s_half_store(s_r, Vbh, i, hf, x);
+  if (act) s_half_store(s_r, ns, i, hf, x);
   __syncthreads();
   const Half<T> chi_o =
-      clover_half(st, ro, hf, half_axpy(rho_o, block_hops<T>(st, Vbh, ro, s_r, pkO, 0, hf, i, np, s_x), T(-1)));
+      clover_half(st, ro, hf, half_axpy(rho_o, block_hops<T>(st, ns, ro, s_r, pkO, 0, hf, i, np, s_x), T(-1)));
   __syncthreads();
 
   // ---- outputs: solution, block residual (r on even, 0 on odd), faces
@@ -926,7 +981,7 @@ template <int P, typename T>
 static size_t sap_smem_bytes(const Geom& g) {
   typedef typename StageFor<P>::type ST;
   const int np = pairs_per_half(g.Vbh);
-  return ST::bytes(g.Vb) + sizeof(T) * (2 * 24 * (size_t)g.Vbh + 24 * (size_t)np + 3 * 32) + 16;
+  return ST::bytes(g.Vb) + sizeof(T) * (2 * 24 * (size_t)(g.Vbh + 1) + 24 * (size_t)np + 3 * 32) + 16;
 }
 
 template <int P, typename T>
