@@ -473,8 +473,10 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the comparison and batched sections")
     ap.add_argument("--sap-prec", choices=["f64", "f32", "f16", "bf16"], default="f16",
                     help="storage precision of the SAP block fields")
-    ap.add_argument("--outer-prec", choices=["f64", "f32"], default="f32",
-                    help="FGCR recursion precision (f32: the iterative-refinement scheme, FP64 restarts)")
+    ap.add_argument("--outer-prec", choices=["f64", "f32"], default="f64",
+                    help="FGCR recursion precision: f64 (the benchmarked configuration: Gram-Schmidt, dots, "
+                         "chi = D phi and the update in FP64) or f32 (the paper's iterative-refinement split, "
+                         "FP64 only at restarts)")
     args = ap.parse_args()
     if args.impl == "reference":
         world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -188,8 +188,23 @@ struct HalfStage {
   }
 };
 
-// 16-bit, links expanded once at stage-in: links [4 mu][9][Vb] as 16-bit
-// complex pairs (all three rows), clover as in HalfStage.  The compressed
+// a packed pair of 16-bit reals -> FP32 complex
+template <int P>
+__device__ __forceinline__ cpx<float> to_f2(uint32_t w);
+template <>
+__device__ __forceinline__ cpx<float> to_f2<P16>(uint32_t w) {
+  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+  return {f.x, f.y};
+}
+template <>
+__device__ __forceinline__ cpx<float> to_f2<PB16>(uint32_t w) {
+  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+  return {f.x, f.y};
+}
+
+// 16-bit, links expanded once at stage-in: full matrices as 16-bit complex
+// pairs, entries 0-7 in two 16-byte chunks [4 mu][2][Vb] and entry 8 in
+// [4 mu][Vb] (three loads per link); clover as in HalfStage.  The compressed
 // links arrive by bulk copy in a landing zone and are rebuilt there into full
 // matrices, so no hop pays for the third row.
 template <int P>
@@ -203,14 +218,13 @@ struct HalfExpStage {
   typedef typename Storage<P>::real hr;
   static constexpr size_t bytes(int Vb) { return (size_t)(144 + 144 + 4) * Vb; }
   __device__ __forceinline__ SU3<float> link(int r, int mu) const {
-    const uint32_t* p = (const uint32_t*)base + (mu * 9) * Vb + r;
+    const uint4* q = (const uint4*)base + (2 * mu) * Vb + r;
+    const uint4 a = q[0], b = q[Vb];
+    const uint32_t c = ((const uint32_t*)(base + 128 * Vb))[mu * Vb + r];
+    const uint32_t w[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c};
     SU3<float> u;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const uint32_t v = p[k * Vb];
-      const hr* h = reinterpret_cast<const hr*>(&v);
-      u.m[k / 3][k % 3] = {to_f<P>(h[0]), to_f<P>(h[1])};
-    }
+    for (int k = 0; k < 9; ++k) u.m[k / 3][k % 3] = to_f2<P>(w[k]);
     return u;
   }
   __device__ __forceinline__ const uint4* clover_chunks() const { return (const uint4*)(base + 144 * Vb); }
@@ -277,7 +291,7 @@ __device__ __forceinline__ void stage_issue(const SapArgs& a, int blk, unsigned 
 }
 
 // rebuild the compressed 16-bit links of the landing zone (rows 0-1, layout of
-// the storage format) into full 16-bit matrices [mu][9][Vb]
+// the storage format) into full 16-bit matrices (HalfExpStage layout)
 template <int P>
 __device__ __forceinline__ void expand_links(const unsigned char* land, unsigned char* out, int Vb) {
   typedef typename Storage<P>::real hr;
@@ -296,15 +310,17 @@ __device__ __forceinline__ void expand_links(const unsigned char* land, unsigned
       u.m[1][1] = {to_f<P>(hb[0]), to_f<P>(hb[1])};
       u.m[1][2] = {to_f<P>(hb[2]), to_f<P>(hb[3])};
       reconstruct(u);
-      uint32_t* o = (uint32_t*)out + (mu * 9) * Vb + r;
+      uint32_t w[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        uint32_t v;
-        hr* h = reinterpret_cast<hr*>(&v);
+        hr* h = reinterpret_cast<hr*>(&w[k]);
         h[0] = from_f<P>(u.m[k / 3][k % 3].re);
         h[1] = from_f<P>(u.m[k / 3][k % 3].im);
-        o[k * Vb] = v;
       }
+      uint4* q = (uint4*)out + (2 * mu) * Vb + r;
+      q[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      q[Vb] = make_uint4(w[4], w[5], w[6], w[7]);
+      ((uint32_t*)(out + 128 * Vb))[mu * Vb + r] = w[8];
     }
   }
 }
@@ -455,18 +471,24 @@ __device__ __forceinline__ Half<T> clover_half(const ExpandedStage<T>& st, int r
 template <int P>
 __device__ __forceinline__ Half<float> clover_half_native(const uint4* A, const float* scales, int Vb, int r, int hf,
                                                           const Half<float>& in) {
-  typedef typename Storage<P>::real hr;
-  float h40[40];  // chunks 4 hf .. 4 hf + 4 hold this chiral block's 36 values at offset 4 hf
+  // chunks 4 hf .. 4 hf + 4 hold this chiral block's 36 values (18 packed
+  // pairs) starting at pair 2 hf
+  uint32_t w20[20];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const uint4 v = A[(4 * hf + k) * Vb + r];
-    const hr* h = reinterpret_cast<const hr*>(&v);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) h40[8 * k + e] = to_f<P>(h[e]);
+    w20[4 * k] = v.x;
+    w20[4 * k + 1] = v.y;
+    w20[4 * k + 2] = v.z;
+    w20[4 * k + 3] = v.w;
   }
   float c[36];
 #pragma unroll
-  for (int k = 0; k < 36; ++k) c[k] = hf ? h40[k + 4] : h40[k];
+  for (int k = 0; k < 18; ++k) {
+    const cpx<float> f = to_f2<P>(hf ? w20[k + 2] : w20[k]);
+    c[2 * k] = f.re;
+    c[2 * k + 1] = f.im;
+  }
   Half<float> o = clover_half_apply(c, in);
   const float s = scales[r];
 #pragma unroll
