@@ -19,6 +19,7 @@ iteration count the GPU solve needs.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -45,6 +46,19 @@ METRIC = "SAP+FGCR time to |r|/|b|<1e-10 and D_w GB/s vs HBM peak, 1 GB300"
 # as 12 reals (two rows), 72-real clover; 16-bit adds the per-site scales
 DW_BYTES = {"f64": 1344.0, "f32": 672.0, "f16": 352.0}
 DW_FLOPS = 1824.0  # 1320 hopping + 504 clover per site
+# DRAM bytes (read + write) per solved site of one FP16 SAP launch, averaged over
+# the 8 launches of one preconditioner application (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum, 24^3x48 lattice, 331,776 solved sites per launch); valid
+# for the kernel sources whose hash is stored with it, scaled by solved sites
+SAP_TRAFFIC = {"bytes_per_site": 613.2, "src_sha": "040dbbb58ba27124"}
+
+
+def sap_src_sha():
+    h = hashlib.sha256()
+    for f in ("sap.cu", "qcd.cuh"):
+        with open(os.path.join(ROOT, "paper_1109_4279_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 DTYPE = {(sp, op): "%s recursion (f64 residual and solution at restarts) + %s SAP arithmetic on %s SAP storage"
                    % (op, "f64" if sp == "f64" else "f32", sp)
          for sp in ("f64", "f32", "f16", "bf16") for op in ("f64", "f32")}
@@ -254,6 +268,7 @@ def run_comparisons(args, lat, w, U, b_t, sp_main, main_ms):
     out = {main: {"ms": main_ms, "note": "the benchmarked solve"}}
     variants = [("sap_%s_outer_%s" % (sp_, op_), dict(sap_prec=sp_, outer_prec=op_))
                 for sp_, op_ in (("f16", "f64"), ("f16", "f32"), ("f32", "f32"), ("bf16", "f32"), ("f32", "f64"))]
+    variants.append(("fgmres_dr_16_4_sap_f16_outer_f64", dict(solver="fgmres_dr", ndefl=4, sap_prec="f16")))
     variants.append(("gcr_f64_unpreconditioned", dict(precond="none", max_restarts=400)))
     for name, kw in variants:
         if name == main:
@@ -273,6 +288,30 @@ def run_comparisons(args, lat, w, U, b_t, sp_main, main_ms):
     lat64.close()
     plain = min(out["gcr_f64_unpreconditioned"]["ms"], out["sap_f64_outer_f64_blocks_4x4x4x2"]["ms"])
     out["speedup_vs_plain_fp64"] = plain / main_ms
+    return out
+
+
+def run_near_critical(args):
+    """Sec. 4 Fig. 1 analogue: 16^3 x 32 (eps 0.5, seed 2, c_sw 1.5) at
+    m0 = -0.45, close to the critical mass of this ensemble: FGCR with plain
+    restarts of 8 and 16 vectors against FGMRES-DR with 4 deflated vectors."""
+    import numpy as np
+    import torch
+    from paper_1109_4279_gb300 import binding as B, synth
+    dims = (32, 16, 16, 16)
+    U, rng = synth.gauge_field(dims, 0.5, 2)
+    b = torch.from_numpy(synth.gaussian_spinor(dims, rng)).cuda()
+    lat = B.Lattice(dims, (4, 4, 4, 4), -0.45, 1.5)
+    lat.load_gauge(torch.from_numpy(U).cuda())
+    out = {"workload": "16^3x32, m0 -0.45, SAP f16 (4 cycles, 4 MR), FP64 recursion, tol 1e-10"}
+    for name, kw in (("fgcr_8", dict(nkv=8)), ("fgcr_16", dict(nkv=16)),
+                     ("fgmres_dr_8_4", dict(nkv=8, solver="fgmres_dr", ndefl=4)),
+                     ("fgmres_dr_16_4", dict(nkv=16, solver="fgmres_dr", ndefl=4))):
+        sp = B.solver_params(tol=1e-10, sap_prec="f16", max_restarts=400, **kw)
+        ms, info = _time_solve(lat, b, sp)
+        out[name] = {"ms": ms, "iterations": info["iterations"], "cycles": info["restarts"],
+                     "status": info["status"], "true_residual": info["true_residual"]}
+    lat.close()
     return out
 
 
@@ -388,6 +427,9 @@ def run_ours(args, world, rank, local):
                 "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
+    if (dom == "sap" and args.sap_prec == "f16" and SAP_TRAFFIC["bytes_per_site"]
+            and SAP_TRAFFIC["src_sha"] == sap_src_sha()):
+        roof["traffic"] = SAP_TRAFFIC["bytes_per_site"] * V / 2
     roof["peak_source"] = ("FP32/FP64 peaks derived from unit counts at %.0f MHz; HBM from MEASURED_PEAKS.json"
                            % pk["sm_max_mhz"])
 
@@ -412,6 +454,7 @@ def run_ours(args, world, rank, local):
 
     comparisons = run_comparisons(args, lat, w, U, b_t, sp, ms_per_step) if not args.quick else None
     batched = run_batched(args) if not args.quick else None
+    near_critical = run_near_critical(args) if not args.quick else None
 
     # end to end through the public API with host buffers
     b_h = torch.from_numpy(b.copy()).pin_memory()
@@ -448,6 +491,7 @@ def run_ours(args, world, rank, local):
                        "true_residual": max(i["true_residual"] for i in infos),
                        "l2": "no flush: every FP64 solver vector (192 B/site) and the gauge/clover fields exceed the 129 MB L2"},
             "roofline": roof, "kernels": kernels, "dw": dw, "comparisons": comparisons, "batched": batched,
+            "near_critical": near_critical,
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * fbytes, "d2h_bytes_per_step": fbytes},
             "gpu_launches": launches,
             "clocks": clk.summary(), "cpu_baseline": cpu,

@@ -71,6 +71,10 @@ extern "C" {
 #define QCD_PRECOND_NONE 0  /* plain GCR */
 #define QCD_PRECOND_SAP 1   /* Schwarz alternating procedure with MR block solves */
 
+/* Krylov solver of qcd_solve (qcd_solver_params.solver) */
+#define QCD_SOLVER_FGCR 0       /* flexible GCR with plain restarts (Sec. 4) */
+#define QCD_SOLVER_FGMRES_DR 1  /* flexible GMRES with deflated restarts (Sec. 4) */
+
 typedef struct qcd_ctx qcd_ctx;
 
 /* Lattice, action and Schwarz-block parameters (fixed for the life of a context). */
@@ -98,6 +102,10 @@ typedef struct {
                           inner_tol (or the target is met), then the FP32 correction is added to the FP64
                           solution and r = b - D x is recomputed in FP64 */
     double inner_tol;  /* QCD_PREC_F32 recursion only: residual reduction per restart cycle (default 1e-5) */
+    int solver;        /* QCD_SOLVER_FGCR (default) or QCD_SOLVER_FGMRES_DR: flexible GMRES whose restarts keep
+                          the harmonic Ritz vectors of the ndefl smallest values (Sec. 4, deflated restarts);
+                          FP64 recursion (outer_prec must be QCD_PREC_F64), nkv = cycle length m */
+    int ndefl;         /* QCD_SOLVER_FGMRES_DR: deflated vectors k, 0 <= k < nkv (default 4) */
 } qcd_solver_params;
 
 /* Solver report, always filled (also on failure). */

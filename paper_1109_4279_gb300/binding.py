@@ -21,6 +21,7 @@ STATUS = {
 }
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 PRECOND = {"none": 0, "sap": 1}
+SOLVER = {"fgcr": 0, "fgmres_dr": 1}
 KERNEL = {"dirac": 0, "sap": 1, "blas": 2, "residual": 3}
 
 
@@ -41,7 +42,8 @@ class Params(ctypes.Structure):
 class SolverParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("nkv", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("precond", ctypes.c_int), ("ncy", ctypes.c_int), ("nmr", ctypes.c_int),
-                ("sap_prec", ctypes.c_int), ("outer_prec", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+                ("sap_prec", ctypes.c_int), ("outer_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("solver", ctypes.c_int), ("ndefl", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -131,6 +133,8 @@ def solver_params(**kw) -> SolverParams:
             v = PREC[v]
         if k == "precond" and isinstance(v, str):
             v = PRECOND[v]
+        if k == "solver" and isinstance(v, str):
+            v = SOLVER[v]
         setattr(sp, k, v)
     return sp
 

@@ -107,6 +107,8 @@ void qcd_solver_defaults(qcd_solver_params* sp) {
   sp->sap_prec = QCD_PREC_F32;
   sp->outer_prec = QCD_PREC_F64;
   sp->inner_tol = 1e-5;
+  sp->solver = QCD_SOLVER_FGCR;
+  sp->ndefl = 4;
 }
 
 const char* qcd_status_string(int st) {
@@ -300,7 +302,7 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
     fork_streams(s, probs);
     bool prof = false;
     for (auto& p : probs) prof |= p.c->prof;
-    st = fgcr_batch(probs, sp, n > 1 && !prof);
+    st = sp.solver == QCD_SOLVER_FGMRES_DR ? fgmres_dr_batch(probs, sp) : fgcr_batch(probs, sp, n > 1 && !prof);
     join_streams(s, probs);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);

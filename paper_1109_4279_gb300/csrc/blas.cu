@@ -515,6 +515,27 @@ int blas_norm2(qcd_ctx* c, double* part, const R* v, double* d_out, cudaStream_t
   return reduce_partials(part, (int)grid, 1, 1, d_out, s);
 }
 
+// x /= |x| with |x|^2 taken from the Gram-Schmidt results gs (pass 2 when it
+// ran), and the norm stored in *hnorm (the Arnoldi subdiagonal entry)
+__global__ void __launch_bounds__(kBlasThreads)
+    gs_normalise_kernel(double2* __restrict__ x, const double* __restrict__ gs, int two_pass, double* hnorm,
+                        long long n) {
+  const double nrm2 = (two_pass && second_pass_needed(gs)) ? gs[4] : gs[1];
+  const double nv = sqrt(nrm2);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hnorm = nv;
+  const double inv = nv > 0 ? 1.0 / nv : 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = rscale(x[i], inv);
+}
+
+int blas_gs_normalise(qcd_ctx* c, double* x, const double* d_gs, int two_pass, double* d_hnorm, cudaStream_t s) {
+  const long long n = c->V * 12;
+  ProfScope ps(c, QCD_KERNEL_BLAS, s, 32.0 * n, 2.0 * n);
+  gs_normalise_kernel<<<blas_grid(n), kBlasThreads, 0, s>>>((double2*)x, d_gs, two_pass, d_hnorm, n);
+  QCD_LAUNCHED();
+  return QCD_OK;
+}
+
 int blas_gamma5(qcd_ctx* c, const double* x, double* y, int, cudaStream_t s) {
   const long long n = c->V * 12;
   gamma5_kernel<<<blas_grid(n), kBlasThreads, 0, s>>>((const double2*)x, (double2*)y, c->g.Vb, n);

@@ -17,25 +17,49 @@ struct Arith<P64> {
   typedef double T;
 };
 
+// a neighbour's spinor with its 16-bit scale left out (returned in `scale`,
+// 1 for FP32/FP64), so the scale joins the hop coefficient
+template <int P, typename T>
+__device__ __forceinline__ Spinor<T> load_spinor_unscaled(const FieldPtr& f, int Vb, int blk, int r, T& scale) {
+  if constexpr (P == P16 || P == PB16) {
+    float v[24];
+    scale = load_record_raw<P, 24>(f, Vb, blk, r, v);
+    Spinor<T> s;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) s.c[a][b] = {v[6 * a + 2 * b], v[6 * a + 2 * b + 1]};
+    return s;
+  } else {
+    scale = T(1);
+    return load_spinor<P, T>(f, Vb, blk, r);
+  }
+}
+
+// acc += -1/2 [eta U (1 -/+ g) psi(x + mu) + eta U^+ (1 +/- g) psi(x - mu)]; the
+// factor -1/2, the boundary sign and the neighbour's 16-bit scale are one
+// coefficient per hop (U h is linear in h)
 template <int MU, int P, int DAG, typename T>
 __device__ __forceinline__ void hop_pair(const Geom& g, const void* U, const FieldPtr& in, int blk, int r,
                                          const int y[4], const int n[4], Spinor<T>& acc) {
   constexpr int SF = DAG ? +1 : -1;  // D: (1 - g) psi(x + mu); D^+: (1 + g) psi(x + mu)
   {
     Nbr f = neighbour(g, blk, y, n, MU, +1);
-    Spinor<T> p = load_spinor<P, T>(in, g.Vb, f.blk, f.r);
+    T sc;
+    Spinor<T> p = load_spinor_unscaled<P, T>(in, g.Vb, f.blk, f.r, sc);
     Half<T> h = project<MU, SF>(p);
     SU3<T> u = load_link<P, T>(U, g.Vb, blk, r, MU);
     Half<T> w = umul(u, h);
-    expand_add<MU, SF>(acc, w, f.wrap ? (T)g.bc[MU] : T(1));
+    expand_add<MU, SF>(acc, w, (f.wrap ? T(-0.5) * bc_of<T>(g, MU) : T(-0.5)) * sc);
   }
   {
     Nbr b = neighbour(g, blk, y, n, MU, -1);
-    Spinor<T> p = load_spinor<P, T>(in, g.Vb, b.blk, b.r);
+    T sc;
+    Spinor<T> p = load_spinor_unscaled<P, T>(in, g.Vb, b.blk, b.r, sc);
     Half<T> h = project<MU, -SF>(p);
     SU3<T> u = load_link<P, T>(U, g.Vb, b.blk, b.r, MU);
     Half<T> w = udmul(u, h);
-    expand_add<MU, -SF>(acc, w, b.wrap ? (T)g.bc[MU] : T(1));
+    expand_add<MU, -SF>(acc, w, (b.wrap ? T(-0.5) * bc_of<T>(g, MU) : T(-0.5)) * sc);
   }
 }
 
@@ -54,15 +78,51 @@ __device__ __forceinline__ Spinor<T> dirac_site(const Geom& g, const void* U, co
   hop_pair<1, P, DAG, T>(g, U, in, blk, r, y, n, acc);
   hop_pair<2, P, DAG, T>(g, U, in, blk, r, y, n, acc);
   hop_pair<3, P, DAG, T>(g, U, in, blk, r, y, n, acc);
-  Spinor<T> psi = load_spinor<P, T>(in, g.Vb, blk, r);
-  T c[72];
-  load_record<P, 72, T>(A, g.Vb, blk, r, c);
-  Spinor<T> o = clover_apply(c, psi);
+  T sp;
+  Spinor<T> psi = load_spinor_unscaled<P, T>(in, g.Vb, blk, r, sp);
+  if constexpr (P == P16 || P == PB16) {
+    // one chiral 6x6 block at a time: chunks 4 hb .. 4 hb + 4 hold its 18
+    // packed pairs from pair 2 hb on
+    const uint4* d = (const uint4*)A.data + (long long)blk * 9 * g.Vb + r;
+    const T s = (A.norm ? __ldg(A.norm + (long long)blk * g.Vb + r) : 1.0f) * sp;
 #pragma unroll
-  for (int s = 0; s < 4; ++s)
+    for (int hb = 0; hb < 2; ++hb) {
+      uint32_t w[20];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) o.c[s][a] = o.c[s][a] + T(-0.5) * acc.c[s][a];
-  return o;
+      for (int k = 0; k < 5; ++k) {
+        const uint4 v = __ldg(d + (long long)(4 * hb + k) * g.Vb);
+        w[4 * k] = v.x;
+        w[4 * k + 1] = v.y;
+        w[4 * k + 2] = v.z;
+        w[4 * k + 3] = v.w;
+      }
+      T c[36];
+#pragma unroll
+      for (int k = 0; k < 18; ++k) {
+        const float2 x = to_f2<P>(w[2 * hb + k]);
+        c[2 * k] = x.x;
+        c[2 * k + 1] = x.y;
+      }
+      cpx<T> i6[6], o6[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) i6[i] = psi.c[2 * hb + i / 3][i % 3];
+      clover_block_apply(c, i6, o6);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        cpx<T>& a = acc.c[2 * hb + i / 3][i % 3];
+        a = {fma(s, o6[i].re, a.re), fma(s, o6[i].im, a.im)};
+      }
+    }
+  } else {
+    T c[72];
+    load_record<P, 72, T>(A, g.Vb, blk, r, c);
+    const Spinor<T> o = clover_apply(c, psi);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc.c[a][b] = acc.c[a][b] + o.c[a][b];
+  }
+  return acc;
 }
 
 // one thread per site; with nrhs > 1 the thread applies the operator to every

@@ -82,6 +82,11 @@ struct Workspace {
   double* d_gs = nullptr;  // [nkv][8] Gram-Schmidt norms and pass results
   double* d_part = nullptr;  // reduction partial sums
   double* h_pin = nullptr; // pinned host mirror for scalars read back
+  // FGMRES-DR: Arnoldi basis V (m + 1), preconditioned vectors Z (m), k + 1
+  // spare fields for the deflated restart, pinned host copy of H's columns
+  std::vector<Rec> drV, drZ, drT;
+  double* h_hcol = nullptr;
+  double* d_hnorm = nullptr;
   // one captured CUDA graph per FGCR iteration index, valid for graph_key
   std::vector<cudaGraphExec_t> graphs;
   long long graph_key = -1;
@@ -188,6 +193,9 @@ int blas_refine_update(qcd_ctx* c, const float* const* phi, int k, const double*
                        double* x, cudaStream_t s);
 // out32 = r64 / sqrt(*d_rn2)
 int blas_demote_normalised(qcd_ctx* c, const double* r, const double* d_rn2, float* out, cudaStream_t s);
+// x /= |x| (FP64) with |x|^2 from the Gram-Schmidt results (pass 2 when it
+// ran); *d_hnorm = |x| before the scaling
+int blas_gs_normalise(qcd_ctx* c, double* x, const double* d_gs, int two_pass, double* d_hnorm, cudaStream_t s);
 // norm2
 template <typename R>
 int blas_norm2(qcd_ctx* c, double* part, const R* v, double* d_out, cudaStream_t s);
@@ -220,6 +228,9 @@ struct Problem {
 // every active problem on its own stream (replayed from a CUDA graph when
 // use_graphs), then one host synchronisation checks every residual.
 int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool use_graphs);
+// FGMRES with deflated restarts (Sec. 4), FP64 recursion; problems one after another
+int fgmres_dr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp);
+void dr_release(Workspace& w);
 int solve_one(qcd_ctx* c, const Rec& b, const Rec& x, const qcd_solver_params& sp, qcd_solve_info* info,
               cudaStream_t s);
 void workspace_free(qcd_ctx* c);

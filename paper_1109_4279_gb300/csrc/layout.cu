@@ -20,6 +20,7 @@ int setup_geometry(qcd_ctx* c) {
     g.b[mu] = b;
     g.nb[mu] = L / b;
     g.bc[mu] = c->p.bc[mu];
+    g.bcf[mu] = (float)c->p.bc[mu];
     V *= L;
     Vb *= b;
     nblk *= L / b;

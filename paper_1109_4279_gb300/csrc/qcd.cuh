@@ -193,6 +193,7 @@ struct Geom {
   int nblk;         // number of blocks
   long long V;      // lattice volume
   double bc[4];     // sign of the hop that wraps around direction mu
+  float bcf[4];     // the same signs in FP32 (no FP64 conversion in FP32 kernels)
   const int* r2y;   // r -> packed local coordinates (8 bits each, mu = 0 lowest)
   const int* j2r;   // in-block lexicographic index -> r
 };
@@ -206,6 +207,14 @@ __device__ __forceinline__ void block_coords(const Geom& g, int blk, int n[4]) {
   n[1] = t % g.nb[1];
   n[0] = t / g.nb[1];
 }
+
+// boundary sign of direction mu in the arithmetic type
+template <typename T>
+__device__ __forceinline__ T bc_of(const Geom& g, int mu);
+template <>
+__device__ __forceinline__ double bc_of<double>(const Geom& g, int mu) { return g.bc[mu]; }
+template <>
+__device__ __forceinline__ float bc_of<float>(const Geom& g, int mu) { return g.bcf[mu]; }
 
 struct Nbr {
   int blk, r;
@@ -244,7 +253,11 @@ __device__ __forceinline__ Nbr neighbour(const Geom& g, int blk, const int y[4],
       }
     }
   }
-  o.r = __ldg(g.j2r + j);
+  // even block extents: in-block lexicographic sites 2m and 2m + 1 differ only in
+  // y3, hence in parity, so a site's rank among its parity is j >> 1; the
+  // neighbour has the opposite parity (same rule as the j2r table, no load)
+  const int par = (y[0] + y[1] + y[2] + y[3]) & 1;
+  o.r = (par ^ 1) * g.Vbh + (j >> 1);
   return o;
 }
 
@@ -318,6 +331,18 @@ __device__ __forceinline__ __half from_f<P16>(float v) { return __float2half_rn(
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_f<PB16>(float v) { return __float2bfloat16_rn(v); }
 
+// a packed pair of 16-bit reals -> two FP32 values
+template <int P>
+__device__ __forceinline__ float2 to_f2(uint32_t w);
+template <>
+__device__ __forceinline__ float2 to_f2<P16>(uint32_t w) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&w));
+}
+template <>
+__device__ __forceinline__ float2 to_f2<PB16>(uint32_t w) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+}
+
 // load N reals (N a multiple of the chunk width) of site (blk, r) of a field
 // with NC chunks per site; T is the arithmetic type
 template <int P, int N, typename T>
@@ -355,6 +380,30 @@ __device__ __forceinline__ void load_record(const FieldPtr& f, int Vb, int blk, 
         if (8 * k + e < N) out[8 * k + e] = s * to_f<P>(h[e]);
     }
   }
+}
+
+// N reals of a 16-bit record without its per-site scale applied; returns the
+// scale (1 when the field has none), so callers can fold it into a later
+// multiplication
+template <int P, int N>
+__device__ __forceinline__ float load_record_raw(const FieldPtr& f, int Vb, int blk, int r, float* out) {
+  static_assert(P == P16 || P == PB16, "16-bit storage only");
+  constexpr int NC = (N + 7) / 8;
+  const long long base = (long long)blk * NC * Vb + r;
+  const uint4* d = (const uint4*)f.data;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const uint4 v = __ldg(d + base + (long long)k * Vb);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (8 * k + 2 * e < N) {
+        const float2 x = to_f2<P>(w[e]);
+        out[8 * k + 2 * e] = x.x;
+        out[8 * k + 2 * e + 1] = x.y;
+      }
+  }
+  return f.norm ? __ldg(f.norm + (long long)blk * Vb + r) : 1.0f;
 }
 
 // store N reals; 16-bit storage computes the per-site max-abs scale
@@ -467,15 +516,12 @@ __device__ __forceinline__ SU3<T> load_link(const void* U, int Vb, int blk, int 
     const char* base = (const char*)U + (long long)blk * Vb * 96;
     uint4 a = __ldg((const uint4*)base + (long long)mu * Vb + r);
     uint2 b = __ldg((const uint2*)(base + (long long)64 * Vb) + (long long)mu * Vb + r);
-    const hr* ha = reinterpret_cast<const hr*>(&a);
-    const hr* hb = reinterpret_cast<const hr*>(&b);
-    float f[12];
+    const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
 #pragma unroll
-    for (int e = 0; e < 8; ++e) f[e] = to_f<P>(ha[e]);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) f[8 + e] = to_f<P>(hb[e]);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) u.m[k / 3][k % 3] = {(T)f[2 * k], (T)f[2 * k + 1]};
+    for (int k = 0; k < 6; ++k) {
+      const float2 x = to_f2<P>(w[k]);
+      u.m[k / 3][k % 3] = {(T)x.x, (T)x.y};
+    }
     reconstruct(u);
   }
   return u;

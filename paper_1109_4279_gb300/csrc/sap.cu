@@ -188,20 +188,6 @@ struct HalfStage {
   }
 };
 
-// a packed pair of 16-bit reals -> FP32 complex
-template <int P>
-__device__ __forceinline__ cpx<float> to_f2(uint32_t w);
-template <>
-__device__ __forceinline__ cpx<float> to_f2<P16>(uint32_t w) {
-  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
-  return {f.x, f.y};
-}
-template <>
-__device__ __forceinline__ cpx<float> to_f2<PB16>(uint32_t w) {
-  const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
-  return {f.x, f.y};
-}
-
 // 16-bit, links expanded once at stage-in: full matrices as 16-bit complex
 // pairs, entries 0-7 in two 16-byte chunks [4 mu][2][Vb] and entry 8 in
 // [4 mu][Vb] (three loads per link); clover as in HalfStage.  The compressed
@@ -224,7 +210,10 @@ struct HalfExpStage {
     const uint32_t w[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c};
     SU3<float> u;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) u.m[k / 3][k % 3] = to_f2<P>(w[k]);
+    for (int k = 0; k < 9; ++k) {
+      const float2 x = to_f2<P>(w[k]);
+      u.m[k / 3][k % 3] = {x.x, x.y};
+    }
     return u;
   }
   __device__ __forceinline__ const uint4* clover_chunks() const { return (const uint4*)(base + 144 * Vb); }
@@ -485,9 +474,9 @@ __device__ __forceinline__ Half<float> clover_half_native(const uint4* A, const 
   float c[36];
 #pragma unroll
   for (int k = 0; k < 18; ++k) {
-    const cpx<float> f = to_f2<P>(hf ? w20[k + 2] : w20[k]);
-    c[2 * k] = f.re;
-    c[2 * k + 1] = f.im;
+    const float2 f = to_f2<P>(hf ? w20[k + 2] : w20[k]);
+    c[2 * k] = f.x;
+    c[2 * k + 1] = f.y;
   }
   Half<float> o = clover_half_apply(c, in);
   const float s = scales[r];
@@ -704,7 +693,7 @@ __device__ __forceinline__ void send_faces(const SapArgs& a, const ST& st, int b
     const int ymu = mu == 0 ? y[0] : (mu == 1 ? y[1] : (mu == 2 ? y[2] : y[3]));
     const int nmu = mu == 0 ? n[0] : (mu == 1 ? n[1] : (mu == 2 ? n[2] : n[3]));
     if (ymu == 0) {  // to y = x - mu: 1/2 eta_mu(y) (1 - g) chi, projected
-      const T f = T(0.5) * ((nmu == 0) ? (T)g.bc[mu] : T(1));
+      const T f = T(0.5) * ((nmu == 0) ? bc_of<T>(g, mu) : T(1));
       Half<T> h = project_rt<-1>(chi, d);
 #pragma unroll
       for (int s = 0; s < 2; ++s)
@@ -713,7 +702,7 @@ __device__ __forceinline__ void send_faces(const SapArgs& a, const ST& st, int b
       face_store<T>(a, blk, 2 * mu, face_index(g, y, mu), h);
     }
     if (ymu == g.b[mu] - 1) {  // to y = x + mu: 1/2 eta_mu(x) U_mu(x)^+ (1 + g) chi, projected
-      const T f = T(0.5) * ((nmu == g.nb[mu] - 1) ? (T)g.bc[mu] : T(1));
+      const T f = T(0.5) * ((nmu == g.nb[mu] - 1) ? bc_of<T>(g, mu) : T(1));
       Half<T> w = udmul(st.link(r, mu), project_rt<+1>(chi, d));
 #pragma unroll
       for (int s = 0; s < 2; ++s)

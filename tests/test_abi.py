@@ -49,3 +49,14 @@ def test_binding_names_match_header():
         if n in ("qcd_solver_defaults", "qcd_last_error"):
             continue
         assert hasattr(binding, n), n
+
+
+def test_solver_params_layout_matches_header(lib):
+    """qcd_solver_defaults (host only) fills the binding's structure: every
+    field lands where the C layout puts it."""
+    import ctypes
+    from paper_1109_4279_gb300 import binding
+    sp = binding.SolverParams()
+    lib.qcd_solver_defaults(ctypes.byref(sp))
+    assert (sp.tol, sp.nkv, sp.max_restarts, sp.precond, sp.ncy, sp.nmr) == (1e-10, 16, 100, 1, 4, 4)
+    assert (sp.sap_prec, sp.outer_prec, sp.inner_tol, sp.solver, sp.ndefl) == (1, 0, 1e-5, 0, 4)
