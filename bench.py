@@ -49,8 +49,9 @@ DW_FLOPS = 1824.0  # 1320 hopping + 504 clover per site
 # DRAM bytes (read + write) per solved site of one FP16 SAP launch, averaged over
 # the 8 launches of one preconditioner application (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum, 24^3x48 lattice, 331,776 solved sites per launch); valid
-# for the kernel sources whose hash is stored with it, scaled by solved sites
-SAP_TRAFFIC = {"bytes_per_site": 613.2, "src_sha": "040dbbb58ba27124"}
+# for the kernel sources whose hash is stored with it and that block shape,
+# scaled by solved sites
+SAP_TRAFFIC = {"bytes_per_site": 596.9, "src_sha": "a3bda967a5547982", "block": (8, 4, 4, 4)}
 
 
 def sap_src_sha():
@@ -359,6 +360,21 @@ def run_ours(args, world, rank, local):
     pk = peaks()
     w, U, b = make_inputs(args.workload)
     V = int(np.prod(w["dims"]))
+    w = dict(w)
+    tuning = None
+    if args.block:
+        w["block"] = tuple(int(v) for v in args.block.split("x"))
+    elif not args.no_tune:
+        # Schwarz block shape by the autotuner (timed complete solves, outside
+        # the timed region): 4^4 against 8 x 4^3 (8 along time)
+        cands = [c for c in ((4, 4, 4, 4), (8, 4, 4, 4))
+                 if all(w["dims"][m] % c[m] == 0 and (w["dims"][m] // c[m]) % 2 == 0 for m in range(4))]
+        sp_t = B.solver_params(tol=1e-10, nkv=w["nkv"], ncy=w["ncy"], nmr=w["nmr"], sap_prec=args.sap_prec,
+                               outer_prec=args.outer_prec)
+        best, times = B.qcd_tune_block(w["dims"], w["m0"], w["csw"], torch.from_numpy(U).cuda(),
+                                       torch.from_numpy(b).cuda(), candidates=cands, params=sp_t)
+        w["block"] = tuple(best)
+        tuning = {"x".join(map(str, c)): t for c, t in times.items()}
     lat = B.Lattice(w["dims"], w["block"], w["m0"], w["csw"])
     lat.load_gauge(torch.from_numpy(U).cuda())
     b_t = torch.from_numpy(b).cuda()
@@ -428,7 +444,7 @@ def run_ours(args, world, rank, local):
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
     if (dom == "sap" and args.sap_prec == "f16" and SAP_TRAFFIC["bytes_per_site"]
-            and SAP_TRAFFIC["src_sha"] == sap_src_sha()):
+            and SAP_TRAFFIC["src_sha"] == sap_src_sha() and tuple(w["block"]) == SAP_TRAFFIC["block"]):
         roof["traffic"] = SAP_TRAFFIC["bytes_per_site"] * V / 2
     roof["peak_source"] = ("FP32/FP64 peaks derived from unit counts at %.0f MHz; HBM from MEASURED_PEAKS.json"
                            % pk["sm_max_mhz"])
@@ -489,7 +505,8 @@ def run_ours(args, world, rank, local):
                        "ncy": w["ncy"], "nmr": w["nmr"], "sap_prec": args.sap_prec, "outer_prec": args.outer_prec,
                        "iterations": iters, "restarts": int(statistics.median(i["restarts"] for i in infos)),
                        "true_residual": max(i["true_residual"] for i in infos),
-                       "l2": "no flush: every FP64 solver vector (192 B/site) and the gauge/clover fields exceed the 129 MB L2"},
+                       "l2": "no flush: every FP64 solver vector (192 B/site) and the gauge/clover fields exceed the 129 MB L2",
+                       "block_tuning_ms": tuning},
             "roofline": roof, "kernels": kernels, "dw": dw, "comparisons": comparisons, "batched": batched,
             "near_critical": near_critical,
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * fbytes, "d2h_bytes_per_step": fbytes},
@@ -515,6 +532,8 @@ def main():
                          "(measured on the GPU: 7)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the comparison and batched sections")
+    ap.add_argument("--no-tune", action="store_true", help="use the workload's 4^4 blocks without the block autotuner")
+    ap.add_argument("--block", default=None, help="Schwarz block shape, e.g. 8x4x4x4 (skips the autotuner)")
     ap.add_argument("--sap-prec", choices=["f64", "f32", "f16", "bf16"], default="f16",
                     help="storage precision of the SAP block fields")
     ap.add_argument("--outer-prec", choices=["f64", "f32"], default="f64",
