@@ -261,33 +261,44 @@ def _time_solve(lat, b_t, sp, reps=1):
 
 
 def run_comparisons(args, lat, w, U, b_t, sp_main, main_ms):
-    """Time-to-solution of the same system with other precision splits and
-    the plain FP64 solvers (one timed solve each after a warm-up)."""
+    """Time-to-solution of the same system with other precision splits, the
+    deflated-restart solver and the plain FP64 solvers (one timed solve each
+    after a warm-up).  A variant whose block fields do not fit in shared memory
+    with the benchmarked block shape (FP32 SAP fields of 8x4x4x4 blocks) runs
+    with 4^4 blocks; all-FP64 SAP with 4x4x4x2 blocks; each entry names its
+    block shape."""
     import torch
     from paper_1109_4279_gb300 import binding as B
     main = "sap_%s_outer_%s" % (args.sap_prec, args.outer_prec)
-    out = {main: {"ms": main_ms, "note": "the benchmarked solve"}}
+    blk = "x".join(map(str, w["block"]))
+    out = {main: {"ms": main_ms, "block": blk, "note": "the benchmarked solve"}}
+    lats = {tuple(w["block"]): lat}
+
+    def lattice(block):
+        if block not in lats:
+            lats[block] = B.Lattice(w["dims"], block, w["m0"], w["csw"])
+            lats[block].load_gauge(torch.from_numpy(U).cuda())
+        return lats[block]
+
     variants = [("sap_%s_outer_%s" % (sp_, op_), dict(sap_prec=sp_, outer_prec=op_))
-                for sp_, op_ in (("f16", "f64"), ("f16", "f32"), ("f32", "f32"), ("bf16", "f32"), ("f32", "f64"))]
+                for sp_, op_ in (("f16", "f64"), ("f16", "f32"), ("f32", "f32"), ("bf16", "f32"), ("f32", "f64"),
+                                 ("f64", "f64"))]
     variants.append(("fgmres_dr_16_4_sap_f16_outer_f64", dict(solver="fgmres_dr", ndefl=4, sap_prec="f16")))
     variants.append(("gcr_f64_unpreconditioned", dict(precond="none", max_restarts=400)))
     for name, kw in variants:
         if name == main:
             continue
         sp = B.solver_params(tol=1e-10, nkv=w["nkv"], ncy=w["ncy"], nmr=w["nmr"], **kw)
-        ms, info = _time_solve(lat, b_t, sp)
-        out[name] = {"ms": ms, "iterations": info["iterations"], "status": info["status"],
-                     "true_residual": info["true_residual"]}
-    # all-FP64 SAP: FP64 block fields of a 4^4 block exceed shared memory, so 4x4x4x2 blocks
-    blk64 = (4, 4, 4, 2)
-    lat64 = B.Lattice(w["dims"], blk64, w["m0"], w["csw"])
-    lat64.load_gauge(torch.from_numpy(U).cuda())
-    sp = B.solver_params(tol=1e-10, nkv=w["nkv"], ncy=w["ncy"], nmr=w["nmr"], sap_prec="f64")
-    ms, info = _time_solve(lat64, b_t, sp)
-    out["sap_f64_outer_f64_blocks_4x4x4x2"] = {"ms": ms, "iterations": info["iterations"], "status": info["status"],
-                                               "true_residual": info["true_residual"]}
-    lat64.close()
-    plain = min(out["gcr_f64_unpreconditioned"]["ms"], out["sap_f64_outer_f64_blocks_4x4x4x2"]["ms"])
+        for block in (tuple(w["block"]), (4, 4, 4, 4), (4, 4, 4, 2)):
+            ms, info = _time_solve(lattice(block), b_t, sp)
+            if info["status"] != -11:  # QCD_ERR_UNSUPPORTED: block fields exceed shared memory
+                break
+        out[name] = {"ms": ms, "block": "x".join(map(str, block)), "iterations": info["iterations"],
+                     "status": info["status"], "true_residual": info["true_residual"]}
+    for block, l in lats.items():
+        if l is not lat:
+            l.close()
+    plain = min(out["gcr_f64_unpreconditioned"]["ms"], out["sap_f64_outer_f64"]["ms"])
     out["speedup_vs_plain_fp64"] = plain / main_ms
     return out
 
@@ -312,6 +323,91 @@ def run_near_critical(args):
         ms, info = _time_solve(lat, b, sp)
         out[name] = {"ms": ms, "iterations": info["iterations"], "cycles": info["restarts"],
                      "status": info["status"], "true_residual": info["true_residual"]}
+    lat.close()
+    return out
+
+
+def run_configs(args, pk):
+    """The other named workloads, one measurement each (CUDA events / wall
+    clock around complete calls with synchronisation; setup not timed)."""
+    import numpy as np
+    import torch
+    from paper_1109_4279_gb300 import binding as B, synth
+    out = {}
+    # 4^4, FP64 throughout (SAP on 2^4 blocks with FP64 fields)
+    wl = synth.WORKLOADS["4^4 fp64"]
+    U, rng = synth.gauge_field(wl["dims"], wl["eps"], wl["seed"])
+    b = torch.from_numpy(synth.gaussian_spinor(wl["dims"], rng)).cuda()
+    lat = B.Lattice(wl["dims"], wl["block"], wl["m0"], wl["csw"])
+    lat.load_gauge(torch.from_numpy(U).cuda())
+    ms, info = _time_solve(lat, b, B.solver_params(tol=1e-10, sap_prec="f64"))
+    out["4^4_fp64_solve"] = {"ms": ms, "iterations": info["iterations"], "true_residual": info["true_residual"]}
+    lat.close()
+    # 16^3 x 32: operator apply in FP64 and FP32 (fields of 100 / 50 MB: L2-resident), FP32-SAP solve
+    wl = synth.WORKLOADS["16^3x32 fp32"]
+    V = int(np.prod(wl["dims"]))
+    U, rng = synth.gauge_field(wl["dims"], wl["eps"], wl["seed"])
+    bn = synth.gaussian_spinor(wl["dims"], rng)
+    b = torch.from_numpy(bn).cuda()
+    lat = B.Lattice(wl["dims"], wl["block"], wl["m0"], wl["csw"])
+    lat.load_gauge(torch.from_numpy(U).cuda())
+    for prec in ("f64", "f32"):
+        ms = time_dirac(lat, b, prec, reps=50)
+        out["16^3x32_dw_" + prec] = {"ms": ms, "gbs": DW_BYTES[prec] * V / (ms * 1e-3) / 1e9,
+                                     "gflops": DW_FLOPS * V / (ms * 1e-3) / 1e9, "note": "fields L2-resident"}
+    ms, info = _time_solve(lat, b, B.solver_params(tol=1e-10, sap_prec="f32"))
+    out["16^3x32_sap_f32_solve"] = {"ms": ms, "iterations": info["iterations"], "true_residual": info["true_residual"]}
+    lat.close()
+    # ten uneven lattices in one batched call against one at a time
+    blocks = {(8, 8, 8, 8): (4, 4, 2, 2), (16, 8, 8, 8): (4, 4, 4, 4), (24, 12, 12, 12): (4, 6, 2, 2),
+              (32, 16, 16, 16): (4, 4, 4, 4)}
+    lats, bs, xs = [], [], []
+    for k, dims in enumerate(synth.UNEVEN_LATTICES):
+        U, rng = synth.gauge_field(dims, 0.5, 10 + k)
+        l = B.Lattice(dims, blocks[dims], 0.0, 1.5)
+        l.load_gauge(torch.from_numpy(U).cuda())
+        lats.append(l)
+        bs.append(torch.from_numpy(synth.gaussian_spinor(dims, rng)).cuda())
+        xs.append(torch.zeros_like(bs[-1]))
+    sp = B.solver_params(tol=1e-10, sap_prec="f16")
+    for _ in range(2):  # warm-up (workspaces, graphs), then timed
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, infos = B.qcd_solve_batch([l.ctx for l in lats], bs, xs, sp)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+    t_seq = 0.0
+    for l, bb, x in zip(lats, bs, xs):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.qcd_solve(l.ctx, bb, x, 1, sp)
+        torch.cuda.synchronize()
+        t_seq += time.perf_counter() - t0
+    out["uneven_10_lattices"] = {"batched_s": t_batch, "sequential_s": t_seq,
+                                 "max_true_residual": max(i["true_residual"] for i in infos)}
+    for l in lats:
+        l.close()
+    # 16^3 x 32 gradient: solve, adjoint solve (gamma5 D gamma5) and force
+    wl = synth.WORKLOADS["16^3x32 gradient"]
+    U, rng = synth.gauge_field(wl["dims"], wl["eps"], wl["seed"])
+    phi = torch.from_numpy(synth.gaussian_spinor(wl["dims"], rng)).cuda()
+    lat = B.Lattice(wl["dims"], wl["block"], wl["m0"], wl["csw"])
+    lat.load_gauge(torch.from_numpy(U).cuda())
+    V = int(np.prod(wl["dims"]))
+    dphi = torch.empty_like(phi)
+    dth = torch.empty((V, 4, 8), dtype=torch.float64, device="cuda")
+    sp = B.solver_params(tol=1e-10, sap_prec="f16")
+    for k in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.qcd_gradient(lat.ctx, phi, dphi, dth, None, None, sp)
+        torch.cuda.synchronize()
+        t_grad = time.perf_counter() - t0
+    out["16^3x32_gradient"] = {"s": t_grad, "note": "x = D^-1 phi, y = gamma5 D^-1 gamma5 phi, dL/dphi and the "
+                                                    "su(3) force of every link"}
     lat.close()
     return out
 
@@ -471,6 +567,7 @@ def run_ours(args, world, rank, local):
     comparisons = run_comparisons(args, lat, w, U, b_t, sp, ms_per_step) if not args.quick else None
     batched = run_batched(args) if not args.quick else None
     near_critical = run_near_critical(args) if not args.quick else None
+    configs = run_configs(args, pk) if not args.quick else None
 
     # end to end through the public API with host buffers
     b_h = torch.from_numpy(b.copy()).pin_memory()
@@ -508,7 +605,7 @@ def run_ours(args, world, rank, local):
                        "l2": "no flush: every FP64 solver vector (192 B/site) and the gauge/clover fields exceed the 129 MB L2",
                        "block_tuning_ms": tuning},
             "roofline": roof, "kernels": kernels, "dw": dw, "comparisons": comparisons, "batched": batched,
-            "near_critical": near_critical,
+            "near_critical": near_critical, "configs": configs,
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 2 * fbytes, "d2h_bytes_per_step": fbytes},
             "gpu_launches": launches,
             "clocks": clk.summary(), "cpu_baseline": cpu,
