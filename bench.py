@@ -285,6 +285,7 @@ def run_comparisons(args, lat, w, U, b_t, sp_main, main_ms):
                                  ("f64", "f64"))]
     variants.append(("fgmres_dr_16_4_sap_f16_outer_f64", dict(solver="fgmres_dr", ndefl=4, sap_prec="f16")))
     variants.append(("gcr_f64_unpreconditioned", dict(precond="none", max_restarts=400)))
+    variants.append(("cgne_f64", dict(solver="cg")))
     for name, kw in variants:
         if name == main:
             continue
@@ -293,7 +294,8 @@ def run_comparisons(args, lat, w, U, b_t, sp_main, main_ms):
             ms, info = _time_solve(lattice(block), b_t, sp)
             if info["status"] != -11:  # QCD_ERR_UNSUPPORTED: block fields exceed shared memory
                 break
-        out[name] = {"ms": ms, "block": "x".join(map(str, block)), "iterations": info["iterations"],
+        out[name] = {"ms": ms, "block": "x".join(map(str, block)),
+                     "iterations": info["cg_iterations"] if kw.get("solver") == "cg" else info["iterations"],
                      "status": info["status"], "true_residual": info["true_residual"]}
     for block, l in lats.items():
         if l is not lat:

@@ -74,6 +74,8 @@ extern "C" {
 /* Krylov solver of qcd_solve (qcd_solver_params.solver) */
 #define QCD_SOLVER_FGCR 0       /* flexible GCR with plain restarts (Sec. 4) */
 #define QCD_SOLVER_FGMRES_DR 1  /* flexible GMRES with deflated restarts (Sec. 4) */
+#define QCD_SOLVER_CG 2         /* CG on the normal equations D^+ D x = D^+ b, FP64 (Sec. 4: CG for the
+                                   most difficult cases) */
 
 typedef struct qcd_ctx qcd_ctx;
 
@@ -106,18 +108,22 @@ typedef struct {
                           the harmonic Ritz vectors of the ndefl smallest values (Sec. 4, deflated restarts);
                           FP64 recursion (outer_prec must be QCD_PREC_F64), nkv = cycle length m */
     int ndefl;         /* QCD_SOLVER_FGMRES_DR: deflated vectors k, 0 <= k < nkv (default 4) */
+    int cg_fallback;   /* 1: when FGCR or FGMRES-DR stagnates or exhausts max_restarts, continue from its
+                          iterate with CG on the normal equations (default 0) */
+    int cg_max_iter;   /* iteration limit of CG, as solver or fallback (default 20000) */
 } qcd_solver_params;
 
 /* Solver report, always filled (also on failure). */
 typedef struct {
     int status;            /* same value as the call's return code */
-    int iterations;        /* total FGCR iterations */
+    int iterations;        /* total FGCR iterations (FGMRES-DR: Arnoldi steps) */
     int restarts;          /* restart cycles performed */
     double true_residual;  /* final |b - D x| / |b| recomputed in FP64 */
     double time_ms;        /* wall time of the solve on the stream (CUDA events) */
     double sap_ms;         /* time inside the SAP preconditioner (profiling only, else 0) */
     double dirac_ms;       /* time inside the outer operator applies (profiling only, else 0) */
     double blas_ms;        /* time inside the FP64 vector algebra (profiling only, else 0) */
+    int cg_iterations;     /* CG iterations (QCD_SOLVER_CG, or the fallback after FGCR / FGMRES-DR) */
 } qcd_solve_info;
 
 /* Default solver parameters: tol 1e-10, nkv 16, max_restarts 100, SAP with

@@ -21,7 +21,7 @@ STATUS = {
 }
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 PRECOND = {"none": 0, "sap": 1}
-SOLVER = {"fgcr": 0, "fgmres_dr": 1}
+SOLVER = {"fgcr": 0, "fgmres_dr": 1, "cg": 2}
 KERNEL = {"dirac": 0, "sap": 1, "blas": 2, "residual": 3}
 
 
@@ -43,13 +43,14 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("nkv", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("precond", ctypes.c_int), ("ncy", ctypes.c_int), ("nmr", ctypes.c_int),
                 ("sap_prec", ctypes.c_int), ("outer_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("solver", ctypes.c_int), ("ndefl", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("ndefl", ctypes.c_int), ("cg_fallback", ctypes.c_int),
+                ("cg_max_iter", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("true_residual", ctypes.c_double), ("time_ms", ctypes.c_double), ("sap_ms", ctypes.c_double),
-                ("dirac_ms", ctypes.c_double), ("blas_ms", ctypes.c_double)]
+                ("dirac_ms", ctypes.c_double), ("blas_ms", ctypes.c_double), ("cg_iterations", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -109,6 +109,8 @@ void qcd_solver_defaults(qcd_solver_params* sp) {
   sp->inner_tol = 1e-5;
   sp->solver = QCD_SOLVER_FGCR;
   sp->ndefl = 4;
+  sp->cg_fallback = 0;
+  sp->cg_max_iter = 20000;
 }
 
 const char* qcd_status_string(int st) {
@@ -302,7 +304,24 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
     fork_streams(s, probs);
     bool prof = false;
     for (auto& p : probs) prof |= p.c->prof;
-    st = sp.solver == QCD_SOLVER_FGMRES_DR ? fgmres_dr_batch(probs, sp) : fgcr_batch(probs, sp, n > 1 && !prof);
+    if (sp.solver == QCD_SOLVER_CG)
+      st = cg_batch(probs, sp, false);
+    else if (sp.solver == QCD_SOLVER_FGMRES_DR)
+      st = fgmres_dr_batch(probs, sp);
+    else
+      st = fgcr_batch(probs, sp, n > 1 && !prof);
+    // CG fallback from the Krylov solver's iterate (Sec. 4: CG for the most difficult cases)
+    if (sp.solver != QCD_SOLVER_CG && sp.cg_fallback && st != QCD_OK) {
+      bool any = false;
+      for (auto& p : probs) any |= (p.status == QCD_STAGNATED || p.status == QCD_NOT_CONVERGED);
+      if (any) {
+        int st2 = cg_batch(probs, sp, true);
+        st = QCD_OK;
+        for (auto& p : probs)
+          if (p.status != QCD_OK && st == QCD_OK) st = p.status;
+        (void)st2;
+      }
+    }
     join_streams(s, probs);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);

@@ -536,6 +536,64 @@ int blas_gs_normalise(qcd_ctx* c, double* x, const double* d_gs, int two_pass, d
   return QCD_OK;
 }
 
+// CG on the normal equations: alpha = rr / tt;  x += alpha p;  r -= alpha q;
+// partial |r|^2
+__global__ void __launch_bounds__(kBlasThreads)
+    cg_update_kernel(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ p,
+                     const double2* __restrict__ q, const double* __restrict__ rr, const double* __restrict__ tt,
+                     long long n, double* part) {
+  const double alpha = *tt > 0 ? *rr / *tt : 0.0;
+  double acc[1] = {0};
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double2 xi = x[i], ri = r[i];
+    const double2 pi = __ldg(p + i), qi = __ldg(q + i);
+    xi.x = fma(alpha, pi.x, xi.x);
+    xi.y = fma(alpha, pi.y, xi.y);
+    ri.x = fma(-alpha, qi.x, ri.x);
+    ri.y = fma(-alpha, qi.y, ri.y);
+    x[i] = xi;
+    r[i] = ri;
+    nrm_acc(ri, acc[0]);
+  }
+  cta_reduce_store<1>(acc, part);
+}
+
+// p = r + (rr_new / rr) p
+__global__ void __launch_bounds__(kBlasThreads)
+    cg_direction_kernel(double2* __restrict__ p, const double2* __restrict__ r, const double* __restrict__ rr_new,
+                        const double* __restrict__ rr, long long n) {
+  const double beta = *rr > 0 ? *rr_new / *rr : 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 ri = __ldg(r + i);
+    double2 pi = p[i];
+    pi.x = fma(beta, pi.x, ri.x);
+    pi.y = fma(beta, pi.y, ri.y);
+    p[i] = pi;
+  }
+}
+
+int blas_cg_update(qcd_ctx* c, double* part, double* x, double* r, const double* p, const double* q,
+                   const double* d_rr, const double* d_tt, double* d_rr_new, cudaStream_t s) {
+  const long long n = c->V * 12;
+  const unsigned grid = blas_grid(n);
+  {
+    ProfScope ps(c, QCD_KERNEL_BLAS, s, 96.0 * n, 10.0 * n);
+    cg_update_kernel<<<grid, kBlasThreads, 0, s>>>((double2*)x, (double2*)r, (const double2*)p, (const double2*)q,
+                                                    d_rr, d_tt, n, part);
+    QCD_LAUNCHED();
+  }
+  return reduce_partials(part, (int)grid, 1, 1, d_rr_new, s);
+}
+
+int blas_cg_direction(qcd_ctx* c, double* p, const double* r, const double* d_rr_new, const double* d_rr,
+                      cudaStream_t s) {
+  const long long n = c->V * 12;
+  ProfScope ps(c, QCD_KERNEL_BLAS, s, 48.0 * n, 4.0 * n);
+  cg_direction_kernel<<<blas_grid(n), kBlasThreads, 0, s>>>((double2*)p, (const double2*)r, d_rr_new, d_rr, n);
+  QCD_LAUNCHED();
+  return QCD_OK;
+}
+
 int blas_gamma5(qcd_ctx* c, const double* x, double* y, int, cudaStream_t s) {
   const long long n = c->V * 12;
   gamma5_kernel<<<blas_grid(n), kBlasThreads, 0, s>>>((const double2*)x, (double2*)y, c->g.Vb, n);

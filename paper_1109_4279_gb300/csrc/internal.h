@@ -85,6 +85,10 @@ struct Workspace {
   // FGMRES-DR: Arnoldi basis V (m + 1), preconditioned vectors Z (m), k + 1
   // spare fields for the deflated restart, pinned host copy of H's columns
   std::vector<Rec> drV, drZ, drT;
+  // CG on the normal equations: r, p, t = D p, q = D^+ t; device scalars, pinned mirror
+  std::vector<Rec> cgv;
+  double* d_cg = nullptr;
+  double* h_cg = nullptr;
   double* h_hcol = nullptr;
   double* d_hnorm = nullptr;
   // one captured CUDA graph per FGCR iteration index, valid for graph_key
@@ -196,6 +200,12 @@ int blas_demote_normalised(qcd_ctx* c, const double* r, const double* d_rn2, flo
 // x /= |x| (FP64) with |x|^2 from the Gram-Schmidt results (pass 2 when it
 // ran); *d_hnorm = |x| before the scaling
 int blas_gs_normalise(qcd_ctx* c, double* x, const double* d_gs, int two_pass, double* d_hnorm, cudaStream_t s);
+// CG on the normal equations (FP64): x += a p, r -= a q with a = *d_rr / *d_tt,
+// *d_rr_new = |r|^2; and p = r + (*d_rr_new / *d_rr) p
+int blas_cg_update(qcd_ctx* c, double* part, double* x, double* r, const double* p, const double* q,
+                   const double* d_rr, const double* d_tt, double* d_rr_new, cudaStream_t s);
+int blas_cg_direction(qcd_ctx* c, double* p, const double* r, const double* d_rr_new, const double* d_rr,
+                      cudaStream_t s);
 // norm2
 template <typename R>
 int blas_norm2(qcd_ctx* c, double* part, const R* v, double* d_out, cudaStream_t s);
@@ -231,6 +241,11 @@ int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool us
 // FGMRES with deflated restarts (Sec. 4), FP64 recursion; problems one after another
 int fgmres_dr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp);
 void dr_release(Workspace& w);
+// CG on the normal equations (FP64), problems one after another; with
+// fallback_only, only problems whose status is QCD_STAGNATED or
+// QCD_NOT_CONVERGED run, from their current x
+int cg_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool fallback_only);
+void cg_release(Workspace& w);
 int solve_one(qcd_ctx* c, const Rec& b, const Rec& x, const qcd_solver_params& sp, qcd_solve_info* info,
               cudaStream_t s);
 void workspace_free(qcd_ctx* c);

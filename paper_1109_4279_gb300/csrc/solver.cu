@@ -107,6 +107,7 @@ int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream
 void ws_release(Workspace& w) {
   graphs_clear(w);
   dr_release(w);
+  cg_release(w);
   rec_free(w.sap.rho);
   rec_free(w.sap.psi);
   if (w.sap.faces) cudaFree(w.sap.faces);
