@@ -223,6 +223,50 @@ int qcd_gradient(qcd_ctx* ctx, const double* phi, double* dL_dphi, double* dL_dt
  */
 int qcd_force(qcd_ctx* ctx, const double* x, const double* y, double* F, void* stream);
 
+/* ---- Hybrid Monte Carlo molecular dynamics (Sec. 1: the inversions feed the
+ * HMC fermion force), two degenerate clover flavours, one pseudofermion.
+ * Gauge fields U here are lexicographic device arrays (V, 4, 3, 3) complex128
+ * (qcd_load_gauge's layout, periodic links); momenta pi and forces F are
+ * device (V, 4, 8) float64 with P(x, mu) = sum_a pi_a lambda_a / 2, and every
+ * derivative is taken for U_mu(x) -> exp(i theta_a lambda_a / 2) U_mu(x).
+ * Errors: QCD_ERR_ARG (null pointer, nsteps < 1, eps <= 0), QCD_ERR_NOMEM,
+ * and the status of any solve of the trajectory. */
+typedef struct {
+    int accepted;             /* Metropolis: u_accept < exp(-dH) */
+    double dH;                /* H1 - H0 */
+    double H0, H1;            /* H = kin + S_g + S_f at the start and the end */
+    double kin0, S_g0, S_f0;  /* kin = 1/2 sum pi^2; S_g plaquette action; S_f = |D^-+ phi|^2 */
+    double kin1, S_g1, S_f1;
+    int solves;               /* linear solves of the trajectory */
+    int iterations;           /* Krylov (and CG) iterations summed over the solves */
+    double time_ms;           /* CUDA-event time of the trajectory */
+} qcd_hmc_info;
+
+/* Wilson plaquette action S = beta sum_{x, mu<nu} (1 - Re tr U_munu(x) / 3),
+ * written to *S (host).  U: device, ctx's lattice. */
+int qcd_gauge_action(qcd_ctx* ctx, const double* U, double beta, double* S, void* stream);
+
+/* Its force F_a(x, mu) = dS/dtheta_a = (beta / 6) Im tr(lambda_a U_mu(x) V_mu(x)),
+ * V_mu(x) the sum of the six staples; U, F device. */
+int qcd_gauge_force(qcd_ctx* ctx, const double* U, double beta, double* F, void* stream);
+
+/* U_mu(x) <- exp(i eps P(x, mu)) U_mu(x) for every link, in place (exponential
+ * by a scaled Taylor series, exact to rounding). */
+int qcd_update_links(qcd_ctx* ctx, double* U, const double* pi, double eps, void* stream);
+
+/* One HMC trajectory: pseudofermion phi = D(U)^+ eta (eta: device (V, 4, 3)
+ * complex128, a Gaussian draw); leapfrog of nsteps steps of size eps on
+ * H = 1/2 sum pi^2 + S_g + S_f with S_f = phi^+ (D^+ D)^-1 phi: pi -= eps/2 F,
+ * then nsteps times {U <- exp(i eps P) U; pi -= eps F} with a final half step,
+ * F = dS_g/dtheta - 2 Re(Y^+ dD/dtheta X), Y = D^-+ phi, X = D^-1 Y (solved
+ * with sp).  Metropolis with the caller's uniform u_accept in [0, 1): on
+ * acceptance U holds the new links, on rejection the starting links; pi holds
+ * the final momenta either way.  The context is left loaded with the returned
+ * links (clover rebuilt). */
+int qcd_hmc_trajectory(qcd_ctx* ctx, double* U, double* pi, const double* eta, double beta, double eps,
+                       int nsteps, double u_accept, const qcd_solver_params* sp, qcd_hmc_info* info,
+                       void* stream);
+
 /*
  * Pick, by timing on the device, the fastest CTA size of the operator kernel
  * for each storage precision of this context, and keep the choice in the

@@ -98,6 +98,11 @@ def lib():
             "qcd_profile_reset": (I, [P]),
             "qcd_profile_get": (I, [P, I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(D),
                                     ctypes.POINTER(D), ctypes.POINTER(D)]),
+            "qcd_gauge_action": (I, [P, P, D, ctypes.POINTER(D), P]),
+            "qcd_gauge_force": (I, [P, P, D, P, P]),
+            "qcd_update_links": (I, [P, P, P, D, P]),
+            "qcd_hmc_trajectory": (I, [P, P, P, P, D, D, I, D, ctypes.POINTER(SolverParams),
+                                       ctypes.POINTER(HmcInfo), P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -239,6 +244,39 @@ def qcd_tune_block(dims, m0, csw, U, b, candidates=None, params=None, bc=(-1.0, 
     return tuple(out), result
 
 
+class HmcInfo(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int), ("dH", ctypes.c_double), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
+                ("kin0", ctypes.c_double), ("S_g0", ctypes.c_double), ("S_f0", ctypes.c_double),
+                ("kin1", ctypes.c_double), ("S_g1", ctypes.c_double), ("S_f1", ctypes.c_double),
+                ("solves", ctypes.c_int), ("iterations", ctypes.c_int), ("time_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def qcd_gauge_action(ctx, U, beta):
+    S = ctypes.c_double()
+    check(lib().qcd_gauge_action(ctx, _ptr(U), ctypes.c_double(beta), ctypes.byref(S), _stream()),
+          "qcd_gauge_action")
+    return S.value
+
+
+def qcd_gauge_force(ctx, U, beta, F):
+    return check(lib().qcd_gauge_force(ctx, _ptr(U), ctypes.c_double(beta), _ptr(F), _stream()), "qcd_gauge_force")
+
+
+def qcd_update_links(ctx, U, pi, eps):
+    return check(lib().qcd_update_links(ctx, _ptr(U), _ptr(pi), ctypes.c_double(eps), _stream()), "qcd_update_links")
+
+
+def qcd_hmc_trajectory(ctx, U, pi, eta, beta, eps, nsteps, u_accept, params: SolverParams | None = None):
+    info = HmcInfo()
+    check(lib().qcd_hmc_trajectory(ctx, _ptr(U), _ptr(pi), _ptr(eta), ctypes.c_double(beta), ctypes.c_double(eps),
+                                   int(nsteps), ctypes.c_double(u_accept), ctypes.byref(params) if params else None,
+                                   ctypes.byref(info), _stream()), "qcd_hmc_trajectory")
+    return info.as_dict()
+
+
 def qcd_status_string(st):
     return _status_string(st)
 
@@ -340,6 +378,11 @@ class Lattice:
         nrhs = b.numel() // (self.V * 12)
         st, info = qcd_solve(self.ctx, b.contiguous(), x, nrhs, solver_params(**kw))
         return x, info
+
+    def hmc_trajectory(self, U, pi, eta, beta, eps, nsteps, u_accept=0.0, **kw):
+        """One HMC trajectory; U (V,4,3,3) complex128 and pi (V,4,8) float64 device
+        tensors are updated in place."""
+        return qcd_hmc_trajectory(self.ctx, U, pi, eta, beta, eps, nsteps, u_accept, solver_params(**kw))
 
     def sap(self, eta, ncy=4, nmr=4, prec="f32"):
         import torch
