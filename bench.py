@@ -410,6 +410,18 @@ def run_configs(args, pk):
         t_grad = time.perf_counter() - t0
     out["16^3x32_gradient"] = {"s": t_grad, "note": "x = D^-1 phi, y = gamma5 D^-1 gamma5 phi, dL/dphi and the "
                                                     "su(3) force of every link"}
+    # one HMC trajectory on the same lattice: beta 5.5, 5 leapfrog steps of 0.02,
+    # two clover flavours (2 solves per force, 1 per Hamiltonian)
+    pi = torch.from_numpy(rng.standard_normal((V, 4, 8))).cuda()
+    eta = torch.from_numpy(synth.gaussian_spinor(wl["dims"], rng)).cuda()
+    Ud = torch.from_numpy(U.copy()).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = lat.hmc_trajectory(Ud, pi, eta, 5.5, 0.02, 5, 0.0, tol=1e-10, sap_prec="f16")
+    torch.cuda.synchronize()
+    out["16^3x32_hmc_trajectory"] = {"s": time.perf_counter() - t0, "dH": info["dH"], "solves": info["solves"],
+                                     "iterations": info["iterations"], "accepted": info["accepted"],
+                                     "note": "beta 5.5, 5 leapfrog steps of 0.02, FP16 SAP, tol 1e-10"}
     lat.close()
     return out
 

@@ -99,8 +99,9 @@ def test_trajectory_reversible(traj_case):
 def test_dH_scales_with_step_squared():
     """Leapfrog is second order: at a fixed trajectory length, halving the
     step quarters dH once the step is small enough (on this 8^4 system dH =
-    -20 eps^2 + 5300 eps^4 fits eps = 0.04, 0.02, 0.01 with every solver, so
-    eps = 0.02 against 0.01 is in the asymptotic range)."""
+    -20 eps^2 + 5300 eps^4 fits eps = 0.04, 0.02, 0.01 at trajectory length
+    0.04 with every solver, so eps = 0.02 against 0.01 is in the asymptotic
+    range)."""
     dims, block = (8, 8, 8, 8), (4, 4, 2, 2)
     U, rng = synth.gauge_field(dims, 0.3, 17)
     V = 8 ** 4
@@ -108,7 +109,7 @@ def test_dH_scales_with_step_squared():
     eta = synth.gaussian_spinor(dims, rng)
     lat = _lat(dims, block, 0.1, 1.0, U)
     dH = []
-    for eps, n in ((0.02, 1), (0.01, 2)):
+    for eps, n in ((0.02, 2), (0.01, 4)):
         Ut, pit = torch.from_numpy(U.copy()).cuda(), torch.from_numpy(pi.copy()).cuda()
         info = lat.hmc_trajectory(Ut, pit, torch.from_numpy(eta).cuda(), 5.5, eps, n, 0.0, tol=1e-12, sap_prec="f32")
         dH.append(info["dH"])
