@@ -124,6 +124,61 @@ __device__ __forceinline__ Half<T> udmul(const SU3<T>& u, const Half<T>& h) {
   return w;
 }
 
+// FP32 overloads on packed FP32x2 arithmetic (sm_100 family): the two spin
+// components of h travel in the two lanes, so each multiply-add by a link
+// entry (broadcast to both lanes) serves both components.
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ Half<float> umul(const SU3<float>& u, const Half<float>& h) {
+  float2 hr[3], hi[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    hr[b] = make_float2(h.c[0][b].re, h.c[1][b].re);
+    hi[b] = make_float2(h.c[0][b].im, h.c[1][b].im);
+  }
+  Half<float> w;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float2 wr = __fmul2_rn(bc2(u.m[a][0].re), hr[0]);
+    float2 wi = __fmul2_rn(bc2(u.m[a][0].re), hi[0]);
+    wr = __ffma2_rn(bc2(-u.m[a][0].im), hi[0], wr);
+    wi = __ffma2_rn(bc2(u.m[a][0].im), hr[0], wi);
+#pragma unroll
+    for (int b = 1; b < 3; ++b) {
+      wr = __ffma2_rn(bc2(u.m[a][b].re), hr[b], __ffma2_rn(bc2(-u.m[a][b].im), hi[b], wr));
+      wi = __ffma2_rn(bc2(u.m[a][b].re), hi[b], __ffma2_rn(bc2(u.m[a][b].im), hr[b], wi));
+    }
+    w.c[0][a] = {wr.x, wi.x};
+    w.c[1][a] = {wr.y, wi.y};
+  }
+  return w;
+}
+
+__device__ __forceinline__ Half<float> udmul(const SU3<float>& u, const Half<float>& h) {
+  float2 hr[3], hi[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    hr[b] = make_float2(h.c[0][b].re, h.c[1][b].re);
+    hi[b] = make_float2(h.c[0][b].im, h.c[1][b].im);
+  }
+  Half<float> w;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {  // w_a = sum_b conj(u_ba) h_b
+    float2 wr = __fmul2_rn(bc2(u.m[0][a].re), hr[0]);
+    float2 wi = __fmul2_rn(bc2(u.m[0][a].re), hi[0]);
+    wr = __ffma2_rn(bc2(u.m[0][a].im), hi[0], wr);
+    wi = __ffma2_rn(bc2(-u.m[0][a].im), hr[0], wi);
+#pragma unroll
+    for (int b = 1; b < 3; ++b) {
+      wr = __ffma2_rn(bc2(u.m[b][a].re), hr[b], __ffma2_rn(bc2(u.m[b][a].im), hi[b], wr));
+      wi = __ffma2_rn(bc2(u.m[b][a].re), hi[b], __ffma2_rn(bc2(-u.m[b][a].im), hr[b], wi));
+    }
+    w.c[0][a] = {wr.x, wi.x};
+    w.c[1][a] = {wr.y, wi.y};
+  }
+  return w;
+}
+
 // ------------------------------------------------------------------------
 // Spin projection in the chiral basis.  Every g_mu has the form
 // [[0, B], [B^+, 0]] with B unitary (B = -1, -i s1, -i s2, -i s3 for
