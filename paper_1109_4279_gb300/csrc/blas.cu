@@ -46,27 +46,28 @@ __device__ __forceinline__ void nrm_acc(const double2& b, double& n) { n = fma(b
 __device__ __forceinline__ void nrm_acc(const float4& b, float& n) {
   n = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, n))));
 }
-// b -= (cr + i ci) a
+// b -= (cr + i ci) a, two fused multiply-adds per real (the FP64 pipe is the
+// bound of these kernels on GB300)
 __device__ __forceinline__ void csub(double2& b, double cr, double ci, const double2& a) {
-  b.x -= cr * a.x - ci * a.y;
-  b.y -= cr * a.y + ci * a.x;
+  b.x = fma(-cr, a.x, fma(ci, a.y, b.x));
+  b.y = fma(-cr, a.y, fma(-ci, a.x, b.y));
 }
 __device__ __forceinline__ void csub(float4& b, float cr, float ci, const float4& a) {
-  b.x -= cr * a.x - ci * a.y;
-  b.y -= cr * a.y + ci * a.x;
-  b.z -= cr * a.z - ci * a.w;
-  b.w -= cr * a.w + ci * a.z;
+  b.x = fmaf(-cr, a.x, fmaf(ci, a.y, b.x));
+  b.y = fmaf(-cr, a.y, fmaf(-ci, a.x, b.y));
+  b.z = fmaf(-cr, a.z, fmaf(ci, a.w, b.z));
+  b.w = fmaf(-cr, a.w, fmaf(-ci, a.z, b.w));
 }
 // b += (cr + i ci) a
 __device__ __forceinline__ void cadd(double2& b, double cr, double ci, const double2& a) {
-  b.x += cr * a.x - ci * a.y;
-  b.y += cr * a.y + ci * a.x;
+  b.x = fma(cr, a.x, fma(-ci, a.y, b.x));
+  b.y = fma(cr, a.y, fma(ci, a.x, b.y));
 }
 __device__ __forceinline__ void cadd(float4& b, float cr, float ci, const float4& a) {
-  b.x += cr * a.x - ci * a.y;
-  b.y += cr * a.y + ci * a.x;
-  b.z += cr * a.z - ci * a.w;
-  b.w += cr * a.w + ci * a.z;
+  b.x = fmaf(cr, a.x, fmaf(-ci, a.y, b.x));
+  b.y = fmaf(cr, a.y, fmaf(ci, a.x, b.y));
+  b.z = fmaf(cr, a.z, fmaf(-ci, a.w, b.z));
+  b.w = fmaf(cr, a.w, fmaf(ci, a.z, b.w));
 }
 __device__ __forceinline__ double2 rscale(const double2& a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ float4 rscale(const float4& a, float s) {

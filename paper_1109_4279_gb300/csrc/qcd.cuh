@@ -207,30 +207,39 @@ __device__ __forceinline__ Half<T> project(const Spinor<T>& p) {
   return h;
 }
 
-// acc += coef * [w ; S B^+ w]   (inverse of project<MU, S>)
+// acc += f z and acc += f (i z) for real f: two fused multiply-adds per complex
+template <typename T>
+__device__ __forceinline__ void fadd(cpx<T>& acc, T f, const cpx<T>& z) {
+  acc = {fma(f, z.re, acc.re), fma(f, z.im, acc.im)};
+}
+template <typename T>
+__device__ __forceinline__ void fadd_i(cpx<T>& acc, T f, const cpx<T>& z) {
+  acc = {fma(-f, z.im, acc.re), fma(f, z.re, acc.im)};
+}
+
+// acc += coef * [w ; S B^+ w]   (inverse of project<MU, S>); B^+ w is
+// (-w0, -w1), (i w1, i w0), (w1, -w0), (i w0, -i w1) for mu = 0..3, and the
+// coefficient and sign go into fused multiply-adds
 template <int MU, int S, typename T>
 __device__ __forceinline__ void expand_add(Spinor<T>& acc, const Half<T>& w, T coef) {
+  const T f = S > 0 ? coef : -coef;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    cpx<T> w0 = coef * w.c[0][a], w1 = coef * w.c[1][a];
-    acc.c[0][a] = acc.c[0][a] + w0;
-    acc.c[1][a] = acc.c[1][a] + w1;
-    cpx<T> l0, l1;  // B^+ w
+    const cpx<T> w0 = w.c[0][a], w1 = w.c[1][a];
+    fadd(acc.c[0][a], coef, w0);
+    fadd(acc.c[1][a], coef, w1);
     if (MU == 0) {
-      l0 = -w0; l1 = -w1;
+      fadd(acc.c[2][a], -f, w0);
+      fadd(acc.c[3][a], -f, w1);
     } else if (MU == 1) {
-      l0 = ti(w1); l1 = ti(w0);
+      fadd_i(acc.c[2][a], f, w1);
+      fadd_i(acc.c[3][a], f, w0);
     } else if (MU == 2) {
-      l0 = w1; l1 = -w0;
+      fadd(acc.c[2][a], f, w1);
+      fadd(acc.c[3][a], -f, w0);
     } else {
-      l0 = ti(w0); l1 = mti(w1);
-    }
-    if (S > 0) {
-      acc.c[2][a] = acc.c[2][a] + l0;
-      acc.c[3][a] = acc.c[3][a] + l1;
-    } else {
-      acc.c[2][a] = acc.c[2][a] - l0;
-      acc.c[3][a] = acc.c[3][a] - l1;
+      fadd_i(acc.c[2][a], f, w0);
+      fadd_i(acc.c[3][a], -f, w1);
     }
   }
 }
