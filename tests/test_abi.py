@@ -61,3 +61,37 @@ def test_solver_params_layout_matches_header(lib):
     assert (sp.tol, sp.nkv, sp.max_restarts, sp.precond, sp.ncy, sp.nmr) == (1e-10, 16, 100, 1, 4, 4)
     assert (sp.sap_prec, sp.outer_prec, sp.inner_tol, sp.solver, sp.ndefl) == (1, 0, 1e-5, 0, 4)
     assert (sp.cg_fallback, sp.cg_max_iter) == (0, 20000)
+
+
+def _params(dims, block, bc=(-1.0, 1.0, 1.0, 1.0)):
+    from paper_1109_4279_gb300 import binding
+    p = binding.Params()
+    p.dims[:] = list(dims)
+    p.block[:] = list(block)
+    p.m0, p.csw = 0.0, 1.0
+    p.bc[:] = list(bc)
+    return p
+
+
+@pytest.mark.parametrize("dims, block", [
+    ((12, 4, 4, 4), (4, 2, 2, 2)),   # 3 blocks in direction 0: no chessboard colouring
+    ((8, 6, 4, 4), (4, 3, 2, 2)),    # odd block extent: no even/odd split inside blocks
+    ((8, 8, 4, 4), (4, 3, 2, 2)),    # block extent does not divide L
+    ((32, 32, 16, 8), (16, 16, 8, 4)),  # Vb = 8192 > 4096, the largest block
+    ((8, 8, 8, 0), (2, 2, 2, 2)),    # empty lattice
+])
+def test_create_rejects_bad_geometry_on_the_host(lib, dims, block):
+    """Geometry is validated before any device call, so the checks run here."""
+    import ctypes
+    h = ctypes.c_void_p()
+    st = lib.qcd_create(ctypes.byref(h), ctypes.byref(_params(dims, block)))
+    assert st in (-2, -1) and not h.value  # QCD_ERR_GEOMETRY (QCD_ERR_ARG for a zero extent)
+
+
+def test_create_rejects_bad_arguments_on_the_host(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.qcd_create(ctypes.byref(h), ctypes.byref(_params((8, 8, 8, 8), (4, 4, 2, 2), bc=(0.5, 1, 1, 1)))) == -1
+    assert lib.qcd_create(None, ctypes.byref(_params((8, 8, 8, 8), (4, 4, 2, 2)))) == -1
+    assert lib.qcd_create(ctypes.byref(h), None) == -1
+    assert lib.qcd_solve(None, None, None, 1, None, None, None) == -1
