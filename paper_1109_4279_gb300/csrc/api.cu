@@ -282,11 +282,22 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
     const double* bd = b[k];
     const double* xd = x[k];
     if (!dev) {
-      if (cudaMalloc(&stage[k], 2 * fbytes) != cudaSuccess) {
-        cudaGetLastError();
-        st = QCD_ERR_NOMEM;
-        break;
+      // lexicographic staging of b and x for host buffers, kept by the
+      // problem's workspace across calls
+      Workspace& w = *p.w;
+      if (w.stage_bytes < 2 * fbytes) {
+        if (w.stage) cudaFree(w.stage);
+        w.stage = nullptr;
+        w.stage_bytes = 0;
+        if (cudaMalloc(&w.stage, 2 * fbytes) != cudaSuccess) {
+          cudaGetLastError();
+          w.stage = nullptr;
+          st = QCD_ERR_NOMEM;
+          break;
+        }
+        w.stage_bytes = 2 * fbytes;
       }
+      stage[k] = w.stage;
       cudaError_t e = cudaMemcpyAsync(stage[k], b[k], fbytes, cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(stage[k] + p.c->V * 24, x[k], fbytes, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) st = cuda_fail(e, "solve upload");
@@ -344,7 +355,7 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
   }
   cudaStreamSynchronize(s);
   for (int k = 0; k < n; ++k) {
-    if (stage[k]) cudaFree(stage[k]);
+
     if (info) info[k] = probs[k].info;
   }
   return st;

@@ -89,6 +89,9 @@ struct Workspace {
   std::vector<Rec> cgv;
   double* d_cg = nullptr;
   double* h_cg = nullptr;
+  // device staging of lexicographic b and x when the caller passes host buffers
+  double* stage = nullptr;
+  size_t stage_bytes = 0;
   double* h_hcol = nullptr;
   double* d_hnorm = nullptr;
   // one captured CUDA graph per FGCR iteration index, valid for graph_key

@@ -108,6 +108,9 @@ void ws_release(Workspace& w) {
   graphs_clear(w);
   dr_release(w);
   cg_release(w);
+  if (w.stage) cudaFree(w.stage);
+  w.stage = nullptr;
+  w.stage_bytes = 0;
   rec_free(w.sap.rho);
   rec_free(w.sap.psi);
   if (w.sap.faces) cudaFree(w.sap.faces);
