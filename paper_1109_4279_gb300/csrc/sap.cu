@@ -7,12 +7,12 @@
 // threads per (even site, odd site) pair.  The block's links and clover blocks
 // are staged in shared memory, so the n_mr MR steps never touch HBM (Sec. 4:
 // "all the data necessary for a block solve fit the local store").  With
-// 16-bit block fields the staged copy keeps the storage format (two link rows,
-// scaled clover halves) and is brought in by bulk (TMA) copies of the block's
-// contiguous ranges; the third link row and the scales are applied on use.
-// This halves the shared-memory footprint (two CTAs per SM) and the
-// shared-memory bytes per hop.  FP32 and FP64 block fields are expanded to
-// full matrices at stage-in.
+// 16-bit block fields the block's contiguous ranges arrive by bulk (TMA)
+// copies: the two-row links are rebuilt once per block into full 16-bit
+// matrices, the clover blocks stay in the storage format and their per-site
+// scale is applied on use (112 KB per 4^4 block: two CTAs per SM; 224 KB per
+// 8x4x4x4 block: one).  FP32 and FP64 block fields are expanded to full
+// matrices at stage-in.
 //
 // Residual update on the neighbouring blocks (Sec. 4: "the residue is then
 // updated ... on the internal border of the black blocks") goes through face
@@ -145,52 +145,10 @@ struct ExpandedStage {
   }
 };
 
-// 16-bit: the storage format itself -- links [4 mu][Vb] uint4 + [4 mu][Vb]
-// uint2 (rows 0-1), clover [9][Vb] uint4 (scaled halves) + [Vb] float scales
-template <int P>
-struct HalfStage {
-  const unsigned char* base;
-  int Vb;
-  typedef typename Storage<P>::real hr;
-  static constexpr size_t bytes(int Vb) { return (size_t)(96 + 144 + 4) * Vb; }
-  __device__ __forceinline__ SU3<float> link(int r, int mu) const {
-    const uint4 a = ((const uint4*)base)[mu * Vb + r];
-    const uint2 b = ((const uint2*)(base + 64 * Vb))[mu * Vb + r];
-    const hr* ha = reinterpret_cast<const hr*>(&a);
-    const hr* hb = reinterpret_cast<const hr*>(&b);
-    SU3<float> u;
-    u.m[0][0] = {to_f<P>(ha[0]), to_f<P>(ha[1])};
-    u.m[0][1] = {to_f<P>(ha[2]), to_f<P>(ha[3])};
-    u.m[0][2] = {to_f<P>(ha[4]), to_f<P>(ha[5])};
-    u.m[1][0] = {to_f<P>(ha[6]), to_f<P>(ha[7])};
-    u.m[1][1] = {to_f<P>(hb[0]), to_f<P>(hb[1])};
-    u.m[1][2] = {to_f<P>(hb[2]), to_f<P>(hb[3])};
-    reconstruct(u);
-    return u;
-  }
-  __device__ __forceinline__ Spinor<float> clover(int r, const Spinor<float>& in) const {
-    const uint4* A = (const uint4*)(base + 96 * Vb);
-    float c[72];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const uint4 v = A[k * Vb + r];
-      const hr* h = reinterpret_cast<const hr*>(&v);
-#pragma unroll
-      for (int e = 0; e < 8; ++e) c[8 * k + e] = to_f<P>(h[e]);
-    }
-    Spinor<float> o = clover_apply(c, in);
-    const float s = ((const float*)(base + 240 * Vb))[r];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) o.c[a][b] = s * o.c[a][b];
-    return o;
-  }
-};
-
 // 16-bit, links expanded once at stage-in: full matrices as 16-bit complex
 // pairs, entries 0-7 in two 16-byte chunks [4 mu][2][Vb] and entry 8 in
-// [4 mu][Vb] (three loads per link); clover as in HalfStage.  The compressed
+// [4 mu][Vb] (three loads per link); the clover blocks in the storage format,
+// [9][Vb] uint4 (scaled halves) + [Vb] float scales, applied on use.  The compressed
 // links arrive by bulk copy in a landing zone and are rebuilt there into full
 // matrices, so no hop pays for the third row.
 template <int P>
@@ -485,12 +443,6 @@ __device__ __forceinline__ Half<float> clover_half_native(const uint4* A, const 
 #pragma unroll
     for (int b = 0; b < 3; ++b) o.c[a][b] = s * o.c[a][b];
   return o;
-}
-
-template <int P>
-__device__ __forceinline__ Half<float> clover_half(const HalfStage<P>& st, int r, int hf, const Half<float>& in) {
-  return clover_half_native<P>((const uint4*)(st.base + 96 * st.Vb), (const float*)(st.base + 240 * st.Vb), st.Vb, r,
-                               hf, in);
 }
 
 template <int P>
