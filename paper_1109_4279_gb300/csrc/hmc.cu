@@ -343,6 +343,26 @@ struct DevBuf {
   }
 };
 
+// CUDA-event pair timing a region on one stream, released on every exit path
+struct EventTimer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  EventTimer() {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
+  ~EventTimer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+  float elapsed_ms(cudaStream_t s) {
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  }
+};
+
 struct Traj {
   qcd_ctx* c;
   cudaStream_t s;
@@ -406,10 +426,8 @@ extern "C" int qcd_hmc_trajectory(qcd_ctx* c, double* U, double* pi, const doubl
   qcd_solver_params sp;
   if (sp_in) sp = *sp_in; else qcd_solver_defaults(&sp);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
+  EventTimer timer;
+  cudaEventRecord(timer.e0, s);
   Traj t{c, s, &sp, info};
   t.V = c->V;
   const long long V = c->V;
@@ -442,12 +460,6 @@ extern "C" int qcd_hmc_trajectory(qcd_ctx* c, double* U, double* pi, const doubl
     QCD_CUDA(cudaMemcpyAsync(U, U0.p, sizeof(double) * 72 * V, cudaMemcpyDeviceToDevice, s));
     QCD_TRY(t.load(U));
   }
-  cudaEventRecord(e1, s);
-  cudaEventSynchronize(e1);
-  float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  info->time_ms = ms;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  info->time_ms = timer.elapsed_ms(s);
   return QCD_OK;
 }
