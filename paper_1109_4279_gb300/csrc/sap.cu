@@ -681,13 +681,15 @@ struct StageFor<P64> {
 // site pairs per half-CTA: Vbh rounded up to whole warps
 __host__ __device__ __forceinline__ int pairs_per_half(int Vbh) { return (Vbh + 31) / 32 * 32; }
 
-template <int P, typename T>
+// VB: the block volume as a compile-time constant (shared-memory and link
+// offsets become immediates, which frees registers), or 0 for any volume
+template <int P, typename T, int VB>
 __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   typedef typename StageFor<P>::type ST;
   constexpr bool kHalf = (P == P16 || P == PB16);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Geom& g = a.g;
-  const int Vb = g.Vb, Vbh = g.Vbh;
+  const int Vb = VB ? VB : g.Vb, Vbh = VB ? VB / 2 : g.Vbh;
   const int np = pairs_per_half(Vbh);
 
   // shared memory: staged block fields, then the FP vectors r (even sites),
@@ -947,12 +949,42 @@ static size_t sap_smem_bytes(const Geom& g) {
   return ST::bytes(g.Vb) + sizeof(T) * (2 * 24 * (size_t)(g.Vbh + 1) + 24 * (size_t)np + 3 * 32) + 16;
 }
 
+// block volumes with their own instantiation (4^4 and 8 x 4^3 blocks)
+static int sap_vb_key(int Vb) { return Vb == 256 || Vb == 512 ? Vb : 0; }
+
+template <int P, typename T, int VB>
+static int set_smem_attr_vb(size_t smem) {
+  QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P, T, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return QCD_OK;
+}
+
 template <int P, typename T>
 static int set_smem_attr(const Geom& g, int maxsm) {
   const size_t smem = sap_smem_bytes<P, T>(g);
   if (smem > (size_t)maxsm) return QCD_ERR_UNSUPPORTED;
-  QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  return QCD_OK;
+  if constexpr (P == P16) {
+    if (sap_vb_key(g.Vb) == 256) return set_smem_attr_vb<P, T, 256>(smem);
+    if (sap_vb_key(g.Vb) == 512) return set_smem_attr_vb<P, T, 512>(smem);
+  }
+  return set_smem_attr_vb<P, T, 0>(smem);
+}
+
+// launch one colour half-sweep; FP16 block fields of 4^4 and 8 x 4^3 blocks
+// run the instantiation for their volume
+template <int P, typename T>
+static void sap_launch(const Geom& g, unsigned grid, int threads, cudaStream_t s, const SapArgs& a) {
+  const size_t smem = sap_smem_bytes<P, T>(g);
+  if constexpr (P == P16) {
+    if (sap_vb_key(g.Vb) == 256) {
+      sap_sweep_kernel<P, T, 256><<<grid, threads, smem, s>>>(a);
+      return;
+    }
+    if (sap_vb_key(g.Vb) == 512) {
+      sap_sweep_kernel<P, T, 512><<<grid, threads, smem, s>>>(a);
+      return;
+    }
+  }
+  sap_sweep_kernel<P, T, 0><<<grid, threads, smem, s>>>(a);
 }
 
 // allocate the SAP work fields and set the kernel's shared-memory limit for
@@ -1042,10 +1074,10 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
       a.psi_mode = last ? (cy == 0 ? 2 : 3) : (cy == 0 ? 0 : 1);
       ProfScope ps(c, QCD_KERNEL_SAP, s, bytes, flops);
       switch (prec) {
-        case P64: sap_sweep_kernel<P64, double><<<grid, threads, sap_smem_bytes<P64, double>(g), s>>>(a); break;
-        case P32: sap_sweep_kernel<P32, float><<<grid, threads, sap_smem_bytes<P32, float>(g), s>>>(a); break;
-        case P16: sap_sweep_kernel<P16, float><<<grid, threads, sap_smem_bytes<P16, float>(g), s>>>(a); break;
-        case PB16: sap_sweep_kernel<PB16, float><<<grid, threads, sap_smem_bytes<PB16, float>(g), s>>>(a); break;
+        case P64: sap_launch<P64, double>(g, grid, threads, s, a); break;
+        case P32: sap_launch<P32, float>(g, grid, threads, s, a); break;
+        case P16: sap_launch<P16, float>(g, grid, threads, s, a); break;
+        case PB16: sap_launch<PB16, float>(g, grid, threads, s, a); break;
         default: return QCD_ERR_ARG;
       }
       QCD_LAUNCHED();
