@@ -125,13 +125,41 @@ __device__ __forceinline__ Spinor<T> dirac_site(const Geom& g, const void* U, co
   return acc;
 }
 
+// Schwarz block shapes with their own instantiation: BS = 1 for 4^4 and 2 for
+// 8 x 4^3 (time extent 8); the in-block extents, strides and volume are then
+// compile-time constants, which shortens the neighbour and address arithmetic
+static int block_shape_id(const Geom& g) {
+  if (g.b[1] == 4 && g.b[2] == 4 && g.b[3] == 4) {
+    if (g.b[0] == 4) return 1;
+    if (g.b[0] == 8) return 2;
+  }
+  return 0;
+}
+
+template <int BS>
+__device__ __forceinline__ void fix_block_shape(Geom& g) {
+  if constexpr (BS != 0) {
+    constexpr int b0 = BS == 1 ? 4 : 8;
+    g.b[0] = b0;
+    g.b[1] = g.b[2] = g.b[3] = 4;
+    g.ystr[0] = 64;
+    g.ystr[1] = 16;
+    g.ystr[2] = 4;
+    g.ystr[3] = 1;
+    g.Vb = 64 * b0;
+    g.Vbh = 32 * b0;
+  }
+}
+
 // one thread per site; with nrhs > 1 the thread applies the operator to every
 // right-hand side in turn (fields nrhs apart by `stride` sites), so the
 // site's links and clover block come from HBM once and from L1 afterwards
-template <int P, int DAG>
-__global__ void __launch_bounds__(512) dirac_kernel(Geom g, const void* __restrict__ U, FieldPtr A, FieldPtr in,
+template <int P, int DAG, int BS>
+__global__ void __launch_bounds__(512) dirac_kernel(Geom g0, const void* __restrict__ U, FieldPtr A, FieldPtr in,
                                                     FieldPtr out, int nrhs) {
   typedef typename Arith<P>::T T;
+  Geom g = g0;
+  fix_block_shape<BS>(g);
   long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
@@ -204,16 +232,26 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
   const double spin = prec == P64 ? 384 : (prec == P32 ? 192 : 104);
   const double bytes = ((bytes_per_site(prec) - spin) + spin * nrhs) * (double)c->V;
   ProfScope ps(c, QCD_KERNEL_DIRAC, s, bytes, 1824.0 * (double)c->V * nrhs);
-#define LAUNCH(PP)                                                                                 \
-  if (dagger)                                                                                      \
-    dirac_kernel<PP, 1><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);           \
-  else                                                                                             \
-    dirac_kernel<PP, 0><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);
+#define LAUNCH(PP, BS)                                                                                 \
+  if (dagger)                                                                                          \
+    dirac_kernel<PP, 1, BS><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);           \
+  else                                                                                                 \
+    dirac_kernel<PP, 0, BS><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);
+  // 16-bit storage is issue-bound, so it gets the fixed-shape instantiations
+  const int bs = block_shape_id(c->g);
   switch (prec) {
-    case P64: LAUNCH(P64); break;
-    case P32: LAUNCH(P32); break;
-    case P16: LAUNCH(P16); break;
-    case PB16: LAUNCH(PB16); break;
+    case P64: LAUNCH(P64, 0); break;
+    case P32: LAUNCH(P32, 0); break;
+    case P16:
+      if (bs == 1) {
+        LAUNCH(P16, 1);
+      } else if (bs == 2) {
+        LAUNCH(P16, 2);
+      } else {
+        LAUNCH(P16, 0);
+      }
+      break;
+    case PB16: LAUNCH(PB16, 0); break;
     default: return QCD_ERR_ARG;
   }
 #undef LAUNCH

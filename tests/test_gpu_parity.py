@@ -36,6 +36,7 @@ CASES = [
     ((8, 4, 4, 8), (4, 2, 2, 4), 0.5, 7, -0.05, 1.5, AP),         # non-cubic blocks
     ((4, 8, 12, 4), (2, 4, 6, 2), 0.5, 8, 0.0, 1.2, (1, -1, 1, -1)),  # block extent 6, mixed signs
     ((32, 16, 16, 16), (4, 4, 4, 4), 0.5, 2, 0.0, 1.5, AP),       # the 16^3 x 32 workload
+    ((16, 8, 8, 8), (8, 4, 4, 4), 0.5, 12, -0.05, 1.5, AP),       # the benchmarked block shape
 ]
 
 
