@@ -153,9 +153,12 @@ __device__ __forceinline__ void fix_block_shape(Geom& g) {
 
 // one thread per site; with nrhs > 1 the thread applies the operator to every
 // right-hand side in turn (fields nrhs apart by `stride` sites), so the
-// site's links and clover block come from HBM once and from L1 afterwards
+// site's links and clover block come from HBM once and from L1 afterwards.
+// The FP32 instantiation is told it runs one 512-thread CTA per SM (the full
+// 128 registers, used to issue more gathers ahead); the others keep the
+// compiler's default
 template <int P, int DAG, int BS>
-__global__ void __launch_bounds__(512) dirac_kernel(Geom g0, const void* __restrict__ U, FieldPtr A, FieldPtr in,
+__global__ void __launch_bounds__(512, P == P32 ? 1 : 0) dirac_kernel(Geom g0, const void* __restrict__ U, FieldPtr A, FieldPtr in,
                                                     FieldPtr out, int nrhs) {
   typedef typename Arith<P>::T T;
   Geom g = g0;

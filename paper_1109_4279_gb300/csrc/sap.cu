@@ -343,8 +343,10 @@ __device__ __forceinline__ Spinor<T> s_spinor(const T* base, int n, int i) {
 // of every site operation.  Thread half hf computes the hops in directions
 // mu = 2 hf and 2 hf + 1 (so no link is loaded twice) and owns spin
 // components 2 hf and 2 hf + 1 of every vector; the clover term, being block
-// diagonal in chirality, acts on the owned half alone.  Partial hop sums are
-// exchanged with one shuffle per real.
+// diagonal in chirality, acts on the owned half alone.  The two threads of a
+// pair sit in different warps (hf is warp-uniform, so the two direction sets
+// never diverge inside a warp) and exchange their partial hop sums through
+// shared memory.
 // ------------------------------------------------------------------------
 
 // owned half (spins 2 hf, 2 hf + 1: reals 12 hf .. 12 hf + 11) of a chunked
@@ -488,12 +490,20 @@ __device__ __forceinline__ Spinor<T> hops_pair(const ST& st, int n, int r, const
 // pairs per half, a multiple of 32).  Both calls below contain a barrier and
 // must be reached by every thread of the CTA.
 
+// barrier of the two warps that hold pairs 32 w .. 32 w + 31 (warp w of each
+// half): named barrier 1 + w (np / 32 <= 8 of them; barrier 0 is the CTA-wide one)
+__device__ __forceinline__ void pair_warps_sync(int i) {
+  asm volatile("bar.sync %0, 64;" ::"r"(1 + (i >> 5)) : "memory");
+}
+
 // own half of the pair's summed partial spinors (thread (hf, i) stores the
-// part its partner owns in slot hf and reads its partner's slot 1 - hf)
+// part its partner owns in slot hf and reads its partner's slot 1 - hf).  Only
+// the pair's two warps meet here; every caller passes a CTA-wide barrier
+// before its next call, so no slot is overwritten before the partner read it.
 template <typename T>
 __device__ __forceinline__ Half<T> pair_reduce_s(const Spinor<T>& acc, int hf, int i, int np, T* xb) {
   s_half_store(xb, np, i, hf, half_of(acc, 1 - hf));
-  __syncthreads();
+  pair_warps_sync(i);
   return half_axpy(half_of(acc, hf), s_half(xb, np, i, 1 - hf), T(1));
 }
 
