@@ -359,10 +359,25 @@ int qcd_apply_D_noalloc(qcd_ctx* ctx, const double* in, double* out, int dagger,
 int qcd_sap_apply(qcd_ctx* ctx, const double* eta, double* psi, int ncy, int nmr, int sap_prec, void* stream);
 
 /*
+ * Precision codecs (Sec. 4: single-precision preconditioner inside a double
+ * precision solver).  The kernels that move fields between the FP64 recursion
+ * and the FP32 preconditioner (the first and last Schwarz sweeps, the
+ * refinement updates) convert with integer operations instead of GB300's
+ * FP64 conversion unit; this entry point exposes those conversions so that
+ * they can be checked against the hardware ones:
+ *   out32[i] = in64[i] rounded to FP32 (nearest, ties to even),
+ *   out64[i] = in32[i] widened to FP64 (exact),  i < n.
+ * All four are device pointers of n elements (n >= 0); the call is
+ * asynchronous on `stream`.  Returns QCD_ERR_ARG for n < 0 or a null pointer.
+ */
+int qcd_convert_check(const double* in64, const float* in32, float* out32, double* out64, long long n, void* stream);
+
+/*
  * Kernel timing: when enabled, each launch of the instrumented kernels is
  * bracketed by CUDA events on its stream.  qcd_profile_get returns, for a
  * kernel id (QCD_KERNEL_*), the launch count and summed device time (ms), and
- * the algorithmic bytes and flops per launch of the last launch.
+ * the algorithmic bytes and flops per launch averaged over those launches (a
+ * conditional second Gram-Schmidt pass counts as no work).
  */
 #define QCD_KERNEL_DIRAC 0      /* full-lattice operator apply (any precision) */
 #define QCD_KERNEL_SAP 1        /* one SAP colour sweep */

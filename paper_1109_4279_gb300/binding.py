@@ -93,6 +93,7 @@ def lib():
             "qcd_apply_D_field": (I, [P, P, P, I, P]),
             "qcd_apply_D_noalloc": (I, [P, P, P, I, P]),
             "qcd_sap_apply": (I, [P, P, P, I, I, I, P]),
+            "qcd_convert_check": (I, [P, P, P, P, ctypes.c_longlong, P]),
             "qcd_profile_enable": (I, [P, I]),
             "qcd_launch_count": (ctypes.c_longlong, []),
             "qcd_profile_reset": (I, [P]),
@@ -317,6 +318,15 @@ def qcd_apply_D_noalloc(ctx, inp, out, dagger=False):
 def qcd_sap_apply(ctx, eta, psi, ncy, nmr, prec="f32"):
     return check(lib().qcd_sap_apply(ctx, _ptr(eta), _ptr(psi), int(ncy), int(nmr), PREC[prec], _stream()),
                  "qcd_sap_apply")
+
+
+def qcd_convert_check(in64, in32, out32, out64):
+    """out32 = FP32 of in64 (nearest even), out64 = FP64 of in32, through the
+    library's integer-pipe conversions; contiguous CUDA tensors of one length."""
+    n = in64.numel()
+    assert in32.numel() == n and out32.numel() == n and out64.numel() == n
+    return check(lib().qcd_convert_check(_ptr(in64), _ptr(in32), _ptr(out32), _ptr(out64), n, _stream()),
+                 "qcd_convert_check")
 
 
 def qcd_profile_enable(ctx, on=True):

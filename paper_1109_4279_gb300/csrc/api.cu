@@ -58,8 +58,8 @@ ProfScope::ProfScope(qcd_ctx* ctx, int kernel, cudaStream_t st, double bytes, do
   }
   cudaEventRecord(e0, s);
   c->timers[k].pending.emplace_back(e0, e1);
-  c->timers[k].bytes = bytes;
-  c->timers[k].flops = flops;
+  c->timers[k].bytes += bytes;
+  c->timers[k].flops += flops;
 }
 
 ProfScope::~ProfScope() {
@@ -544,6 +544,12 @@ int qcd_sap_apply(qcd_ctx* c, const double* eta, double* psi, int ncy, int nmr, 
   return QCD_OK;
 }
 
+int qcd_convert_check(const double* in64, const float* in32, float* out32, double* out64, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!in64 || !in32 || !out32 || !out64))) return QCD_ERR_ARG;
+  QCD_TRY(convert_check(in64, in32, out32, out64, n, (cudaStream_t)stream));
+  return QCD_OK;
+}
+
 int qcd_profile_enable(qcd_ctx* c, int on) {
   if (!c) return QCD_ERR_ARG;
   c->prof = on != 0;
@@ -556,6 +562,7 @@ int qcd_profile_reset(qcd_ctx* c) {
   for (auto& t : c->timers) {
     t.launches = 0;
     t.total_ms = 0;
+    t.bytes = t.flops = 0;
   }
   return QCD_OK;
 }
@@ -566,8 +573,8 @@ int qcd_profile_get(qcd_ctx* c, int kernel, long long* launches, double* total_m
   const Timer& t = c->timers[kernel];
   if (launches) *launches = t.launches;
   if (total_ms) *total_ms = t.total_ms;
-  if (bytes) *bytes = t.bytes;
-  if (flops) *flops = t.flops;
+  if (bytes) *bytes = t.launches ? t.bytes / (double)t.launches : 0.0;  // averages over the launches
+  if (flops) *flops = t.launches ? t.flops / (double)t.launches : 0.0;
   return QCD_OK;
 }
 

@@ -272,10 +272,10 @@ __global__ void __launch_bounds__(kBlasThreads)
     const long long c = rem / Vb, r = rem - c * Vb;
     const long long e0 = (blk * 12 + 2 * c) * Vb + r;
     double2 x0 = x[e0], x1 = x[e0 + Vb];
-    x0.x = fma(scale, (double)d.x, x0.x);
-    x0.y = fma(scale, (double)d.y, x0.y);
-    x1.x = fma(scale, (double)d.z, x1.x);
-    x1.y = fma(scale, (double)d.w, x1.y);
+    x0.x = fma(scale, f32_to_f64(d.x), x0.x);  // widening on the integer pipes
+    x0.y = fma(scale, f32_to_f64(d.y), x0.y);
+    x1.x = fma(scale, f32_to_f64(d.z), x1.x);
+    x1.y = fma(scale, f32_to_f64(d.w), x1.y);
     x[e0] = x0;
     x[e0 + Vb] = x1;
   }
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kBlasThreads)
     const long long c = rem / Vb, rr = rem - c * Vb;
     const long long e0 = (blk * 12 + 2 * c) * Vb + rr;
     const double2 a = __ldg(r + e0), b = __ldg(r + e0 + Vb);
-    out[i] = make_float4((float)(a.x * inv), (float)(a.y * inv), (float)(b.x * inv), (float)(b.y * inv));
+    out[i] = make_float4(f64_to_f32(a.x * inv), f64_to_f32(a.y * inv), f64_to_f32(b.x * inv), f64_to_f32(b.y * inv));
   }
 }
 
@@ -361,7 +361,10 @@ int blas_multidot(qcd_ctx* c, double* part, const R* const* v, int k, const R* w
   if (k > kMaxVec) return QCD_ERR_ARG;
   const long long n = nel<R>(c);
   const unsigned grid = blas_grid(n);
-  ProfScope ps(c, QCD_KERNEL_BLAS, s, sizeof(E) * (double)n * (k + 1), 8.0 * c->V * 12 * k);
+  // a conditional (second Gram-Schmidt) pass is counted as no work: the host
+  // cannot know whether it runs, and on well-conditioned bases it returns at once
+  const double work = cond ? 0.0 : 1.0;
+  ProfScope ps(c, QCD_KERNEL_BLAS, s, work * sizeof(E) * (double)n * (k + 1), work * 8.0 * c->V * 12 * k);
   const int K = pick_k(k);
   int done = 0;
   while (done < k) {
@@ -399,7 +402,9 @@ static int axpy_dot_impl(qcd_ctx* c, double* part, const R* const* v, int k, con
   const unsigned grid = blas_grid(n);
   const int K = pick_k(k);
   const int M = DOT == 1 ? 2 * K : 3;
-  ProfScope ps(c, QCD_KERNEL_BLAS, s, sizeof(E) * (double)n * (k + 2 + (DOT == 2)), 16.0 * c->V * 12 * k);
+  const double work = cond ? 0.0 : 1.0;  // conditional pass: counted as no work (see blas_multidot)
+  ProfScope ps(c, QCD_KERNEL_BLAS, s, work * sizeof(E) * (double)n * (k + 2 + (DOT == 2)),
+               work * 16.0 * c->V * 12 * k);
   auto vl = make_list<R>(v, k);
   const E* r2 = (const E*)rho;
   E* w2 = (E*)w;

@@ -52,7 +52,7 @@ struct Rec {
 struct Timer {  // CUDA-event timing of one kernel class
   long long launches = 0;
   double total_ms = 0;
-  double bytes = 0, flops = 0;  // per launch, of the last launch
+  double bytes = 0, flops = 0;  // summed algorithmic bytes and flops of the timed launches
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
 };
 
@@ -155,6 +155,8 @@ int load_gauge_device(qcd_ctx* c, const double* lex_dev, cudaStream_t s);
 int ensure_gauge(qcd_ctx* c, int prec, cudaStream_t s);
 // convert records between precisions (same layout family)
 int convert_rec(qcd_ctx* c, const Rec& in, const Rec& out, cudaStream_t s);
+// out32 = FP32 of in64, out64 = FP64 of in32 through the integer-pipe conversions
+int convert_check(const double* in64, const float* in32, float* out32, double* out64, long long n, cudaStream_t s);
 
 // ---- clover.cu
 int build_clover(qcd_ctx* c, cudaStream_t s);

@@ -329,4 +329,22 @@ int convert_rec(qcd_ctx* c, const Rec& in, const Rec& out, cudaStream_t s) {
   return QCD_ERR_ARG;
 }
 
+// element by element: out32 = f64_to_f32(in64), out64 = f32_to_f64(in32), the
+// integer-pipe conversions of the SAP edges and the refinement kernels
+__global__ void convert_check_kernel(const double* __restrict__ in64, const float* __restrict__ in32,
+                                     float* __restrict__ out32, double* __restrict__ out64, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    out32[i] = f64_to_f32(in64[i]);
+    out64[i] = f32_to_f64(in32[i]);
+  }
+}
+
+int convert_check(const double* in64, const float* in32, float* out32, double* out64, long long n, cudaStream_t s) {
+  if (n == 0) return QCD_OK;
+  const long long blocks = (n + 255) / 256;
+  convert_check_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(in64, in32, out32, out64, n);
+  QCD_LAUNCHED();
+  return QCD_OK;
+}
+
 }  // namespace qcd

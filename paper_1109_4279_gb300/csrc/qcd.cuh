@@ -21,6 +21,42 @@ namespace qcd {
 enum Prec : int { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
 
 // ------------------------------------------------------------------------
+// FP64 <-> FP32 conversion on the integer pipes.  GB300 runs FP64 conversions
+// on its FP64 unit (2 per clock per SM), which turns kernels that convert a
+// few dozen values per thread into FP64-bound ones; these do the IEEE-754
+// conversion with integer operations for every normal result and hand the
+// rare rest (zero handled here; subnormal results, infinities, NaN) to the
+// hardware conversion, so the results are identical to it.
+// ------------------------------------------------------------------------
+// double -> float, round to nearest even: the 52-bit fraction is cut to 23
+// bits; the dropped 29 bits decide the rounding, and a carry out of the
+// fraction increments the exponent (reaching infinity past the largest float)
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t e = (hi >> 20) & 0x7ffu;  // biased FP64 exponent
+  if (e - 897u <= 253u) {                   // FP32 biased exponent e - 896 in 1 .. 254
+    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t rem = lo & 0x1fffffffu, half = 0x10000000u;
+    uint32_t r = ((e - 896u) << 23) | m;
+    r += (uint32_t)(rem > half) | ((uint32_t)(rem == half) & (m & 1u));
+    return __uint_as_float((hi & 0x80000000u) | r);
+  }
+  if ((b << 1) == 0ull) return __uint_as_float(hi & 0x80000000u);  // +-0
+  return __double2float_rn(x);
+}
+
+// float -> double (exact): rebias the exponent, widen the fraction
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e - 1u <= 253u)  // normal
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+  if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);  // +-0
+  return (double)f;
+}
+
+// ------------------------------------------------------------------------
 // complex arithmetic
 // ------------------------------------------------------------------------
 template <typename T>

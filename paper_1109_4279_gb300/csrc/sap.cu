@@ -574,6 +574,12 @@ struct PsiPrec<P64> {
   static constexpr int value = P64;
 };
 
+// FP64 values into the arithmetic type and back (integer-pipe conversions)
+__device__ __forceinline__ void from_f64(double x, float& y) { y = f64_to_f32(x); }
+__device__ __forceinline__ void from_f64(double x, double& y) { y = x; }
+__device__ __forceinline__ double as_f64(float x) { return f32_to_f64(x); }
+__device__ __forceinline__ double as_f64(double x) { return x; }
+
 // owned half of an FP32 / FP64 spinor field in global memory (spins 2 hf, 2 hf + 1
 // are reals 12 hf .. 12 hf + 11: float4 chunks 3 hf .. 3 hf + 2, or double2 chunks 6 hf ..)
 template <int PS, typename T>
@@ -584,7 +590,8 @@ __device__ __forceinline__ Half<T> g_half(const FieldPtr& f, int Vb, int blk, in
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const double2 v = d[(long long)k * Vb];
-      h.c[k / 3][k % 3] = {(T)v.x, (T)v.y};
+      from_f64(v.x, h.c[k / 3][k % 3].re);
+      from_f64(v.y, h.c[k / 3][k % 3].im);
     }
   } else {
     const float4* d = (const float4*)f.data + ((long long)blk * 6 + 3 * hf) * Vb + r;
@@ -603,7 +610,7 @@ __device__ __forceinline__ void g_half_store(const FieldPtr& f, int Vb, int blk,
   if constexpr (PS == P64) {
     double2* d = (double2*)f.data + ((long long)blk * 12 + 6 * hf) * Vb + r;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) d[(long long)k * Vb] = make_double2((double)h.c[k / 3][k % 3].re, (double)h.c[k / 3][k % 3].im);
+    for (int k = 0; k < 6; ++k) d[(long long)k * Vb] = make_double2(as_f64(h.c[k / 3][k % 3].re), as_f64(h.c[k / 3][k % 3].im));
   } else {
     float4* d = (float4*)f.data + ((long long)blk * 6 + 3 * hf) * Vb + r;
 #pragma unroll
@@ -612,6 +619,27 @@ __device__ __forceinline__ void g_half_store(const FieldPtr& f, int Vb, int blk,
       d[(long long)k * Vb] = make_float4((float)a.re, (float)a.im, (float)b.re, (float)b.im);
     }
   }
+}
+
+// owned half of a 16-bit spinor record ([blk][3 chunks][Vb] uint4 of 8 reals,
+// complex k at chunk k / 4): half hf is chunk 2 hf and the hf-th 8-byte half of
+// chunk 1, scaled by the site's norm
+template <int P>
+__device__ __forceinline__ Half<float> g_half16(const FieldPtr& f, int Vb, int blk, int r, int hf) {
+  const uint4* d = (const uint4*)f.data + (long long)blk * 3 * Vb + r;
+  const uint4 a = __ldg(d + (long long)(2 * hf) * Vb);
+  const uint2 b = __ldg((const uint2*)(d + Vb) + hf);
+  const float s = f.norm ? __ldg(f.norm + (long long)blk * Vb + r) : 1.0f;
+  // complexes 6 hf .. 6 hf + 5: hf = 0 -> chunk 0 (0-3), chunk 1 low (4-5);
+  // hf = 1 -> chunk 1 high (6-7), chunk 2 (8-11)
+  const uint32_t w[6] = {hf ? b.x : a.x, hf ? b.y : a.y, hf ? a.x : a.z, hf ? a.y : a.w, hf ? a.z : b.x, hf ? a.w : b.y};
+  Half<float> h;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float2 x = to_f2<P>(w[k]);
+    h.c[k / 3][k % 3] = {s * x.x, s * x.y};
+  }
+  return h;
 }
 
 // receive the other colour's face contributions at site (blk, r) for the
@@ -788,36 +816,28 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
     pkO[1] = hf ? pko[3] : pko[1];
   }
 
-  // ---- residual of the two sites (own halves)
+  // ---- residual of the two sites (own halves only: the pair's two threads
+  // read complementary halves)
   Half<T> rho_e, rho_o;
-  {
-    Spinor<T> fe, fo;
-    if (a.read_eta && a.io32) {
-      const Spinor<float> de = load_spinor<P32, float>(a.eta, Vb, blk, re);
-      const Spinor<float> dd = load_spinor<P32, float>(a.eta, Vb, blk, ro);
+  if (a.read_eta && a.io32) {
+    const Half<float> de = g_half<P32, float>(a.eta, Vb, blk, re, hf);
+    const Half<float> dd = g_half<P32, float>(a.eta, Vb, blk, ro, hf);
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          fe.c[s][c] = {(T)de.c[s][c].re, (T)de.c[s][c].im};
-          fo.c[s][c] = {(T)dd.c[s][c].re, (T)dd.c[s][c].im};
-        }
-    } else if (a.read_eta) {
-      const Spinor<double> de = load_spinor<P64, double>(a.eta, Vb, blk, re);
-      const Spinor<double> dd = load_spinor<P64, double>(a.eta, Vb, blk, ro);
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          fe.c[s][c] = {(T)de.c[s][c].re, (T)de.c[s][c].im};
-          fo.c[s][c] = {(T)dd.c[s][c].re, (T)dd.c[s][c].im};
-        }
-    } else {
-      fe = load_spinor<P, T>(a.rho, Vb, blk, re);
-      fo = load_spinor<P, T>(a.rho, Vb, blk, ro);
-    }
-    rho_e = half_of(fe, hf);
-    rho_o = half_of(fo, hf);
+      for (int c = 0; c < 3; ++c) {
+        rho_e.c[s][c] = {(T)de.c[s][c].re, (T)de.c[s][c].im};
+        rho_o.c[s][c] = {(T)dd.c[s][c].re, (T)dd.c[s][c].im};
+      }
+  } else if (a.read_eta) {
+    rho_e = g_half<P64, T>(a.eta, Vb, blk, re, hf);
+    rho_o = g_half<P64, T>(a.eta, Vb, blk, ro, hf);
+  } else if constexpr (kHalf) {
+    rho_e = g_half16<P>(a.rho, Vb, blk, re, hf);
+    rho_o = g_half16<P>(a.rho, Vb, blk, ro, hf);
+  } else {
+    rho_e = g_half<P, T>(a.rho, Vb, blk, re, hf);
+    rho_o = g_half<P, T>(a.rho, Vb, blk, ro, hf);
   }
   if constexpr (kHalf) {
     // every thread waits (bounded) for the staging copies; a time-out is made
@@ -932,12 +952,7 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
         for (int c = 0; c < 3; ++c) fv.c[s][c] = {(float)v.c[s][c].re, (float)v.c[s][c].im};
       g_half_store<P32, float>(a.out, Vb, blk, rs, hf, fv);
     } else {
-      Half<double> dv;
-#pragma unroll
-      for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dv.c[s][c] = {(double)v.c[s][c].re, (double)v.c[s][c].im};
-      g_half_store<P64, double>(a.out, Vb, blk, rs, hf, dv);
+      g_half_store<P64, TS>(a.out, Vb, blk, rs, hf, v);  // widened on the integer pipes
     }
   }
   if (a.write_rho && hf == 0) {
