@@ -111,6 +111,8 @@ typedef struct {
     int cg_fallback;   /* 1: when FGCR or FGMRES-DR stagnates or exhausts max_restarts, continue from its
                           iterate with CG on the normal equations (default 0) */
     int cg_max_iter;   /* iteration limit of CG, as solver or fallback (default 20000) */
+    int zero_guess;    /* 1: start from x = 0 and ignore the input content of x (a host x is then not
+                          uploaded, only written); 0 (default): x holds the initial guess */
 } qcd_solver_params;
 
 /* Solver report, always filled (also on failure). */
@@ -127,7 +129,7 @@ typedef struct {
 } qcd_solve_info;
 
 /* Default solver parameters: tol 1e-10, nkv 16, max_restarts 100, SAP with
- * ncy 4 and nmr 4 in FP32, FP64 outer operator. */
+ * ncy 4 and nmr 4 in FP32, FP64 outer operator, initial guess read from x. */
 void qcd_solver_defaults(qcd_solver_params* sp);
 
 /*

@@ -44,7 +44,7 @@ class SolverParams(ctypes.Structure):
                 ("precond", ctypes.c_int), ("ncy", ctypes.c_int), ("nmr", ctypes.c_int),
                 ("sap_prec", ctypes.c_int), ("outer_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("solver", ctypes.c_int), ("ndefl", ctypes.c_int), ("cg_fallback", ctypes.c_int),
-                ("cg_max_iter", ctypes.c_int)]
+                ("cg_max_iter", ctypes.c_int), ("zero_guess", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

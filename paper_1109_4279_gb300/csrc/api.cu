@@ -111,6 +111,7 @@ void qcd_solver_defaults(qcd_solver_params* sp) {
   sp->ndefl = 4;
   sp->cg_fallback = 0;
   sp->cg_max_iter = 20000;
+  sp->zero_guess = 0;
 }
 
 const char* qcd_status_string(int st) {
@@ -299,13 +300,21 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
       }
       stage[k] = w.stage;
       cudaError_t e = cudaMemcpyAsync(stage[k], b[k], fbytes, cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(stage[k] + p.c->V * 24, x[k], fbytes, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && !sp.zero_guess)
+        e = cudaMemcpyAsync(stage[k] + p.c->V * 24, x[k], fbytes, cudaMemcpyHostToDevice, s);
       if (e != cudaSuccess) st = cuda_fail(e, "solve upload");
       bd = stage[k];
       xd = stage[k] + p.c->V * 24;
     }
     if (st == QCD_OK) st = import_spinor(p.c, bd, p.b, 1, s);
-    if (st == QCD_OK) st = import_spinor(p.c, xd, p.x, 1, s);
+    if (st == QCD_OK) {
+      if (sp.zero_guess) {
+        const cudaError_t e = cudaMemsetAsync(p.x.data, 0, fbytes, s);  // FP64 block-major, same size
+        if (e != cudaSuccess) st = cuda_fail(e, "solve zero guess");
+      } else {
+        st = import_spinor(p.c, xd, p.x, 1, s);
+      }
+    }
   }
   if (st == QCD_OK) {
     cudaEvent_t e0, e1;
@@ -398,7 +407,10 @@ int qcd_solve_dagger(qcd_ctx* c, const double* b, double* x, const qcd_solver_pa
     if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
   // D^+ x = b  <=>  D (g5 x) = g5 b
   QCD_TRY(import_spinor(c, b, w->b, 1, s));
-  QCD_TRY(import_spinor(c, x, w->x, 1, s));
+  if (sp.zero_guess)
+    QCD_CUDA(cudaMemsetAsync(w->x.data, 0, (size_t)c->V * 24 * sizeof(double), s));
+  else
+    QCD_TRY(import_spinor(c, x, w->x, 1, s));
   QCD_TRY(blas_gamma5(c, (const double*)w->b.data, (double*)w->b.data, 0, s));
   QCD_TRY(blas_gamma5(c, (const double*)w->x.data, (double*)w->x.data, 0, s));
   int st = solve_one(c, w->b, w->x, sp, info, s);

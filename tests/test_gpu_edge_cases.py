@@ -160,3 +160,31 @@ def test_solves_are_deterministic():
     x2, i2 = lat.solve(b, tol=1e-10, sap_prec="f16")
     assert torch.equal(x1, x2) and i1[0]["iterations"] == i2[0]["iterations"]
     lat.close()
+
+
+def test_zero_guess_ignores_the_input_x():
+    """zero_guess = 1 starts from x = 0 whatever x holds (here NaN), for device
+    and host buffers and for the adjoint solve: the same iterates, bit for bit,
+    as a solve whose x holds zeros."""
+    from paper_1109_4279_gb300 import binding
+    dims = (8, 8, 8, 8)
+    lat, U, rng = _lat(dims, (4, 4, 2, 2))
+    bn = synth.gaussian_spinor(dims, rng)
+    nan = complex(float("nan"), float("nan"))
+    sp0 = binding.solver_params(tol=1e-10, sap_prec="f16")
+    sp1 = binding.solver_params(tol=1e-10, sap_prec="f16", zero_guess=1)
+    b = torch.from_numpy(bn).cuda()
+    x_ref = torch.zeros_like(b)
+    _, i_ref = binding.qcd_solve(lat.ctx, b, x_ref, 1, sp0)
+    for dev in (True, False):
+        bb = b if dev else b.cpu()
+        x = torch.full_like(bb, nan)
+        st, info = binding.qcd_solve(lat.ctx, bb, x, 1, sp1, raise_on_fail=False)
+        assert st == 0 and info[0]["iterations"] == i_ref[0]["iterations"]
+        assert torch.equal(x.cpu(), x_ref.cpu())
+    y_ref = torch.zeros_like(b)
+    binding.qcd_solve_dagger(lat.ctx, b, y_ref, sp0)
+    y = torch.full_like(b, nan)
+    st, _ = binding.qcd_solve_dagger(lat.ctx, b, y, sp1, raise_on_fail=False)
+    assert st == 0 and torch.equal(y, y_ref)
+    lat.close()
