@@ -233,7 +233,7 @@ struct Problem {
   cudaStream_t s = nullptr;
   Rec b, x;  // FP64 internal fields (b is read, x holds the guess / solution)
   qcd_solve_info info{};
-  // driver state
+  // state of the solver loop
   double bn = 0, rn = 0;
   int kused = 0, slow = 0;
   bool active = true, cycle_done = false;
