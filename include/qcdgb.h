@@ -76,6 +76,9 @@ extern "C" {
 #define QCD_SOLVER_FGMRES_DR 1  /* flexible GMRES with deflated restarts (Sec. 4) */
 #define QCD_SOLVER_CG 2         /* CG on the normal equations D^+ D x = D^+ b, FP64 (Sec. 4: CG for the
                                    most difficult cases) */
+#define QCD_SOLVER_CG_EO 3      /* even/odd-preconditioned CG, FP64: CG on Dhat^+ Dhat x_e = Dhat^+ bhat_e with
+                                   the Schur complement Dhat = A_ee - D_eo A_oo^-1 D_oe on the even sites,
+                                   bhat_e = b_e - D_eo A_oo^-1 b_o, then x_o = A_oo^-1 (b_o - D_oe x_e) */
 
 typedef struct qcd_ctx qcd_ctx;
 
@@ -108,9 +111,10 @@ typedef struct {
                           the harmonic Ritz vectors of the ndefl smallest values (Sec. 4, deflated restarts);
                           FP64 recursion (outer_prec must be QCD_PREC_F64), nkv = cycle length m */
     int ndefl;         /* QCD_SOLVER_FGMRES_DR: deflated vectors k, 0 <= k < nkv (default 4) */
-    int cg_fallback;   /* 1: when FGCR or FGMRES-DR stagnates or exhausts max_restarts, continue from its
-                          iterate with CG on the normal equations (default 0) */
-    int cg_max_iter;   /* iteration limit of CG, as solver or fallback (default 20000) */
+    int cg_fallback;   /* when FGCR or FGMRES-DR stagnates or exhausts max_restarts, continue from its
+                          iterate with 1: CG on the normal equations, 2: even/odd-preconditioned CG
+                          (QCD_SOLVER_CG_EO); 0 (default): no fallback */
+    int cg_max_iter;   /* iteration limit of CG (either form), as solver or fallback (default 20000) */
     int zero_guess;    /* 1: start from x = 0 and ignore the input content of x (a host x is then not
                           uploaded, only written); 0 (default): x holds the initial guess */
 } qcd_solver_params;

@@ -21,7 +21,7 @@ STATUS = {
 }
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 PRECOND = {"none": 0, "sap": 1}
-SOLVER = {"fgcr": 0, "fgmres_dr": 1, "cg": 2}
+SOLVER = {"fgcr": 0, "fgmres_dr": 1, "cg": 2, "cg_eo": 3}
 KERNEL = {"dirac": 0, "sap": 1, "blas": 2, "residual": 3}
 
 

@@ -269,6 +269,8 @@ static int join_streams(cudaStream_t s, std::vector<Problem>& probs) {
 // solve a set of problems whose b/x are lexicographic device or host arrays
 static int solve_problems(std::vector<Problem>& probs, const double* const* b, double* const* x, bool dev,
                           const qcd_solver_params& sp, qcd_solve_info* info, cudaStream_t s) {
+  if (sp.solver < QCD_SOLVER_FGCR || sp.solver > QCD_SOLVER_CG_EO || sp.cg_fallback < 0 || sp.cg_fallback > 2)
+    return QCD_ERR_ARG;
   const int n = (int)probs.size();
   std::vector<double*> stage(n, nullptr);
   int st = QCD_OK;
@@ -324,24 +326,7 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
     fork_streams(s, probs);
     bool prof = false;
     for (auto& p : probs) prof |= p.c->prof;
-    if (sp.solver == QCD_SOLVER_CG)
-      st = cg_batch(probs, sp, false);
-    else if (sp.solver == QCD_SOLVER_FGMRES_DR)
-      st = fgmres_dr_batch(probs, sp);
-    else
-      st = fgcr_batch(probs, sp, n > 1 && !prof);
-    // CG fallback from the Krylov solver's iterate (Sec. 4: CG for the most difficult cases)
-    if (sp.solver != QCD_SOLVER_CG && sp.cg_fallback && st != QCD_OK) {
-      bool any = false;
-      for (auto& p : probs) any |= (p.status == QCD_STAGNATED || p.status == QCD_NOT_CONVERGED);
-      if (any) {
-        int st2 = cg_batch(probs, sp, true);
-        st = QCD_OK;
-        for (auto& p : probs)
-          if (p.status != QCD_OK && st == QCD_OK) st = p.status;
-        (void)st2;
-      }
-    }
+    st = run_solver(probs, sp, n > 1 && !prof);
     join_streams(s, probs);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);

@@ -276,4 +276,84 @@ int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& 
   return reduce_partials(part, (int)grid, 1, 1, d_norm2, s);
 }
 
+// ------------------------------------------------------------------------
+// Even/odd split of D over the whole lattice (the global parity of a site is
+// its block-local parity, block extents being even).  For the sites of
+// parity `par` (r = par * Vbh + rr):
+//   PRE = 1:  out = c1 * M x + c2 * H y
+//   PRE = 0:  out = M (c1 x + c2 H y)
+// with H y = -1/2 sum of the hops from the opposite parity (D's hopping term,
+// its adjoint's with DAG), M = Ahat on these sites (A_ee on even, A_oo^-1 on
+// odd) if USE_M, else 1.  x and out are read / written on parity par only, y
+// on the other parity only, so out may be y.  c2 = 0 skips the hops, c1 = 0
+// the load of x.  FP64 throughout.
+// ------------------------------------------------------------------------
+template <int DAG, int PRE, int USE_M>
+__global__ void __launch_bounds__(256, 2) eo_kernel(Geom g, const void* __restrict__ U, FieldPtr Ahat, FieldPtr x,
+                                                 FieldPtr y, FieldPtr out, int par, double c1, double c2) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.V / 2) return;
+  const int blk = (int)(t / g.Vbh), r = (int)(t - (long long)blk * g.Vbh) + par * g.Vbh;
+  Spinor<double> h;
+  zero(h);
+  if (c2 != 0.0) {
+    int n[4], yc[4];
+    block_coords(g, blk, n);
+    const int packed = __ldg(g.r2y + r);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) yc[mu] = ycoord(packed, mu);
+    hop_pair<0, P64, DAG, double>(g, U, y, blk, r, yc, n, h);
+    hop_pair<1, P64, DAG, double>(g, U, y, blk, r, yc, n, h);
+    hop_pair<2, P64, DAG, double>(g, U, y, blk, r, yc, n, h);
+    hop_pair<3, P64, DAG, double>(g, U, y, blk, r, yc, n, h);
+  }
+  Spinor<double> v;
+  zero(v);
+  if (c1 != 0.0) v = load_spinor<P64, double>(x, g.Vb, blk, r);
+  double cm[72];
+  if (USE_M) load_record<P64, 72, double>(Ahat, g.Vb, blk, r, cm);
+  if (PRE && USE_M) v = clover_apply(cm, v);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      v.c[a][b] = {fma(c2, h.c[a][b].re, c1 * v.c[a][b].re), fma(c2, h.c[a][b].im, c1 * v.c[a][b].im)};
+  if (!PRE && USE_M) v = clover_apply(cm, v);
+  store_spinor<P64, double>(out, g.Vb, blk, r, v);
+}
+
+int eo_apply(qcd_ctx* c, const Rec& x, const Rec& y, const Rec& out, int par, int dagger, int pre, int use_m,
+             double c1, double c2, cudaStream_t s) {
+  if (x.prec != P64 || y.prec != P64 || out.prec != P64 || (par != 0 && par != 1)) return QCD_ERR_ARG;
+  QCD_TRY(ensure_gauge(c, P64, s));
+  QCD_TRY(ensure_clover(c, P64, s));
+  const unsigned grid = (unsigned)((c->V / 2 + 255) / 256);
+  // algorithmic bytes: per site of parity par, 8 neighbour spinors and 8 links
+  // (hops), x and the clover record (if used) and the result
+  const double sites = (double)c->V / 2;
+  const double bytes = sites * ((c2 != 0.0 ? 8 * 192 + 8 * 144 : 0) + (c1 != 0.0 ? 192 : 0) + (use_m ? 576 : 0) + 192);
+  ProfScope ps(c, QCD_KERNEL_DIRAC, s, bytes, sites * ((c2 != 0.0 ? 1320.0 : 0.0) + (use_m ? 504.0 : 0.0)));
+  const void* U = c->U[P64];
+  const FieldPtr A = c->Ahat[P64].ptr();
+#define EO(D, P, M) eo_kernel<D, P, M><<<grid, 256, 0, s>>>(c->g, U, A, x.ptr(), y.ptr(), out.ptr(), par, c1, c2)
+  if (dagger) {
+    if (pre) { if (use_m) EO(1, 1, 1); else EO(1, 1, 0); }
+    else { if (use_m) EO(1, 0, 1); else EO(1, 0, 0); }
+  } else {
+    if (pre) { if (use_m) EO(0, 1, 1); else EO(0, 1, 0); }
+    else { if (use_m) EO(0, 0, 1); else EO(0, 0, 0); }
+  }
+#undef EO
+  QCD_LAUNCHED();
+  return QCD_OK;
+}
+
+// out_e = Dhat x_e = A_ee x_e - H_eo A_oo^-1 H_oe x_e (dagger: Dhat^+, the same
+// with the adjoint's hops); tmp receives A_oo^-1 H_oe x_e on the odd sites.
+// Only the even sites of x and out are read / written.
+int schur_apply(qcd_ctx* c, const Rec& x, const Rec& tmp, const Rec& out, int dagger, cudaStream_t s) {
+  QCD_TRY(eo_apply(c, x, x, tmp, 1, dagger, 0, 1, 0.0, 1.0, s));
+  return eo_apply(c, x, tmp, out, 0, dagger, 1, 1, 1.0, -1.0, s);
+}
+
 }  // namespace qcd

@@ -168,6 +168,14 @@ int ensure_clover(qcd_ctx* c, int prec, cudaStream_t s);
 int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s, int nrhs = 1);
 // r = b - D x and |r|^2 partial sums (FP64); optional second output of D x
 int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s);
+// even/odd split (FP64): on the sites of parity par,
+//   pre = 1: out = c1 M x + c2 H y;  pre = 0: out = M (c1 x + c2 H y),
+// H the hopping term of D (of D^+ with dagger) from the other parity, M the
+// block clover Ahat (A_ee / A_oo^-1) if use_m, else 1
+int eo_apply(qcd_ctx* c, const Rec& x, const Rec& y, const Rec& out, int par, int dagger, int pre, int use_m,
+             double c1, double c2, cudaStream_t s);
+// out_e = Dhat x_e (dagger: Dhat^+ x_e), Dhat = A_ee - H_eo A_oo^-1 H_oe; tmp: odd-site scratch
+int schur_apply(qcd_ctx* c, const Rec& x, const Rec& tmp, const Rec& out, int dagger, cudaStream_t s);
 
 // ---- sap.cu
 int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s);
@@ -250,6 +258,8 @@ void dr_release(Workspace& w);
 // fallback_only, only problems whose status is QCD_STAGNATED or
 // QCD_NOT_CONVERGED run, from their current x
 int cg_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool fallback_only);
+// dispatch on sp.solver (FGCR, FGMRES-DR, CG, even/odd CG) plus the CG fallback
+int run_solver(std::vector<Problem>& probs, const qcd_solver_params& sp, bool use_graphs);
 void cg_release(Workspace& w);
 int solve_one(qcd_ctx* c, const Rec& b, const Rec& x, const qcd_solver_params& sp, qcd_solve_info* info,
               cudaStream_t s);

@@ -419,6 +419,33 @@ int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool us
   return first;
 }
 
+// the solver sp.solver names on every problem, then (cg_fallback) CG from the
+// iterate of a Krylov solve that stagnated or ran out of restarts (Sec. 4: CG
+// for the most difficult cases)
+int run_solver(std::vector<Problem>& probs, const qcd_solver_params& sp, bool use_graphs) {
+  if (sp.solver < QCD_SOLVER_FGCR || sp.solver > QCD_SOLVER_CG_EO || sp.cg_fallback < 0 || sp.cg_fallback > 2)
+    return QCD_ERR_ARG;
+  const bool cg = sp.solver == QCD_SOLVER_CG || sp.solver == QCD_SOLVER_CG_EO;
+  int st;
+  if (cg)
+    st = cg_batch(probs, sp, false);
+  else if (sp.solver == QCD_SOLVER_FGMRES_DR)
+    st = fgmres_dr_batch(probs, sp);
+  else
+    st = fgcr_batch(probs, sp, use_graphs);
+  if (!cg && sp.cg_fallback && st != QCD_OK) {
+    bool any = false;
+    for (auto& p : probs) any |= (p.status == QCD_STAGNATED || p.status == QCD_NOT_CONVERGED);
+    if (any) {
+      cg_batch(probs, sp, true);
+      st = QCD_OK;
+      for (auto& p : probs)
+        if (p.status != QCD_OK && st == QCD_OK) st = p.status;
+    }
+  }
+  return st;
+}
+
 int solve_one(qcd_ctx* c, const Rec& b, const Rec& x, const qcd_solver_params& sp, qcd_solve_info* info,
               cudaStream_t s) {
   Workspace* w = ensure_ws(c);
@@ -433,7 +460,7 @@ int solve_one(qcd_ctx* c, const Rec& b, const Rec& x, const qcd_solver_params& s
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-  int st = fgcr_batch(probs, sp, false);
+  int st = run_solver(probs, sp, false);
   cudaEventRecord(e1, s);
   cudaEventSynchronize(e1);
   float ms = 0;
