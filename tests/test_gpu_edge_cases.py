@@ -188,3 +188,22 @@ def test_zero_guess_ignores_the_input_x():
     st, _ = binding.qcd_solve_dagger(lat.ctx, b, y, sp1, raise_on_fail=False)
     assert st == 0 and torch.equal(y, y_ref)
     lat.close()
+
+
+def test_zero_guess_with_several_right_hand_sides_on_host(orc):
+    """nrhs = 2 from host buffers with zero_guess: both converge against the
+    oracle's operator although x holds NaN."""
+    from paper_1109_4279_gb300 import binding
+    dims = (8, 8, 8, 8)
+    lat, U, rng = _lat(dims, (4, 4, 2, 2))
+    bn = synth.gaussian_spinor(dims, rng, nrhs=2)
+    b = torch.from_numpy(bn)
+    x = torch.full_like(b, complex(float("nan"), float("nan")))
+    st, info = binding.qcd_solve(lat.ctx, b, x, 2, binding.solver_params(tol=1e-10, sap_prec="f16", zero_guess=1),
+                                 raise_on_fail=False)
+    assert st == 0 and [i["status"] for i in info] == [0, 0]
+    A = orc.clover(dims, U, 0.0, 1.5)
+    for k in range(2):
+        r = bn[k] - orc.apply_D(dims, U, A, AP, x[k].numpy())
+        assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(bn[k])
+    lat.close()
