@@ -240,7 +240,7 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
     dirac_kernel<PP, 1, BS><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);           \
   else                                                                                                 \
     dirac_kernel<PP, 0, BS><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);
-  // 16-bit storage is issue-bound, so it gets the fixed-shape instantiations
+  // 16-bit storage (FP16, BF16) is issue-bound, so it gets the fixed-shape instantiations
   const int bs = block_shape_id(c->g);
   switch (prec) {
     case P64: LAUNCH(P64, 0); break;
@@ -254,7 +254,15 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
         LAUNCH(P16, 0);
       }
       break;
-    case PB16: LAUNCH(PB16, 0); break;
+    case PB16:
+      if (bs == 1) {
+        LAUNCH(PB16, 1);
+      } else if (bs == 2) {
+        LAUNCH(PB16, 2);
+      } else {
+        LAUNCH(PB16, 0);
+      }
+      break;
     default: return QCD_ERR_ARG;
   }
 #undef LAUNCH

@@ -987,19 +987,19 @@ template <int P, typename T>
 static int set_smem_attr(const Geom& g, int maxsm) {
   const size_t smem = sap_smem_bytes<P, T>(g);
   if (smem > (size_t)maxsm) return QCD_ERR_UNSUPPORTED;
-  if constexpr (P == P16) {
+  if constexpr (P == P16 || P == PB16) {
     if (sap_vb_key(g.Vb) == 256) return set_smem_attr_vb<P, T, 256>(smem);
     if (sap_vb_key(g.Vb) == 512) return set_smem_attr_vb<P, T, 512>(smem);
   }
   return set_smem_attr_vb<P, T, 0>(smem);
 }
 
-// launch one colour half-sweep; FP16 block fields of 4^4 and 8 x 4^3 blocks
+// launch one colour half-sweep; 16-bit block fields of 4^4 and 8 x 4^3 blocks
 // run the instantiation for their volume
 template <int P, typename T>
 static void sap_launch(const Geom& g, unsigned grid, int threads, cudaStream_t s, const SapArgs& a) {
   const size_t smem = sap_smem_bytes<P, T>(g);
-  if constexpr (P == P16) {
+  if constexpr (P == P16 || P == PB16) {
     if (sap_vb_key(g.Vb) == 256) {
       sap_sweep_kernel<P, T, 256><<<grid, threads, smem, s>>>(a);
       return;
