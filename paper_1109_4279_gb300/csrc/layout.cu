@@ -90,7 +90,7 @@ __global__ void import_kernel(Geom g, const double* __restrict__ lex, FieldPtr o
   } else {
     float w[24];
 #pragma unroll
-    for (int k = 0; k < 24; ++k) w[k] = (float)v[k];
+    for (int k = 0; k < 24; ++k) w[k] = f64_to_f32(v[k]);
     store_record<P, 24, float>(f, g.Vb, blk, r, w);
   }
 }
@@ -114,7 +114,7 @@ __global__ void export_kernel(Geom g, FieldPtr in, double* __restrict__ lex, lon
     float w[24];
     load_record<P, 24, float>(f, g.Vb, blk, r, w);
 #pragma unroll
-    for (int k = 0; k < 24; ++k) v[k] = w[k];
+    for (int k = 0; k < 24; ++k) v[k] = f32_to_f64(w[k]);
   }
   double2* dst = (double2*)lex + ((long long)rhs * g.V + lex_index(g, x)) * 12;
 #pragma unroll

@@ -158,17 +158,25 @@ def test_solve_unpreconditioned_and_initial_guess(orc):
     lat.close()
 
 
-def test_solve_host_pointers(orc):
-    """b and x in host memory: the library stages them itself."""
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "page-locked"])
+def test_solve_host_pointers(orc, pinned):
+    """b and x in host memory (pageable or page-locked): the library stages
+    them through device memory; the solution is bit for bit the one of the
+    same solve on device buffers."""
     w = synth.WORKLOADS["4^4 fp64"]
     dims = w["dims"]
     lat, U, A, b = _setup(dims, w["block"], w["eps"], w["seed"], w["m0"], w["csw"])
     from paper_1109_4279_gb300 import binding
     bt = torch.from_numpy(b.copy())
     x = torch.zeros_like(bt)
+    if pinned:
+        bt, x = bt.pin_memory(), x.pin_memory()
     st, info = binding.qcd_solve(lat.ctx, bt, x, 1, binding.solver_params(tol=1e-10))
     assert st == 0
     assert _oracle_residual(orc, dims, U, A, b, x.numpy()) <= 1.05e-10
+    xd = torch.zeros_like(bt).cuda()
+    binding.qcd_solve(lat.ctx, bt.cuda(), xd, 1, binding.solver_params(tol=1e-10))
+    assert torch.equal(xd.cpu(), x)
     lat.close()
 
 
