@@ -189,6 +189,17 @@ def max_over_ranks(world, value, device="cuda"):
     return float(t.item())
 
 
+def from_rank0(world, value, device="cuda"):
+    """rank 0's integer value on every rank (one choice for all replicas)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([int(value)], dtype=torch.int64, device=device)
+    dist.broadcast(t, src=0)
+    return int(t.item())
+
+
 # --------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------
@@ -505,7 +516,8 @@ def run_ours(args, world, rank, local):
                                outer_prec=args.outer_prec)
         best, times = B.qcd_tune_block(w["dims"], w["m0"], w["csw"], torch.from_numpy(U).cuda(),
                                        torch.from_numpy(b).cuda(), candidates=cands, params=sp_t)
-        w["block"] = tuple(best)
+        # every replica runs rank 0's choice
+        w["block"] = cands[from_rank0(world, cands.index(tuple(best)))]
         tuning = {"x".join(map(str, c)): t for c, t in times.items()}
     lat = B.Lattice(w["dims"], w["block"], w["m0"], w["csw"])
     lat.load_gauge(torch.from_numpy(U).cuda())
@@ -600,10 +612,12 @@ def run_ours(args, world, rank, local):
                                      "bytes_per_site_rhs": byts / V / R,
                                      "site_rhs_per_s": V * R / (ms * 1e-3)}
 
-    comparisons = run_comparisons(args, lat, w, U, b_t, sp, ms_per_step) if not args.quick else None
-    batched = run_batched(args) if not args.quick else None
-    near_critical = run_near_critical(args) if not args.quick else None
-    configs = run_configs(args, pk) if not args.quick else None
+    # the comparison sections run at N = 1 only (they hold the GPUs for minutes)
+    extra = not args.quick and world == 1
+    comparisons = run_comparisons(args, lat, w, U, b_t, sp, ms_per_step) if extra else None
+    batched = run_batched(args) if extra else None
+    near_critical = run_near_critical(args) if extra else None
+    configs = run_configs(args, pk) if extra else None
 
     # end to end through the public API with host buffers
     b_h = torch.from_numpy(b.copy()).pin_memory()

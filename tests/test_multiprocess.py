@@ -2,7 +2,8 @@
 
 bench.py under torchrun runs one independent solve per GPU (weak scaling, no
 data-path collective); the only cross-rank steps are the barriers around the
-timed region and the max-over-ranks of the elapsed time, exercised here.
+timed region, the max-over-ranks of the elapsed time and the broadcast of
+rank 0's Schwarz block choice, exercised here.
 """
 import os
 import socket
@@ -28,8 +29,9 @@ def _worker(rank, world, port, q):
     import bench
     bench.barrier(world)
     t = bench.max_over_ranks(world, 1.0 + rank, device="cpu")
+    c = bench.from_rank0(world, 7 + rank, device="cpu")  # the block choice every replica runs
     bench.barrier(world)
-    q.put((rank, t))
+    q.put((rank, (t, c)))
     dist.destroy_process_group()
 
 
@@ -45,7 +47,7 @@ def test_max_over_ranks_two_gloo_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    assert out == {0: 2.0, 1: 2.0}
+    assert out == {0: (2.0, 7), 1: (2.0, 7)}
 
 
 def test_reference_arm_silent_on_nonzero_rank(monkeypatch, capsys):
