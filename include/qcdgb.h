@@ -365,6 +365,23 @@ int qcd_apply_D_noalloc(qcd_ctx* ctx, const double* in, double* out, int dagger,
 int qcd_sap_apply(qcd_ctx* ctx, const double* eta, double* psi, int ncy, int nmr, int sap_prec, void* stream);
 
 /*
+ * Test hooks for failure detection without a GPU fault.  The SAP kernel waits
+ * for its staging copies with a bounded spin (about a second); when the
+ * budget runs out the kernel records it, lets the copies in flight land and
+ * returns, and the calling solve or qcd_sap_apply reports QCD_ERR_TIMEOUT
+ * with the context still usable.  qcd_debug_set lets a test make that happen:
+ *   QCD_DEBUG_SAP_WAIT_CYCLES: budget of the staging wait in clock cycles,
+ *                              1 .. 2^31 (default 2^31);
+ *   QCD_DEBUG_SAP_EXTRA_TX:    bytes the staging barrier expects beyond the
+ *                              copies, 0 .. 4096 (default 0; any other value
+ *                              makes every wait run out).
+ * Returns QCD_ERR_ARG for an unknown setting or a value out of range.
+ */
+#define QCD_DEBUG_SAP_WAIT_CYCLES 0
+#define QCD_DEBUG_SAP_EXTRA_TX 1
+int qcd_debug_set(qcd_ctx* ctx, int what, long long value);
+
+/*
  * Precision codecs (Sec. 4: single-precision preconditioner inside a double
  * precision solver).  The kernels that move fields between the FP64 recursion
  * and the FP32 preconditioner (the first and last Schwarz sweeps, the

@@ -94,6 +94,7 @@ def lib():
             "qcd_apply_D_noalloc": (I, [P, P, P, I, P]),
             "qcd_sap_apply": (I, [P, P, P, I, I, I, P]),
             "qcd_convert_check": (I, [P, P, P, P, ctypes.c_longlong, P]),
+            "qcd_debug_set": (I, [P, I, ctypes.c_longlong]),
             "qcd_profile_enable": (I, [P, I]),
             "qcd_launch_count": (ctypes.c_longlong, []),
             "qcd_profile_reset": (I, [P]),
@@ -318,6 +319,15 @@ def qcd_apply_D_noalloc(ctx, inp, out, dagger=False):
 def qcd_sap_apply(ctx, eta, psi, ncy, nmr, prec="f32"):
     return check(lib().qcd_sap_apply(ctx, _ptr(eta), _ptr(psi), int(ncy), int(nmr), PREC[prec], _stream()),
                  "qcd_sap_apply")
+
+
+DEBUG = {"sap_wait_cycles": 0, "sap_extra_tx": 1}
+
+
+def qcd_debug_set(ctx, what, value):
+    """Test hooks of the SAP staging wait (see include/qcdgb.h)."""
+    return check(lib().qcd_debug_set(ctx, DEBUG[what] if isinstance(what, str) else int(what), int(value)),
+                 "qcd_debug_set")
 
 
 def qcd_convert_check(in64, in32, out32, out64):

@@ -535,10 +535,29 @@ int qcd_sap_apply(qcd_ctx* c, const double* eta, double* psi, int ncy, int nmr, 
   for (Rec* f : {&w->b, &w->x})
     if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, c->V));
   QCD_TRY(import_spinor(c, eta, w->b, 1, s));
+  QCD_CUDA(cudaMemsetAsync(c->d_scalars + 128, 0, sizeof(double), s));  // staging time-out flag
   QCD_TRY(sap_apply(c, w->sap, w->b, w->x, ncy, nmr, sap_prec, s));
   QCD_TRY(export_spinor(c, w->x, psi, 1, s));
+  int timed_out = 0;
+  QCD_CUDA(cudaMemcpyAsync(&timed_out, c->d_scalars + 128, sizeof(int), cudaMemcpyDeviceToHost, s));
   QCD_CUDA(cudaStreamSynchronize(s));
-  return QCD_OK;
+  return timed_out ? QCD_ERR_TIMEOUT : QCD_OK;
+}
+
+int qcd_debug_set(qcd_ctx* c, int what, long long value) {
+  if (!c) return QCD_ERR_ARG;
+  switch (what) {
+    case QCD_DEBUG_SAP_WAIT_CYCLES:
+      if (value < 1 || value > (1ll << 31)) return QCD_ERR_ARG;
+      c->dbg_sap_wait_cycles = value;
+      return QCD_OK;
+    case QCD_DEBUG_SAP_EXTRA_TX:
+      if (value < 0 || value > 4096) return QCD_ERR_ARG;
+      c->dbg_sap_extra_tx = (int)value;
+      return QCD_OK;
+    default:
+      return QCD_ERR_ARG;
+  }
 }
 
 int qcd_convert_check(const double* in64, const float* in32, float* out32, double* out64, long long n, void* stream) {

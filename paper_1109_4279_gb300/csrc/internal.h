@@ -128,6 +128,10 @@ struct qcd_ctx {
   int dirac_threads[4] = {256, 256, 256, 256};  // CTA size of the operator kernel per precision
   double* d_scalars = nullptr;  // small device array for coefficients
   double* h_scalars = nullptr;  // pinned host mirror
+  // test hooks (qcd_debug_set): budget of the SAP staging wait, and bytes its
+  // barrier expects beyond the copies (a count that never arrives)
+  long long dbg_sap_wait_cycles = 1ll << 31;
+  int dbg_sap_extra_tx = 0;
 };
 
 namespace qcd {

@@ -48,6 +48,8 @@ struct SapArgs {
   int F;                // face sites per block
   int fo[8];            // offset of face 2 mu + dir inside a block's face list
   int* err;             // set to 1 if a staging wait timed out
+  long long wait_cycles;  // budget of the staging wait (clock cycles)
+  int extra_tx;         // bytes the staging barrier expects beyond the copies (0; a test sets more)
 };
 
 template <typename T>
@@ -209,11 +211,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 
-// wait for phase 0 of the barrier for at most ~2^31 cycles (about a second)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b) {
+// wait for phase 0 of the barrier for at most `budget` clock cycles (2^31, about
+// a second, unless a test asks for less)
+static constexpr long long kWaitCycles = 1ll << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, long long budget) {
   const long long t0 = clock64();
   while (!mbar_try_wait(b, 0)) {
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > budget) return false;
   }
   return true;
 }
@@ -229,7 +233,7 @@ __device__ __forceinline__ void stage_issue(const SapArgs& a, int blk, unsigned 
                                   (const unsigned char*)(a.Ahat.norm + (size_t)blk * Vb)};
   unsigned char* dsts[3] = {links, clover, clover + 144 * Vb};
   const uint32_t sizes[3] = {(uint32_t)(96 * Vb), (uint32_t)(144 * Vb), (uint32_t)(4 * Vb)};
-  mbar_expect_tx(bar, sizes[0] + sizes[1] + sizes[2]);
+  mbar_expect_tx(bar, sizes[0] + sizes[1] + sizes[2] + (uint32_t)a.extra_tx);
   for (int k = 0; k < 3; ++k)
     for (uint32_t o = 0; o < sizes[k]; o += 16384) {
       const uint32_t n = sizes[k] - o < 16384 ? sizes[k] - o : 16384;
@@ -842,10 +846,10 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   if constexpr (kHalf) {
     // every thread waits (bounded) for the staging copies; a time-out is made
     // block-uniform, recorded, and the block is skipped
-    const bool ok = mbar_wait_bounded(bar);
+    const bool ok = mbar_wait_bounded(bar, a.wait_cycles);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicExch(a.err, 1);
-      mbar_wait_bounded(bar);  // let copies still in flight land before the CTA exits
+      mbar_wait_bounded(bar, kWaitCycles);  // let copies still in flight land before the CTA exits
       return;
     }
     expand_links<P>((const unsigned char*)s_r, (unsigned char*)st.base, Vb);
@@ -1071,6 +1075,8 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
   a.out = psi64.ptr();
   a.faces = w.faces;
   a.err = (int*)(c->d_scalars + 128);
+  a.wait_cycles = c->dbg_sap_wait_cycles;
+  a.extra_tx = c->dbg_sap_extra_tx;
   int off = 0;
   for (int mu = 0; mu < 4; ++mu) {
     a.fo[2 * mu] = off;

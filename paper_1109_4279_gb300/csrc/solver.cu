@@ -170,6 +170,10 @@ static int enqueue_iteration(Problem& p, const qcd_solver_params& sp, int k) {
   else
     QCD_TRY(gram_schmidt<double>(c, w, sp, k, s));
   QCD_CUDA(cudaMemcpyAsync(w.h_pin + k, w.d_rn + k, sizeof(double), cudaMemcpyDeviceToHost, s));
+  // the SAP staging time-out flag, so that a skipped block (whose garbage may
+  // turn into a NaN) is reported as the time-out it is
+  if (sp.precond == QCD_PRECOND_SAP)
+    QCD_CUDA(cudaMemcpyAsync(w.h_pin + w.nkv + 4, c->d_scalars + 128, sizeof(double), cudaMemcpyDeviceToHost, s));
   return QCD_OK;
 }
 
@@ -345,6 +349,13 @@ int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool us
         const double rk2 = p.w->h_pin[k];
         ++p.info.iterations;
         p.kused = k + 1;
+        int sap_err = 0;
+        if (sp.precond == QCD_PRECOND_SAP) memcpy(&sap_err, p.w->h_pin + p.w->nkv + 4, sizeof(int));
+        if (sap_err) {
+          p.status = QCD_ERR_TIMEOUT;
+          p.active = false;
+          continue;
+        }
         if (!(rk2 == rk2)) {
           p.status = QCD_NAN;
           p.active = false;

@@ -207,3 +207,37 @@ def test_zero_guess_with_several_right_hand_sides_on_host(orc):
         r = bn[k] - orc.apply_D(dims, U, A, AP, x[k].numpy())
         assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(bn[k])
     lat.close()
+
+
+def test_sap_staging_wait_runs_out_and_the_context_recovers(orc):
+    """A staging barrier told to expect 16 bytes more than its copies deliver
+    never completes: every block's bounded wait runs out (the drain wait after
+    it takes about a second), the kernel records it and returns, and
+    qcd_sap_apply and qcd_solve report QCD_ERR_TIMEOUT.  With the hook
+    cleared, the same context reproduces the oracle's SAP and solves."""
+    import ctypes
+    from paper_1109_4279_gb300 import binding
+    dims, block = (8, 8, 8, 8), (4, 4, 4, 4)
+    lat, U, rng = _lat(dims, block)
+    bn = synth.gaussian_spinor(dims, rng)
+    b = torch.from_numpy(bn).cuda()
+    psi = torch.empty_like(b)
+    binding.qcd_debug_set(lat.ctx, "sap_extra_tx", 16)
+    binding.qcd_debug_set(lat.ctx, "sap_wait_cycles", 1 << 20)
+    st = binding.lib().qcd_sap_apply(lat.ctx, binding._ptr(b), binding._ptr(psi), 1, 4, 2, binding._stream())
+    assert st == -13  # QCD_ERR_TIMEOUT
+    x = torch.zeros_like(b)
+    st, info = binding.qcd_solve(lat.ctx, b, x, 1, binding.solver_params(tol=1e-10, sap_prec="f16", ncy=1, nkv=1,
+                                                                         max_restarts=1), raise_on_fail=False)
+    assert st == -13 and info[0]["status"] == -13
+    for what, value in (("sap_extra_tx", -1), ("sap_wait_cycles", 0), (7, 1)):
+        assert binding.lib().qcd_debug_set(lat.ctx, binding.DEBUG.get(what, what), ctypes.c_longlong(value)) == -1
+    binding.qcd_debug_set(lat.ctx, "sap_extra_tx", 0)
+    binding.qcd_debug_set(lat.ctx, "sap_wait_cycles", 1 << 31)
+    out = lat.sap(b, ncy=4, nmr=4, prec="f16").cpu().numpy()
+    A = orc.clover(dims, U, 0.0, 1.5)
+    assert rel(out, orc.sap(dims, U, A, AP, block, bn, ncy=4, nmr=4)) < 5e-3
+    x, info = lat.solve(b, tol=1e-10, sap_prec="f16")
+    assert info[0]["status"] == 0
+    assert np.linalg.norm(bn - orc.apply_D(dims, U, A, AP, x.cpu().numpy())) <= 1.05e-10 * np.linalg.norm(bn)
+    lat.close()
