@@ -51,7 +51,7 @@ DW_FLOPS = 1824.0  # 1320 hopping + 504 clover per site
 # dram__bytes_write.sum, 24^3x48 lattice, 331,776 solved sites per launch); valid
 # for the kernel sources whose hash is stored with it and that block shape,
 # scaled by solved sites
-SAP_TRAFFIC = {"bytes_per_site": 589.9, "src_sha": "5dbcb0b6c53761fa", "block": (8, 4, 4, 4)}
+SAP_TRAFFIC = {"bytes_per_site": 589.8, "src_sha": "1184717e845a30eb", "block": (8, 4, 4, 4)}
 
 
 def sap_src_sha():
