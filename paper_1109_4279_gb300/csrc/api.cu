@@ -357,6 +357,7 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
 
 int qcd_solve(qcd_ctx* c, const double* b, double* x, int nrhs, const qcd_solver_params* sp_in, qcd_solve_info* info,
               void* stream) {
+  NvtxRange nv("qcd_solve");
   if (!c || !b || !x || nrhs < 1) return QCD_ERR_ARG;
   if (!c->clover_built) return QCD_ERR_STATE;
   qcd_solver_params sp;
@@ -381,6 +382,7 @@ int qcd_solve(qcd_ctx* c, const double* b, double* x, int nrhs, const qcd_solver
 
 int qcd_solve_dagger(qcd_ctx* c, const double* b, double* x, const qcd_solver_params* sp_in, qcd_solve_info* info,
                      void* stream) {
+  NvtxRange nv("qcd_solve_dagger");
   if (!c || !b || !x) return QCD_ERR_ARG;
   if (!c->clover_built) return QCD_ERR_STATE;
   qcd_solver_params sp;
@@ -407,6 +409,7 @@ int qcd_solve_dagger(qcd_ctx* c, const double* b, double* x, const qcd_solver_pa
 
 int qcd_solve_batch(qcd_ctx** ctxs, int n, const double* const* b, double* const* x, const qcd_solver_params* sp_in,
                     qcd_solve_info* info, void* stream) {
+  NvtxRange nv("qcd_solve_batch");
   if (!ctxs || !b || !x || n < 1) return QCD_ERR_ARG;
   qcd_solver_params sp;
   if (sp_in) sp = *sp_in; else qcd_solver_defaults(&sp);
@@ -446,6 +449,7 @@ int qcd_force(qcd_ctx* c, const double* x, const double* y, double* F, void* str
 
 int qcd_gradient(qcd_ctx* c, const double* phi, double* dL_dphi, double* dL_dtheta, double* x_out, double* y_out,
                  const qcd_solver_params* sp_in, void* stream) {
+  NvtxRange nv("qcd_gradient");
   if (!c || !phi) return QCD_ERR_ARG;
   if (!c->clover_built) return QCD_ERR_STATE;
   qcd_solver_params sp;

@@ -204,6 +204,7 @@ static int cg_eo_solve(Problem& p, const qcd_solver_params& sp, bool fallback) {
 }
 
 int cg_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool fallback_only) {
+  NvtxRange nv(fallback_only ? "cg_fallback" : "cg");
   if (!(sp.tol > 0)) return QCD_ERR_ARG;
   int first = QCD_OK;
   for (auto& p : probs) {

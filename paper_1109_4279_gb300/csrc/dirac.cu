@@ -271,6 +271,7 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
 }
 
 int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s) {
+  NvtxRange nv("residual64");
   if (b.prec != P64 || x.prec != P64 || r.prec != P64) return QCD_ERR_ARG;
   QCD_TRY(ensure_gauge(c, P64, s));
   QCD_TRY(ensure_clover(c, P64, s));

@@ -284,6 +284,7 @@ static int dr_solve(Problem& p, const qcd_solver_params& sp) {
 }
 
 int fgmres_dr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp) {
+  NvtxRange nv("fgmres_dr");
   if (sp.nkv < 2 || sp.nkv > 64 || sp.ndefl < 0 || sp.ndefl >= sp.nkv || !(sp.tol > 0) || sp.max_restarts < 1)
     return QCD_ERR_ARG;
   if (sp.outer_prec != P64) return QCD_ERR_UNSUPPORTED;

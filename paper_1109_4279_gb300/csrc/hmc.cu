@@ -419,6 +419,7 @@ struct Traj {
 extern "C" int qcd_hmc_trajectory(qcd_ctx* c, double* U, double* pi, const double* eta, double beta, double eps,
                                   int nsteps, double u_accept, const qcd_solver_params* sp_in, qcd_hmc_info* info,
                                   void* stream) {
+  NvtxRange nv("qcd_hmc_trajectory");
   if (!c || !U || !pi || !eta || nsteps < 1 || !(eps > 0)) return QCD_ERR_ARG;
   qcd_hmc_info local;
   if (!info) info = &local;

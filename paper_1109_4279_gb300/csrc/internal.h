@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/qcdgb.h"
 #include "qcd.cuh"
 
@@ -137,6 +139,16 @@ struct qcd_ctx {
 namespace qcd {
 
 // ---- instrumentation (api.cu)
+// NVTX range around a solver phase (header-only NVTX; a no-op unless a
+// profiler is attached): the phases appear by name in the profiler's timeline
+// and can select kernels for a capture
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct ProfScope {
   qcd_ctx* c;
   int k;

@@ -137,6 +137,7 @@ void ws_release(Workspace& w) {
 // the squared norm
 template <typename R>
 static int gram_schmidt(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, int k, cudaStream_t s) {
+  NvtxRange nv("gram_schmidt");
   const R* chi_p[64];
   for (int j = 0; j < k; ++j) chi_p[j] = (const R*)w.chi[j].data;
   R* chik = (R*)w.chi[k].data;
@@ -160,11 +161,15 @@ static int enqueue_iteration(Problem& p, const qcd_solver_params& sp, int k) {
   Workspace& w = *p.w;
   cudaStream_t s = p.s;
   if (sp.precond == QCD_PRECOND_SAP) {
+    NvtxRange nv("sap");
     QCD_TRY(sap_apply(c, w.sap, w.rho, w.phi[k], sp.ncy, sp.nmr, sp.sap_prec, s));
   } else {
     QCD_CUDA(cudaMemcpyAsync(w.phi[k].data, w.rho.data, w.rho.bytes, cudaMemcpyDeviceToDevice, s));
   }
-  QCD_TRY(dirac_apply(c, w.phi[k], w.chi[k], 0, s));
+  {
+    NvtxRange nv("outer_operator");
+    QCD_TRY(dirac_apply(c, w.phi[k], w.chi[k], 0, s));
+  }
   if (w.rprec == P32)
     QCD_TRY(gram_schmidt<float>(c, w, sp, k, s));
   else
@@ -219,6 +224,7 @@ static int sync_all(std::vector<Problem>& probs) {
 }
 
 int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool use_graphs) {
+  NvtxRange nv("fgcr");
   if (sp.nkv < 1 || sp.nkv > 64 || !(sp.tol > 0) || sp.max_restarts < 1) return QCD_ERR_ARG;
   if (sp.precond != QCD_PRECOND_NONE && sp.precond != QCD_PRECOND_SAP) return QCD_ERR_ARG;
   if (sp.outer_prec != P64 && sp.outer_prec != P32) return QCD_ERR_ARG;
