@@ -350,7 +350,10 @@ int qcd_apply_D_field(qcd_ctx* ctx, const qcd_field* in, qcd_field* out, int dag
  *   - all calls share the array; calls that overlap on the GPU race;
  *   - the first call on each device looks up the array's address; make it
  *     before any stream capture;
- *   - kernel profiling (qcd_profile_enable) must be off.
+ *   - the address is kept for the life of the process: do not call this entry
+ *     point again after cudaDeviceReset in the same process;
+ *   - kernel profiling (qcd_profile_enable) must be off (QCD_ERR_STATE
+ *     otherwise: the profiler creates CUDA events on demand).
  * in/out: device (V, 4, 3) complex128, must not alias.  The call is
  * asynchronous: out is ready when the stream reaches the call's end.  Needs
  * qcd_load_gauge and qcd_build_clover first (QCD_ERR_STATE).

@@ -18,6 +18,7 @@ STATUS = {
     0: "QCD_OK", -1: "QCD_ERR_ARG", -2: "QCD_ERR_GEOMETRY", -3: "QCD_ERR_CUDA", -4: "QCD_ERR_NOMEM",
     -5: "QCD_ERR_STATE", -6: "QCD_ERR_NOT_SU3", -7: "QCD_ERR_SINGULAR_CLOVER", -8: "QCD_NOT_CONVERGED",
     -9: "QCD_STAGNATED", -10: "QCD_NAN", -11: "QCD_ERR_UNSUPPORTED", -12: "QCD_ERR_TOO_LARGE",
+    -13: "QCD_ERR_TIMEOUT",
 }
 PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 PRECOND = {"none": 0, "sap": 1}

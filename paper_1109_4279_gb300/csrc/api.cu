@@ -550,6 +550,7 @@ int qcd_sap_apply(qcd_ctx* c, const double* eta, double* psi, int ncy, int nmr, 
 
 int qcd_debug_set(qcd_ctx* c, int what, long long value) {
   if (!c) return QCD_ERR_ARG;
+  ++c->gen;  // captured SAP launches hold the hook values
   switch (what) {
     case QCD_DEBUG_SAP_WAIT_CYCLES:
       if (value < 1 || value > (1ll << 31)) return QCD_ERR_ARG;

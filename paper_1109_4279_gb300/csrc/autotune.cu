@@ -84,6 +84,7 @@ extern "C" int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
   if (!c->clover_built) return QCD_ERR_STATE;
   const std::string key = tune_key(c, nrhs);
   int best[4] = {256, 256, 256, 256};
+  ++c->gen;  // the operator's launch shape changes under captured graphs
   if (cache_lookup(cache_path, key, best)) {
     for (int p = 0; p < 4; ++p) c->dirac_threads[p] = best[p];
     return QCD_OK;

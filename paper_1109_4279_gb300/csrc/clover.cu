@@ -195,6 +195,7 @@ __global__ void clover_build_kernel(Geom g, const double2* __restrict__ U64, dou
 
 int build_clover(qcd_ctx* c, cudaStream_t s) {
   if (!c->gauge_loaded) return QCD_ERR_STATE;
+  ++c->gen;  // every clover record is reallocated
   for (int p = 0; p < 4; ++p) {
     rec_free(c->A[p]);
     rec_free(c->Ahat[p]);
@@ -217,6 +218,7 @@ int build_clover(qcd_ctx* c, cudaStream_t s) {
 int ensure_clover(qcd_ctx* c, int prec, cudaStream_t s) {
   if (!c->clover_built) return QCD_ERR_STATE;
   if (c->A[prec].data) return QCD_OK;
+  ++c->gen;
   QCD_TRY(rec_alloc(c->A[prec], prec, 72, c->V));
   QCD_TRY(rec_alloc(c->Ahat[prec], prec, 72, c->V));
   QCD_TRY(convert_rec(c, c->A[P64], c->A[prec], s));

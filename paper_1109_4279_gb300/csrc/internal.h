@@ -67,6 +67,21 @@ struct SapWork {
   int prec = -1;
 };
 
+// What a captured FGCR iteration depends on beyond the workspace's own
+// fields: every solver parameter the iteration's launches read, and the
+// generation of the context's operator data (gauge copies, clover records,
+// launch shapes, test hooks), which changes whenever those are reallocated or
+// altered.  A captured graph is replayed only while its key is unchanged.
+struct GraphKey {
+  unsigned long long gen = ~0ull;
+  int nkv = -1, precond = -1, ncy = -1, nmr = -1, sap_prec = -1, outer_prec = -1;
+  bool operator==(const GraphKey& o) const {
+    return gen == o.gen && nkv == o.nkv && precond == o.precond && ncy == o.ncy && nmr == o.nmr &&
+           sap_prec == o.sap_prec && outer_prec == o.outer_prec;
+  }
+  bool operator!=(const GraphKey& o) const { return !(*this == o); }
+};
+
 // solver work fields of one right-hand side (FP64 internal layout unless
 // stated).  Every buffer a solve touches is allocated by ws_prepare, so the
 // iteration itself never allocates (and can be captured in a CUDA graph).
@@ -96,9 +111,10 @@ struct Workspace {
   size_t stage_bytes = 0;
   double* h_hcol = nullptr;
   double* d_hnorm = nullptr;
-  // one captured CUDA graph per FGCR iteration index, valid for graph_key
+  // one captured CUDA graph per FGCR iteration index, valid while graph_key
+  // equals the key of the current solve (parameters and context generation)
   std::vector<cudaGraphExec_t> graphs;
-  long long graph_key = -1;
+  GraphKey graph_key;
 };
 }  // namespace qcd
 
@@ -134,6 +150,11 @@ struct qcd_ctx {
   // barrier expects beyond the copies (a count that never arrives)
   long long dbg_sap_wait_cycles = 1ll << 31;
   int dbg_sap_extra_tx = 0;
+  // bumped whenever device operator data or a launch setting that captured
+  // graphs bake in changes (gauge load, clover build, lazily built copies,
+  // autotuning, test hooks): graphs captured under another generation are
+  // discarded instead of replayed
+  unsigned long long gen = 0;
 };
 
 namespace qcd {

@@ -190,6 +190,7 @@ __global__ void gauge_import_kernel(Geom g, const double* __restrict__ lex, doub
 }
 
 int load_gauge_device(qcd_ctx* c, const double* lex_dev, cudaStream_t s) {
+  ++c->gen;  // the links change (and their reduced-precision copies are freed)
   if (!c->U[P64]) {
     c->U_bytes[P64] = (size_t)c->V * GaugeLayout<P64>::bytes_per_site;
     if (cudaMalloc(&c->U[P64], c->U_bytes[P64]) != cudaSuccess) {
@@ -251,6 +252,7 @@ __global__ void gauge_compress_kernel(Geom g, const double2* __restrict__ U64, v
 int ensure_gauge(qcd_ctx* c, int prec, cudaStream_t s) {
   if (!c->gauge_loaded) return QCD_ERR_STATE;
   if (c->U[prec]) return QCD_OK;
+  ++c->gen;
   size_t bytes = (size_t)c->V * (prec == P64 ? GaugeLayout<P64>::bytes_per_site
                                              : (prec == P32 ? GaugeLayout<P32>::bytes_per_site
                                                             : GaugeLayout<P16>::bytes_per_site));

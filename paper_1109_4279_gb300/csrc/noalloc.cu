@@ -22,7 +22,12 @@
 //  * calls that overlap on the GPU (different streams, or different contexts
 //    on the same device, without ordering between them) race on the array;
 //  * the first call on each device looks up the array's device address with
-//    cudaGetSymbolAddress; make that first call before any stream capture.
+//    cudaGetSymbolAddress; make that first call before any stream capture;
+//  * the looked-up address is kept for the life of the process: after
+//    cudaDeviceReset (which destroys the context the address belongs to) this
+//    entry point must not be called again in the same process;
+//  * kernel profiling (qcd_profile_enable) records CUDA events, which are
+//    created on demand: a context with profiling on gets QCD_ERR_STATE.
 #include <mutex>
 
 #include "internal.h"
@@ -60,7 +65,7 @@ using namespace qcd;
 extern "C" int qcd_apply_D_noalloc(qcd_ctx* c, const double* in, double* out, int dagger, void* stream) {
   if (!c || !in || !out) return QCD_ERR_ARG;
   if (c->V > kMaxSites) return QCD_ERR_TOO_LARGE;
-  if (!c->clover_built || !c->U[P64] || !c->A[P64].data) return QCD_ERR_STATE;
+  if (!c->clover_built || !c->U[P64] || !c->A[P64].data || c->prof) return QCD_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   void* base = nullptr;
   QCD_TRY(scratch_address(&base));

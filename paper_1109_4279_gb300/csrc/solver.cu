@@ -44,7 +44,7 @@ static void graphs_clear(Workspace& w) {
   for (auto g : w.graphs)
     if (g) cudaGraphExecDestroy(g);
   w.graphs.clear();
-  w.graph_key = -1;
+  w.graph_key = GraphKey();
 }
 
 int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream_t s) {
@@ -182,15 +182,23 @@ static int enqueue_iteration(Problem& p, const qcd_solver_params& sp, int k) {
   return QCD_OK;
 }
 
-static long long graph_key(const qcd_solver_params& sp) {
-  return ((((long long)sp.nkv * 8 + sp.precond) * 64 + sp.ncy) * 64 + sp.nmr) * 16 + sp.sap_prec * 4 + sp.outer_prec;
+static GraphKey graph_key(const qcd_ctx* c, const qcd_solver_params& sp) {
+  GraphKey k;
+  k.gen = c->gen;
+  k.nkv = sp.nkv;
+  k.precond = sp.precond;
+  k.ncy = sp.ncy;
+  k.nmr = sp.nmr;
+  k.sap_prec = sp.sap_prec;
+  k.outer_prec = sp.outer_prec;
+  return k;
 }
 
 // enqueue iteration k, from a captured graph when requested
 static int launch_iteration(Problem& p, const qcd_solver_params& sp, int k, bool use_graphs) {
   if (!use_graphs) return enqueue_iteration(p, sp, k);
   Workspace& w = *p.w;
-  const long long key = graph_key(sp);
+  const GraphKey key = graph_key(p.c, sp);
   if (w.graph_key != key) {
     graphs_clear(w);
     w.graphs.assign(sp.nkv, nullptr);
