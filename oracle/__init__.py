@@ -35,24 +35,30 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def bind(cdll):
+    """Declare the argument and result types of the oracle's C entry points on
+    a loaded library (the built liboracle.so, or a variant a test compiled)."""
+    d, i, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_long
+    for name, args in {
+        "oracle_clover": [d, d, ctypes.c_double, ctypes.c_double, d],
+        "oracle_apply_D": [d, d, d, d, d, d, i],
+        "oracle_dD_apply": [d, d, d, d, ctypes.c_double, d, d],
+        "oracle_sap": [d, d, d, d, d, i, i, i, i, d, d, d],
+        "oracle_block_mr": [d, d, d, d, d, l, i, i, d, d],
+        "oracle_block_sites": [d, d, l, d],
+        "oracle_fgcr": [d, d, d, d, d, d, i, i, ctypes.c_double, i, d, i, i, i, i, d, d],
+        "oracle_num_threads": [],
+    }.items():
+        fn = getattr(cdll, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    return cdll
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        d, i, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_long
-        for name, args in {
-            "oracle_clover": [d, d, ctypes.c_double, ctypes.c_double, d],
-            "oracle_apply_D": [d, d, d, d, d, d, i],
-            "oracle_dD_apply": [d, d, d, d, ctypes.c_double, d, d],
-            "oracle_sap": [d, d, d, d, d, i, i, i, i, d, d, d],
-            "oracle_block_mr": [d, d, d, d, d, l, i, i, d, d],
-            "oracle_block_sites": [d, d, l, d],
-            "oracle_fgcr": [d, d, d, d, d, d, i, i, ctypes.c_double, i, d, i, i, i, i, d, d],
-            "oracle_num_threads": [],
-        }.items():
-            fn = getattr(_lib, name)
-            fn.argtypes = args
-            fn.restype = ctypes.c_int
+        _lib = bind(ctypes.CDLL(build()))
     return _lib
 
 
