@@ -76,7 +76,8 @@ def test_gradient_16x32_vs_oracle_and_fd(orc):
     """The 16^3 x 32 gradient workload: dL/dtheta along 32 random link
     directions (and one global direction) agrees with the oracle's directional
     derivative (same x, y) and with central finite differences (h = 1e-5) to
-    1e-6; dL/dphi = x + y checks the adjoint solve."""
+    1e-6 relative, |fd - g| <= 1e-6 |g| for every sampled direction;
+    dL/dphi = x + y checks the adjoint solve."""
     from paper_1109_4279_gb300 import binding
     w = synth.WORKLOADS["16^3x32 gradient"]
     dims, block, m0, csw = w["dims"], w["block"], w["m0"], w["csw"]
@@ -106,7 +107,7 @@ def test_gradient_16x32_vs_oracle_and_fd(orc):
             tf = np.zeros((V, 4, 8))
             tf[s, mu] = th
             fd = _fd_directional(dims, block, U, m0, csw, phi_t, x_t, tf, 1e-5, fd_sp)
-            assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (k, fd, g)
+            assert abs(fd - g) <= 1e-6 * abs(g), (k, fd, g)
     # one global direction over all links
     tf = np.random.default_rng(5 + 2000).standard_normal((V, 4, 8))
     g = float(np.sum(F * tf))
