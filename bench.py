@@ -61,11 +61,17 @@ def sap_src_sha():
             h.update(fh.read())
     return h.hexdigest()[:16]
 DTYPE = {(sp, op): "%s recursion (f64 residual and solution at restarts) + %s SAP arithmetic on %s SAP storage"
-                   % (op, "f64" if sp == "f64" else "f32", sp)
-         for sp in ("f64", "f32", "f16", "bf16") for op in ("f64", "f32")}
+                   % ({"df64": "df64 (double-float: FP32 pairs, error-free transforms; FP64 operator)"}.get(op, op),
+                      "f64" if sp == "f64" else "f32", sp)
+         for sp in ("f64", "f32", "f16", "bf16") for op in ("f64", "f32", "df64")}
 
 
-def peaks():
+def peaks(measure=True):
+    """Roofline denominators.  HBM: the measured copy rate
+    (MEASURED_PEAKS.json; 6.8 TB/s fallback).  FP32 / FP64: fused multiply-add
+    throughput measured on this GPU by qcd_measure_alu_peaks (the larger of
+    scalar FP32 and packed FP32x2), next to the unit-count figures (SM count
+    read from the device, 128 FP32 and 2 FP64 lanes per SM, maximum clock)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     p = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
     if os.path.exists(path):
@@ -74,9 +80,23 @@ def peaks():
         p.update({k: d[k] for k in ("hbm_gbs", "sm_max_mhz") if k in d})
         p["source"] = "measured"
     mhz = p["sm_max_mhz"]
-    # 152 SMs; 128 FP32 lanes/SM (FMA = 2 flops); 2 FP64 FMA/clk/SM on GB300
-    p["fp32_tflops"] = 152 * 128 * 2 * mhz * 1e6 / 1e12
-    p["fp64_tflops"] = 152 * 2 * 2 * mhz * 1e6 / 1e12
+    sms = 152
+    try:
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    except Exception:
+        pass
+    p["sms"] = sms
+    p["fp32_tflops_units"] = sms * 128 * 2 * mhz * 1e6 / 1e12
+    p["fp64_tflops_units"] = sms * 2 * 2 * mhz * 1e6 / 1e12
+    p["fp32_tflops"], p["fp64_tflops"], p["alu_source"] = p["fp32_tflops_units"], p["fp64_tflops_units"], "units"
+    if measure:
+        from paper_1109_4279_gb300 import binding as B
+        m = B.qcd_measure_alu_peaks()
+        p["alu_measured"] = m
+        p["fp32_tflops"] = max(m["fp32"], m["fp32x2"])
+        p["fp64_tflops"] = m["fp64"]
+        p["alu_source"] = "measured (qcd_measure_alu_peaks)"
     return p
 
 
@@ -312,8 +332,8 @@ def run_comparisons(args, lat, w, U, b_t, sp_main, main_ms):
         return lats[block]
 
     variants = [("sap_%s_outer_%s" % (sp_, op_), dict(sap_prec=sp_, outer_prec=op_))
-                for sp_, op_ in (("f16", "f64"), ("f16", "f32"), ("f32", "f32"), ("bf16", "f32"), ("f32", "f64"),
-                                 ("f64", "f64"))]
+                for sp_, op_ in (("f16", "f64"), ("f16", "df64"), ("bf16", "df64"), ("f16", "f32"), ("f32", "f32"),
+                                 ("bf16", "f32"), ("f32", "f64"), ("f64", "f64"))]
     variants.append(("fgmres_dr_16_4_sap_f16_outer_f64", dict(solver="fgmres_dr", ndefl=4, sap_prec="f16")))
     variants.append(("gcr_f64_unpreconditioned", dict(precond="none", max_restarts=400)))
     variants.append(("cgne_f64", dict(solver="cg")))
@@ -459,17 +479,22 @@ def run_configs(args, pk):
     return out
 
 
-def run_batched(args):
+def run_batched(args, block):
     """12 spin-colour point sources on 24^3 x 48 (eps 0.5, seed 4, m0 0,
-    c_sw 1.5): one multi-right-hand-side call against 12 single solves."""
+    c_sw 1.5), with the Schwarz block shape of the main solve: one
+    multi-right-hand-side call (every launch of an FGCR iteration runs over
+    all twelve; the SAP tile chosen by the autotuner) against 12 single
+    solves."""
     import numpy as np
     import torch
     from paper_1109_4279_gb300 import binding as B, synth
     wl = synth.WORKLOADS["24^3x48 12 point sources"]
     U, _ = synth.gauge_field(wl["dims"], wl["eps"], wl["seed"])
     b = torch.from_numpy(synth.point_sources(wl["dims"])).cuda()
-    lat = B.Lattice(wl["dims"], wl["block"], wl["m0"], wl["csw"])
+    lat = B.Lattice(wl["dims"], block, wl["m0"], wl["csw"])
     lat.load_gauge(torch.from_numpy(U).cuda())
+    B.qcd_autotune(lat.ctx, 12)
+    rt = B.qcd_get_sap_tile(lat.ctx, 12)
     sp = B.solver_params(tol=1e-10, nkv=wl["nkv"], ncy=wl["ncy"], nmr=wl["nmr"], sap_prec=args.sap_prec,
                          outer_prec=args.outer_prec)
     x = torch.zeros_like(b)
@@ -489,8 +514,9 @@ def run_batched(args):
         torch.cuda.synchronize()
         t_seq += time.perf_counter() - t0
     lat.close()
-    return {"workload": "24^3x48, 12 point sources, SAP %s / FGCR %s" % (args.sap_prec, args.outer_prec),
-            "batched_s": t_batch, "sequential_s": t_seq,
+    return {"workload": "24^3x48, 12 point sources, SAP %s / FGCR %s, blocks %s" % (
+                args.sap_prec, args.outer_prec, "x".join(map(str, block))),
+            "sap_rhs_tile": rt, "batched_s": t_batch, "sequential_s": t_seq, "speedup": t_seq / t_batch,
             "solves_per_s_batched": 12 / t_batch, "solves_per_s_sequential": 12 / t_seq,
             "iterations": [i["iterations"] for i in info], "max_true_residual": max(i["true_residual"] for i in info)}
 
@@ -521,6 +547,8 @@ def run_ours(args, world, rank, local):
         tuning = {"x".join(map(str, c)): t for c, t in times.items()}
     lat = B.Lattice(w["dims"], w["block"], w["m0"], w["csw"])
     lat.load_gauge(torch.from_numpy(U).cuda())
+    B.qcd_autotune(lat.ctx, 1)  # operator launch shapes, outside the timed region
+    launch = {p: B.qcd_get_launch(lat.ctx, p) for p in ("f64", "f32", "f16")}
     b_t = torch.from_numpy(b).cuda()
     x_t = torch.zeros_like(b_t)
     sp = B.solver_params(tol=1e-10, nkv=w["nkv"], ncy=w["ncy"], nmr=w["nmr"], sap_prec=args.sap_prec,
@@ -590,8 +618,9 @@ def run_ours(args, world, rank, local):
     if (dom == "sap" and args.sap_prec == "f16" and SAP_TRAFFIC["bytes_per_site"]
             and SAP_TRAFFIC["src_sha"] == sap_src_sha() and tuple(w["block"]) == SAP_TRAFFIC["block"]):
         roof["traffic"] = SAP_TRAFFIC["bytes_per_site"] * V / 2
-    roof["peak_source"] = ("FP32/FP64 peaks derived from unit counts at %.0f MHz; HBM from MEASURED_PEAKS.json"
-                           % pk["sm_max_mhz"])
+    roof["peak_source"] = ("FP32/FP64: %s on this GPU (unit counts at %.0f MHz: %.1f / %.2f TFLOP/s); "
+                           "HBM: MEASURED_PEAKS.json" % (pk["alu_source"], pk["sm_max_mhz"], pk["fp32_tflops_units"],
+                                                         pk["fp64_tflops_units"]))
 
     # D_w bandwidth per precision (resident fields)
     dw = {}
@@ -612,10 +641,16 @@ def run_ours(args, world, rank, local):
                                      "bytes_per_site_rhs": byts / V / R,
                                      "site_rhs_per_s": V * R / (ms * 1e-3)}
 
+    # the operator kernels' rooflines next to the dominant kernel's
+    roof["operators"] = {k: {"ms": v["ms"], "gbs": v["gbs"], "frac_hbm": v["frac_hbm_measured"]}
+                         for k, v in dw.items()}
+    roof["operators"]["f64"]["bound"] = "fp64 alu"
+    roof["operators"]["f64"]["frac_fp64_alu"] = dw["f64"]["gflops"] / 1e3 / pk["fp64_tflops"]
+
     # the comparison sections run at N = 1 only (they hold the GPUs for minutes)
     extra = not args.quick and world == 1
     comparisons = run_comparisons(args, lat, w, U, b_t, sp, ms_per_step) if extra else None
-    batched = run_batched(args) if extra else None
+    batched = run_batched(args, tuple(w["block"])) if extra else None
     near_critical = run_near_critical(args) if extra else None
     configs = run_configs(args, pk) if extra else None
 
@@ -657,14 +692,16 @@ def run_ours(args, world, rank, local):
                        "iterations": iters, "restarts": int(statistics.median(i["restarts"] for i in infos)),
                        "true_residual": max(i["true_residual"] for i in infos),
                        "l2": "no flush: every FP64 solver vector (192 B/site) and the gauge/clover fields exceed the 129 MB L2",
-                       "block_tuning_ms": tuning},
+                       "block_tuning_ms": tuning,
+                       "operator_launch": {p: {"threads": t, "threads_per_site": q} for p, (t, q) in launch.items()}},
             "roofline": roof, "kernels": kernels, "dw": dw, "comparisons": comparisons, "batched": batched,
             "near_critical": near_critical, "configs": configs,
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": fbytes, "d2h_bytes_per_step": fbytes},
             "gpu_launches": launches,
             "clocks": clk.summary(), "cpu_baseline": cpu,
             "peaks": {"hbm_gbs": pk["hbm_gbs"], "fp32_tflops": pk["fp32_tflops"], "fp64_tflops": pk["fp64_tflops"],
-                      "source": pk["source"]}}
+                      "source": pk["source"], "alu_source": pk["alu_source"], "alu_measured": pk.get("alu_measured"),
+                      "sms": pk["sms"]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     lat.close()
@@ -687,10 +724,11 @@ def main():
     ap.add_argument("--block", default=None, help="Schwarz block shape, e.g. 8x4x4x4 (skips the autotuner)")
     ap.add_argument("--sap-prec", choices=["f64", "f32", "f16", "bf16"], default="f16",
                     help="storage precision of the SAP block fields")
-    ap.add_argument("--outer-prec", choices=["f64", "f32"], default="f64",
-                    help="FGCR recursion precision: f64 (the benchmarked configuration: Gram-Schmidt, dots, "
-                         "chi = D phi and the update in FP64) or f32 (the paper's iterative-refinement split, "
-                         "FP64 only at restarts)")
+    ap.add_argument("--outer-prec", choices=["f64", "df64", "f32"], default="f64",
+                    help="FGCR recursion precision: f64 (Gram-Schmidt, dots, chi = D phi and the update in FP64), "
+                         "df64 (the same recursion in double-float arithmetic on the FP32 units, FP64 operator, "
+                         "solution and restart residual) or f32 (the paper's iterative-refinement split, FP64 only "
+                         "at restarts)")
     args = ap.parse_args()
     if args.impl == "reference":
         world = int(os.environ.get("WORLD_SIZE", "1"))

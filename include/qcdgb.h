@@ -66,6 +66,10 @@ extern "C" {
 #define QCD_PREC_F32 1   /* FP32 storage and arithmetic */
 #define QCD_PREC_F16 2   /* IEEE FP16 storage with a per-site FP32 scale, FP32 arithmetic */
 #define QCD_PREC_BF16 3  /* bfloat16 storage with a per-site FP32 scale, FP32 arithmetic */
+#define QCD_PREC_DF64 4  /* double-float: pairs of FP32 values (hi + lo, a 48-bit significand) computed
+                            with error-free transformations on the FP32 units; the FGCR recursion
+                            (outer_prec) and the result of qcd_apply_D (an FP64 apply, result stored
+                            as pairs) only */
 
 /* preconditioners */
 #define QCD_PRECOND_NONE 0  /* plain GCR */
@@ -102,6 +106,9 @@ typedef struct {
     int sap_prec;      /* precision of the SAP block fields: QCD_PREC_F64/F32/F16/BF16 */
     int outer_prec;    /* precision of the FGCR recursion (Sec. 4):
                           QCD_PREC_F64 (default): rho, phi_k, chi_k = D phi_k, Gram-Schmidt and dots in FP64;
+                          QCD_PREC_DF64: chi_k = D phi_k by the FP64 operator, rho, chi_k, the Gram-Schmidt
+                          dots and updates in double-float arithmetic on the FP32 units (GB300 runs FP64 at
+                          1/64 of its FP32 rate); phi_k, the solution update and the restart residual FP64;
                           QCD_PREC_F32: iterative refinement -- each restart cycle runs the whole recursion
                           in FP32 on the normalised residual r / |r| until its residual has dropped by
                           inner_tol (or the target is met), then the FP32 correction is added to the FP64
@@ -173,7 +180,9 @@ int qcd_build_clover(qcd_ctx* ctx, void* stream);
  * g5 D g5) for nrhs spinor fields (Sec. 4: the matrix-vector product).
  * in/out: device pointers to nrhs * (V, 4, 3) complex128 (must not alias).
  * prec: QCD_PREC_F64 applies in FP64; F32/F16/BF16 convert the input to that
- * storage, apply with FP32 arithmetic and convert the result back.
+ * storage, apply with FP32 arithmetic and convert the result back;
+ * QCD_PREC_DF64 applies in FP64 and passes the result through the
+ * double-float storage of the df64 recursion.
  * Errors: QCD_ERR_STATE, QCD_ERR_ARG.
  */
 int qcd_apply_D(qcd_ctx* ctx, const double* in, double* out, int dagger, int prec, int nrhs, void* stream);
@@ -274,9 +283,12 @@ int qcd_hmc_trajectory(qcd_ctx* ctx, double* U, double* pi, const double* eta, d
                        void* stream);
 
 /*
- * Pick, by timing on the device, the fastest CTA size of the operator kernel
- * for each storage precision of this context, and keep the choice in the
- * context.  nrhs: right-hand sides per call the tuning should reflect (the
+ * Pick, by timing on the device, the fastest launch shape of the operator
+ * kernel for each storage precision of this context -- CTA size, and for
+ * 16-bit storage one or two threads per site -- and, for nrhs > 1, the
+ * right-hand-side tile of the batched SAP sweep (timed on FP16 block fields);
+ * keep the choices in the context (see qcd_set_launch, qcd_set_sap_tile).
+ * nrhs: right-hand sides per call the tuning should reflect (the operator
  * timing applies that many operators back to back).  cache_path (may be
  * NULL): a JSON file read before tuning (a matching entry is applied without
  * timing) and rewritten after it, keyed by GPU name, dims, block and nrhs.
@@ -300,6 +312,24 @@ int qcd_autotune(qcd_ctx* ctx, int nrhs, const char* cache_path);
  */
 int qcd_tune_block(const qcd_params* p, const double* U, const double* b, int is_device, const qcd_solver_params* sp,
                    const int* candidates, int n, int out_block[4], double* times_ms);
+
+/*
+ * Launch shapes (what qcd_autotune chooses), for callers that pin them:
+ * qcd_set_launch sets, for storage precision prec, the operator kernel's CTA
+ * size `threads` (a multiple of 32, 32..1024) and its threads per site `tps`:
+ * 1, or 2 for 16-bit storage (QCD_PREC_F16 / BF16: two threads share a site,
+ * each taking two of the four directions and half of the spin components, in
+ * CTAs of 256; QCD_ERR_UNSUPPORTED for FP32/FP64).  qcd_get_launch reads the
+ * current shape.  qcd_set_sap_tile sets how many right-hand sides one CTA of a
+ * batched SAP sweep solves with one staging of its block's fields (1..64; 0
+ * restores the default: the largest tile that keeps four CTAs per SM);
+ * qcd_get_sap_tile returns the tile a solve of nrhs right-hand sides uses.
+ * Results do not depend on any of these.
+ */
+int qcd_set_launch(qcd_ctx* ctx, int prec, int threads, int tps);
+int qcd_get_launch(const qcd_ctx* ctx, int prec, int* threads, int* tps);
+int qcd_set_sap_tile(qcd_ctx* ctx, int rt);
+int qcd_get_sap_tile(qcd_ctx* ctx, int nrhs);
 
 /* Static description of a status code. */
 const char* qcd_status_string(int status);
@@ -368,6 +398,18 @@ int qcd_apply_D_noalloc(qcd_ctx* ctx, const double* in, double* out, int dagger,
 int qcd_sap_apply(qcd_ctx* ctx, const double* eta, double* psi, int ncy, int nmr, int sap_prec, void* stream);
 
 /*
+ * The same for nrhs right-hand sides at once (Sec. 4 applies the
+ * preconditioner to one residue at a time; applying it to several shares the
+ * staging of each Schwarz block's links and clover): each CTA of a colour
+ * sweep solves one block for rt right-hand sides in turn (rt = 0: the
+ * library's default tile).  eta, psi: device nrhs * (V, 4, 3) complex128,
+ * lexicographic.  psi_q = M_SAP eta_q for every q, identical to nrhs calls of
+ * qcd_sap_apply.  Allocates and frees its work fields on every call.
+ */
+int qcd_sap_apply_n(qcd_ctx* ctx, const double* eta, double* psi, int nrhs, int rt, int ncy, int nmr, int sap_prec,
+                    void* stream);
+
+/*
  * Test hooks for failure detection without a GPU fault.  The SAP kernel waits
  * for its staging copies with a bounded spin (about a second); when the
  * budget runs out the kernel records it, lets the copies in flight land and
@@ -411,6 +453,17 @@ int qcd_convert_check(const double* in64, const float* in32, float* out32, doubl
 #define QCD_KERNEL_RESIDUAL 3   /* fused true residual r = b - D x */
 #define QCD_KERNEL_COUNT 4
 int qcd_profile_enable(qcd_ctx* ctx, int on);
+/*
+ * Measured arithmetic peaks of the current GPU (the denominators of the ALU
+ * rooflines): throughput of fused multiply-adds with eight independent
+ * register chains per thread on eight CTAs per SM, in TFLOP/s (2 flops per
+ * multiply-add and lane): scalar FP32, packed FP32x2 (the form the operator
+ * and block-solver kernels use for SU(3) products) and FP64.  Any output may
+ * be NULL (that form is not timed).  Takes some tens of milliseconds;
+ * synchronous.
+ */
+int qcd_measure_alu_peaks(double* fp32_tflops, double* fp32x2_tflops, double* fp64_tflops, void* stream);
+
 /* Number of kernels this library has launched since it was loaded (all contexts). */
 long long qcd_launch_count(void);
 int qcd_profile_reset(qcd_ctx* ctx);

@@ -20,7 +20,7 @@ STATUS = {
     -9: "QCD_STAGNATED", -10: "QCD_NAN", -11: "QCD_ERR_UNSUPPORTED", -12: "QCD_ERR_TOO_LARGE",
     -13: "QCD_ERR_TIMEOUT",
 }
-PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "df64": 4}
 PRECOND = {"none": 0, "sap": 1}
 SOLVER = {"fgcr": 0, "fgmres_dr": 1, "cg": 2, "cg_eo": 3}
 KERNEL = {"dirac": 0, "sap": 1, "blas": 2, "residual": 3}
@@ -94,6 +94,12 @@ def lib():
             "qcd_apply_D_field": (I, [P, P, P, I, P]),
             "qcd_apply_D_noalloc": (I, [P, P, P, I, P]),
             "qcd_sap_apply": (I, [P, P, P, I, I, I, P]),
+            "qcd_sap_apply_n": (I, [P, P, P, I, I, I, I, I, P]),
+            "qcd_set_launch": (I, [P, I, I, I]),
+            "qcd_measure_alu_peaks": (I, [ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), P]),
+            "qcd_get_launch": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+            "qcd_set_sap_tile": (I, [P, I]),
+            "qcd_get_sap_tile": (I, [P, I]),
             "qcd_convert_check": (I, [P, P, P, P, ctypes.c_longlong, P]),
             "qcd_debug_set": (I, [P, I, ctypes.c_longlong]),
             "qcd_profile_enable": (I, [P, I]),
@@ -320,6 +326,42 @@ def qcd_apply_D_noalloc(ctx, inp, out, dagger=False):
 def qcd_sap_apply(ctx, eta, psi, ncy, nmr, prec="f32"):
     return check(lib().qcd_sap_apply(ctx, _ptr(eta), _ptr(psi), int(ncy), int(nmr), PREC[prec], _stream()),
                  "qcd_sap_apply")
+
+
+def qcd_sap_apply_n(ctx, eta, psi, nrhs, rt, ncy, nmr, prec="f32"):
+    """M_SAP on nrhs fields at once, rt right-hand sides per CTA (0: default)."""
+    return check(lib().qcd_sap_apply_n(ctx, _ptr(eta), _ptr(psi), int(nrhs), int(rt), int(ncy), int(nmr), PREC[prec],
+                                       _stream()), "qcd_sap_apply_n")
+
+
+def qcd_set_launch(ctx, prec, threads, tps=1):
+    """Pin the operator kernel's CTA size and threads per site for one precision."""
+    return check(lib().qcd_set_launch(ctx, PREC[prec], int(threads), int(tps)), "qcd_set_launch")
+
+
+def qcd_get_launch(ctx, prec):
+    t, p = ctypes.c_int(), ctypes.c_int()
+    check(lib().qcd_get_launch(ctx, PREC[prec], ctypes.byref(t), ctypes.byref(p)), "qcd_get_launch")
+    return t.value, p.value
+
+
+def qcd_measure_alu_peaks():
+    """Measured FMA throughput of this GPU: {"fp32", "fp32x2", "fp64"} in TFLOP/s."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(lib().qcd_measure_alu_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream()),
+          "qcd_measure_alu_peaks")
+    return {"fp32": a.value, "fp32x2": b.value, "fp64": c.value}
+
+
+def qcd_set_sap_tile(ctx, rt):
+    return check(lib().qcd_set_sap_tile(ctx, int(rt)), "qcd_set_sap_tile")
+
+
+def qcd_get_sap_tile(ctx, nrhs):
+    rt = lib().qcd_get_sap_tile(ctx, int(nrhs))
+    if rt < 0:
+        raise QcdError(rt, "qcd_get_sap_tile")
+    return rt
 
 
 DEBUG = {"sap_wait_cycles": 0, "sap_extra_tx": 1}

@@ -208,11 +208,11 @@ int qcd_build_clover(qcd_ctx* c, void* stream) {
 }
 
 int qcd_apply_D(qcd_ctx* c, const double* in, double* out, int dagger, int prec, int nrhs, void* stream) {
-  if (!c || !in || !out || nrhs < 1 || prec < 0 || prec > 3) return QCD_ERR_ARG;
+  if (!c || !in || !out || nrhs < 1 || prec < 0 || prec > 4) return QCD_ERR_ARG;
   if (!c->clover_built) return QCD_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   Rec a, b;
-  int st = rec_alloc(a, prec, 24, c->V * nrhs);
+  int st = rec_alloc(a, prec == PDF ? P64 : prec, 24, c->V * nrhs);
   if (st == QCD_OK) st = rec_alloc(b, prec, 24, c->V * nrhs);
   if (st == QCD_OK) st = import_spinor(c, in, a, nrhs, s);
   if (st == QCD_OK) st = dirac_apply(c, a, b, dagger, s, nrhs);
@@ -255,8 +255,9 @@ static int fork_streams(cudaStream_t s, std::vector<Problem>& probs) {
 }
 
 static int join_streams(cudaStream_t s, std::vector<Problem>& probs) {
-  for (auto& p : probs) {
-    if (p.s == s) continue;
+  for (size_t i = 0; i < probs.size(); ++i) {
+    Problem& p = probs[i];
+    if (p.s == s || (i > 0 && probs[i - 1].s == p.s)) continue;  // each stream once
     cudaEvent_t e;
     QCD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     cudaEventRecord(e, p.s);
@@ -326,7 +327,9 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
     fork_streams(s, probs);
     bool prof = false;
     for (auto& p : probs) prof |= p.c->prof;
-    st = run_solver(probs, sp, n > 1 && !prof);
+    // captured iteration graphs are replayed unless kernels are being timed
+    // one by one (the profiler's events would be baked into the graphs)
+    st = run_solver(probs, sp, !prof);
     join_streams(s, probs);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
@@ -355,6 +358,110 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
   return st;
 }
 
+// nrhs > 1 right-hand sides of one lattice by FGCR, all iterated by the same
+// launches: one workspace holds their fields back to back
+static int solve_tile(qcd_ctx* c, const double* b, double* x, int nrhs, bool dev, const qcd_solver_params& sp,
+                      qcd_solve_info* info, cudaStream_t s) {
+  if (!c->tile_ws) c->tile_ws = new (std::nothrow) Workspace();
+  Workspace* w = c->tile_ws;
+  if (!w) return QCD_ERR_NOMEM;
+  if (sp.nkv < 1 || sp.nkv > 64) return QCD_ERR_ARG;
+  QCD_TRY(ws_prepare(c, *w, sp, s, nrhs));
+  const size_t fbytes = (size_t)c->V * 24 * sizeof(double) * nrhs;
+  const double* bd = b;
+  double* xd = x;
+  if (!dev) {  // lexicographic staging of b and x, kept by the workspace across calls
+    if (w->stage_bytes < 2 * fbytes) {
+      if (w->stage) cudaFree(w->stage);
+      w->stage = nullptr;
+      w->stage_bytes = 0;
+      if (cudaMalloc(&w->stage, 2 * fbytes) != cudaSuccess) {
+        cudaGetLastError();
+        w->stage = nullptr;
+        return QCD_ERR_NOMEM;
+      }
+      w->stage_bytes = 2 * fbytes;
+    }
+    QCD_CUDA(cudaMemcpyAsync(w->stage, b, fbytes, cudaMemcpyHostToDevice, s));
+    if (!sp.zero_guess)
+      QCD_CUDA(cudaMemcpyAsync(w->stage + c->V * 24 * nrhs, x, fbytes, cudaMemcpyHostToDevice, s));
+    bd = w->stage;
+    xd = w->stage + c->V * 24 * nrhs;
+  }
+  QCD_TRY(import_spinor(c, bd, w->b, nrhs, s));
+  if (sp.zero_guess)
+    QCD_CUDA(cudaMemsetAsync(w->x.data, 0, w->x.bytes, s));
+  else
+    QCD_TRY(import_spinor(c, xd, w->x, nrhs, s));
+  // the iterations run on the context's own stream, ordered after and before
+  // the caller's: a stream the library owns can always be captured into graphs
+  // (the legacy default stream cannot)
+  QCD_TRY(ctx_streams(c, 1));
+  const cudaStream_t ws = c->streams[0];
+  std::vector<Problem> probs(nrhs);
+  Group G;
+  G.c = c;
+  G.w = w;
+  G.s = ws;
+  G.rt = sap_tile(c, nrhs);
+  for (int q = 0; q < nrhs; ++q) {
+    probs[q].c = c;
+    probs[q].w = w;
+    probs[q].s = ws;
+    probs[q].b = rhs_view(w->b, q, c->V);
+    probs[q].x = rhs_view(w->x, q, c->V);
+    G.rhs.push_back(&probs[q]);
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  std::vector<Group> groups(1, G);
+  int st = QCD_OK;
+  if (sp.solver != QCD_SOLVER_FGCR || sp.cg_fallback < 0 || sp.cg_fallback > 2) st = QCD_ERR_ARG;
+  if (st == QCD_OK) st = fork_streams(s, probs);
+  if (st == QCD_OK) st = fgcr_groups(groups, sp, !c->prof);
+  join_streams(s, probs);
+  if (st != QCD_OK && sp.cg_fallback) {
+    // CG from the iterate of every right-hand side that stagnated or ran out of
+    // restarts, one after another in the single-right-hand-side workspace
+    std::vector<Problem> fb;
+    Workspace* w1 = ensure_ws(c);
+    for (int q = 0; q < nrhs; ++q)
+      if (probs[q].status == QCD_STAGNATED || probs[q].status == QCD_NOT_CONVERGED) {
+        fb.push_back(probs[q]);
+        fb.back().w = w1;
+      }
+    if (w1 && !fb.empty()) {
+      cg_batch(fb, sp, true);
+      size_t i = 0;
+      for (int q = 0; q < nrhs; ++q)
+        if (probs[q].status == QCD_STAGNATED || probs[q].status == QCD_NOT_CONVERGED) probs[q] = fb[i++];
+    }
+    st = QCD_OK;
+    for (auto& p : probs)
+      if (p.status != QCD_OK && st == QCD_OK) st = p.status;
+  }
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int e2 = export_spinor(c, w->x, xd, nrhs, s);
+  if (e2 == QCD_OK && !dev) {
+    const cudaError_t e = cudaMemcpyAsync(x, xd, fbytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) e2 = cuda_fail(e, "solve download");
+  }
+  cudaStreamSynchronize(s);
+  for (int q = 0; q < nrhs; ++q) {
+    probs[q].info.time_ms = ms;
+    if (e2 != QCD_OK && probs[q].status == QCD_OK) probs[q].status = probs[q].info.status = e2;
+    if (info) info[q] = probs[q].info;
+  }
+  return st != QCD_OK ? st : e2;
+}
+
 int qcd_solve(qcd_ctx* c, const double* b, double* x, int nrhs, const qcd_solver_params* sp_in, qcd_solve_info* info,
               void* stream) {
   NvtxRange nv("qcd_solve");
@@ -365,7 +472,8 @@ int qcd_solve(qcd_ctx* c, const double* b, double* x, int nrhs, const qcd_solver
   cudaStream_t s = (cudaStream_t)stream;
   const bool dev = is_device_ptr(b);
   if (dev != is_device_ptr(x)) return QCD_ERR_ARG;
-  if (nrhs > 1) QCD_TRY(ctx_streams(c, nrhs));
+  if (nrhs > 1 && sp.solver == QCD_SOLVER_FGCR) return solve_tile(c, b, x, nrhs, dev, sp, info, s);
+  QCD_TRY(ctx_streams(c, nrhs));
   std::vector<Problem> probs(nrhs);
   std::vector<const double*> bs(nrhs);
   std::vector<double*> xs(nrhs);
@@ -373,7 +481,7 @@ int qcd_solve(qcd_ctx* c, const double* b, double* x, int nrhs, const qcd_solver
     probs[k].c = c;
     probs[k].w = rhs_workspace(c, k);
     if (!probs[k].w) return QCD_ERR_NOMEM;
-    probs[k].s = nrhs > 1 ? c->streams[k] : s;
+    probs[k].s = c->streams[k];  // a context stream (capturable), forked from and joined to s
     bs[k] = b + (size_t)k * c->V * 24;
     xs[k] = x + (size_t)k * c->V * 24;
   }
@@ -426,7 +534,7 @@ int qcd_solve_batch(qcd_ctx** ctxs, int n, const double* const* b, double* const
     probs[i].c = c;
     probs[i].w = ensure_ws(c);
     if (!probs[i].w) return QCD_ERR_NOMEM;
-    probs[i].s = n > 1 ? c->streams[0] : s;
+    probs[i].s = c->streams[0];  // a context stream (capturable), forked from and joined to s
   }
   return solve_problems(probs, b, x, true, sp, info, s);
 }
@@ -546,6 +654,66 @@ int qcd_sap_apply(qcd_ctx* c, const double* eta, double* psi, int ncy, int nmr, 
   QCD_CUDA(cudaMemcpyAsync(&timed_out, c->d_scalars + 128, sizeof(int), cudaMemcpyDeviceToHost, s));
   QCD_CUDA(cudaStreamSynchronize(s));
   return timed_out ? QCD_ERR_TIMEOUT : QCD_OK;
+}
+
+int qcd_sap_apply_n(qcd_ctx* c, const double* eta, double* psi, int nrhs, int rt, int ncy, int nmr, int sap_prec,
+                    void* stream) {
+  if (!c || !eta || !psi || nrhs < 1 || rt < 0 || ncy < 1 || nmr < 0 || sap_prec < 0 || sap_prec > 3)
+    return QCD_ERR_ARG;
+  if (!c->clover_built) return QCD_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  Rec a, b;
+  SapWork w;
+  int st = rec_alloc(a, P64, 24, c->V * nrhs);
+  if (st == QCD_OK) st = rec_alloc(b, P64, 24, c->V * nrhs);
+  if (st == QCD_OK) st = import_spinor(c, eta, a, nrhs, s);
+  if (st == QCD_OK && cudaMemsetAsync(c->d_scalars + 128, 0, sizeof(double), s) != cudaSuccess) st = QCD_ERR_CUDA;
+  Batch B;
+  B.n = nrhs;
+  if (st == QCD_OK) st = sap_apply(c, w, a, b, ncy, nmr, sap_prec, s, B, rt > nrhs ? nrhs : rt);
+  if (st == QCD_OK) st = export_spinor(c, b, psi, nrhs, s);
+  int timed_out = 0;
+  if (st == QCD_OK && cudaMemcpyAsync(&timed_out, c->d_scalars + 128, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                          cudaSuccess)
+    st = QCD_ERR_CUDA;
+  cudaStreamSynchronize(s);
+  rec_free(a);
+  rec_free(b);
+  rec_free(w.rho);
+  rec_free(w.psi);
+  if (w.faces) cudaFree(w.faces);
+  if (st == QCD_OK && timed_out) st = QCD_ERR_TIMEOUT;
+  return st;
+}
+
+int qcd_set_launch(qcd_ctx* c, int prec, int threads, int tps) {
+  if (!c || prec < 0 || prec > 3) return QCD_ERR_ARG;
+  if (tps != 1 && tps != 2) return QCD_ERR_ARG;
+  if (tps == 2 && prec != QCD_PREC_F16 && prec != QCD_PREC_BF16) return QCD_ERR_UNSUPPORTED;
+  if (threads < 32 || threads > 1024 || threads % 32) return QCD_ERR_ARG;
+  ++c->gen;  // captured graphs hold the launch shape
+  c->dirac_threads[prec] = threads;
+  c->dirac_tps[prec] = tps;
+  return QCD_OK;
+}
+
+int qcd_get_launch(const qcd_ctx* c, int prec, int* threads, int* tps) {
+  if (!c || prec < 0 || prec > 3) return QCD_ERR_ARG;
+  if (threads) *threads = c->dirac_tps[prec] == 2 ? 256 : c->dirac_threads[prec];
+  if (tps) *tps = c->dirac_tps[prec];
+  return QCD_OK;
+}
+
+int qcd_set_sap_tile(qcd_ctx* c, int rt) {
+  if (!c || rt < 0 || rt > 64) return QCD_ERR_ARG;
+  ++c->gen;
+  c->sap_rt = rt;
+  return QCD_OK;
+}
+
+int qcd_get_sap_tile(qcd_ctx* c, int nrhs) {
+  if (!c || nrhs < 1) return QCD_ERR_ARG;
+  return sap_tile(c, nrhs);
 }
 
 int qcd_debug_set(qcd_ctx* c, int what, long long value) {

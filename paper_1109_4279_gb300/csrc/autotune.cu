@@ -1,7 +1,10 @@
 // Launch-shape and block-shape tuning by measurement.
 //
-// qcd_autotune: CTA size of the operator kernel per storage precision, timed
-// with CUDA events on resident fields, cached in a small JSON file.
+// qcd_autotune: the operator kernel's CTA size per storage precision and, for
+// 16-bit storage, one or two threads per site; for several right-hand sides
+// the number of them one CTA of the SAP sweep solves per staging of its
+// block.  Timed with CUDA events on resident fields, cached in a small JSON
+// file.
 // qcd_tune_block: the Schwarz block shape (Sec. 4/5), chosen by timing whole
 // solves, since the shape changes both the kernel speed and the iteration
 // count.
@@ -31,8 +34,19 @@ static std::string tune_key(qcd_ctx* c, int nrhs) {
   return k.str();
 }
 
-// The cache holds one entry per line:  "key": [t64, t32, t16, tb16],
-static bool cache_lookup(const char* path, const std::string& key, int out[4]) {
+// The cache holds one entry per line:
+//   "key": [t64, t32, t16, tb16, tps16, tpsb16, sap_rt],
+// the operator's CTA size per precision, the threads per site of the 16-bit
+// operators, and the SAP right-hand-side tile (0: default)
+static constexpr int kTuneFields = 7;
+
+static bool tune_valid(const int v[kTuneFields]) {
+  for (int i = 0; i < 4; ++i)
+    if (v[i] != 128 && v[i] != 256 && v[i] != 512) return false;
+  return (v[4] == 1 || v[4] == 2) && (v[5] == 1 || v[5] == 2) && v[6] >= 0 && v[6] <= 64;
+}
+
+static bool cache_lookup(const char* path, const std::string& key, int out[kTuneFields]) {
   if (!path) return false;
   std::ifstream f(path);
   std::string line;
@@ -42,18 +56,18 @@ static bool cache_lookup(const char* path, const std::string& key, int out[4]) {
     if (p == std::string::npos) continue;
     const size_t lb = line.find('[', p), rb = line.find(']', p);
     if (lb == std::string::npos || rb == std::string::npos) return false;
-    int v[4];
-    if (sscanf(line.c_str() + lb + 1, "%d , %d , %d , %d", &v[0], &v[1], &v[2], &v[3]) != 4) return false;
-    for (int i = 0; i < 4; ++i) {
-      if (v[i] != 128 && v[i] != 256 && v[i] != 512) return false;
-      out[i] = v[i];
-    }
+    int v[kTuneFields];
+    if (sscanf(line.c_str() + lb + 1, "%d , %d , %d , %d , %d , %d , %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
+               &v[6]) != kTuneFields)
+      return false;
+    if (!tune_valid(v)) return false;
+    for (int i = 0; i < kTuneFields; ++i) out[i] = v[i];
     return true;
   }
   return false;
 }
 
-static void cache_store(const char* path, const std::string& key, const int v[4]) {
+static void cache_store(const char* path, const std::string& key, const int v[kTuneFields]) {
   if (!path) return;
   std::vector<std::string> entries;
   {
@@ -67,12 +81,39 @@ static void cache_store(const char* path, const std::string& key, const int v[4]
     }
   }
   std::ostringstream e;
-  e << "  \"" << key << "\": [" << v[0] << ", " << v[1] << ", " << v[2] << ", " << v[3] << "]";
+  e << "  \"" << key << "\": [";
+  for (int i = 0; i < kTuneFields; ++i) e << v[i] << (i + 1 < kTuneFields ? ", " : "]");
   entries.push_back(e.str());
   std::ofstream f(path, std::ios::trunc);
   f << "{\n";
   for (size_t i = 0; i < entries.size(); ++i) f << entries[i] << (i + 1 < entries.size() ? ",\n" : "\n");
   f << "}\n";
+}
+
+static void tune_apply(qcd_ctx* c, const int v[kTuneFields]) {
+  for (int p = 0; p < 4; ++p) c->dirac_threads[p] = v[p];
+  c->dirac_tps[P64] = c->dirac_tps[P32] = 1;
+  c->dirac_tps[P16] = v[4];
+  c->dirac_tps[PB16] = v[5];
+  c->sap_rt = v[6];
+}
+
+// mean ms of reps calls of f() after one warm-up, CUDA events on s
+template <typename F>
+static float time_ms(cudaStream_t s, int reps, F f, int* st) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  *st = f();
+  cudaEventRecord(e0, s);
+  for (int it = 0; it < reps && *st == QCD_OK; ++it) *st = f();
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / reps;
 }
 
 }  // namespace qcd
@@ -83,48 +124,74 @@ extern "C" int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
   if (!c || nrhs < 1) return QCD_ERR_ARG;
   if (!c->clover_built) return QCD_ERR_STATE;
   const std::string key = tune_key(c, nrhs);
-  int best[4] = {256, 256, 256, 256};
+  int best[kTuneFields] = {256, 256, 256, 256, 1, 1, 0};
   ++c->gen;  // the operator's launch shape changes under captured graphs
   if (cache_lookup(cache_path, key, best)) {
-    for (int p = 0; p < 4; ++p) c->dirac_threads[p] = best[p];
+    tune_apply(c, best);
     return QCD_OK;
   }
   cudaStream_t s = nullptr;
   QCD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
   const bool prof = c->prof;
   c->prof = false;
   int st = QCD_OK;
-  const int cand[3] = {128, 256, 512};
+  // operator: CTA size with one thread per site, and for 16-bit storage the
+  // two-threads-per-site form
+  const int cand[4][2] = {{128, 1}, {256, 1}, {512, 1}, {256, 2}};
   for (int p = P64; p <= PB16 && st == QCD_OK; ++p) {
     Rec a, b;
     st = rec_alloc(a, p, 24, c->V * nrhs);
     if (st == QCD_OK) st = rec_alloc(b, p, 24, c->V * nrhs);
     if (st == QCD_OK && cudaMemsetAsync(a.data, 0, a.bytes, s) != cudaSuccess) st = QCD_ERR_CUDA;
     float best_ms = 1e30f;
-    for (int k = 0; k < 3 && st == QCD_OK; ++k) {
-      c->dirac_threads[p] = cand[k];
-      st = dirac_apply(c, a, b, 0, s, nrhs);  // warm-up (also builds this precision's fields)
-      cudaEventRecord(e0, s);
-      for (int it = 0; it < 5 && st == QCD_OK; ++it) st = dirac_apply(c, a, b, 0, s, nrhs);
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
+    const int ncand = (p == P16 || p == PB16) ? 4 : 3;
+    for (int k = 0; k < ncand && st == QCD_OK; ++k) {
+      c->dirac_threads[p] = cand[k][0];
+      c->dirac_tps[p] = cand[k][1];
+      const float ms = time_ms(s, 5, [&] { return dirac_apply(c, a, b, 0, s, nrhs); }, &st);
+      if (st == QCD_OK && ms < best_ms) {
         best_ms = ms;
-        best[p] = cand[k];
+        best[p] = cand[k][0];
+        if (p >= P16) best[4 + (p - P16)] = cand[k][1];
       }
     }
     c->dirac_threads[p] = best[p];
+    c->dirac_tps[p] = p >= P16 ? best[4 + (p - P16)] : 1;
     rec_free(a);
     rec_free(b);
   }
+  // SAP right-hand-side tile: FP16 block fields, 4 cycles of 4 MR steps
+  if (st == QCD_OK && nrhs > 1) {
+    SapWork w;
+    Rec eta, psi;
+    int s2 = sap_prepare(c, w, P16, s, nrhs);
+    if (s2 == QCD_OK) s2 = rec_alloc(eta, P64, 24, c->V * nrhs);
+    if (s2 == QCD_OK) s2 = rec_alloc(psi, P64, 24, c->V * nrhs);
+    if (s2 == QCD_OK && cudaMemsetAsync(eta.data, 0, eta.bytes, s) != cudaSuccess) s2 = QCD_ERR_CUDA;
+    if (s2 == QCD_OK) {
+      Batch B;
+      B.n = nrhs;
+      float best_ms = 1e30f;
+      const int rts[8] = {1, 2, 3, 4, 6, 8, 12, 16};
+      for (int k = 0; k < 8 && rts[k] <= nrhs && s2 == QCD_OK; ++k) {
+        const float ms = time_ms(s, 2, [&] { return sap_apply(c, w, eta, psi, 4, 4, P16, s, B, rts[k]); }, &s2);
+        if (s2 == QCD_OK && ms < best_ms) {
+          best_ms = ms;
+          best[6] = rts[k];
+        }
+      }
+    }
+    // a SAP that does not fit this block shape leaves the default tile
+    cudaStreamSynchronize(s);
+    rec_free(eta);
+    rec_free(psi);
+    rec_free(w.rho);
+    rec_free(w.psi);
+    if (w.faces) cudaFree(w.faces);
+    cudaGetLastError();
+  }
+  c->sap_rt = best[6];
   c->prof = prof;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   cudaStreamSynchronize(s);
   cudaStreamDestroy(s);
   if (st == QCD_OK) cache_store(cache_path, key, best);

@@ -35,6 +35,7 @@ static int cg_prepare(qcd_ctx* c, Workspace& w, size_t nvec = 4) {
       w.d_part = nullptr;
       return QCD_ERR_NOMEM;
     }
+    w.ps = (long long)partials_for(c->V);
   }
   if (!w.d_cg) QCD_CUDA(cudaMalloc(&w.d_cg, sizeof(double) * 8));
   if (!w.h_cg) QCD_CUDA(cudaMallocHost(&w.h_cg, sizeof(double) * 8));

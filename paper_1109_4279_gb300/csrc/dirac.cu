@@ -159,7 +159,8 @@ __device__ __forceinline__ void fix_block_shape(Geom& g) {
 // compiler's default
 template <int P, int DAG, int BS>
 __global__ void __launch_bounds__(512, P == P32 ? 1 : 0) dirac_kernel(Geom g0, const void* __restrict__ U, FieldPtr A, FieldPtr in,
-                                                    FieldPtr out, int nrhs) {
+                                                    FieldPtr out, int nrhs, const int* __restrict__ mask,
+                                                    int out_df) {
   typedef typename Arith<P>::T T;
   Geom g = g0;
   fix_block_shape<BS>(g);
@@ -169,13 +170,179 @@ __global__ void __launch_bounds__(512, P == P32 ? 1 : 0) dirac_kernel(Geom g0, c
   constexpr int NC = P == P64 ? 12 : (P == P32 ? 6 : 3);
 #pragma unroll 1
   for (int k = 0; k < nrhs; ++k) {
+    if (mask && !mask[k]) continue;  // a right-hand side of a batch that is not being iterated
     FieldPtr fi = in, fo = out;
     fi.data = (char*)in.data + (size_t)k * g.V * NC * 16;
     fo.data = (char*)out.data + (size_t)k * g.V * NC * 16;
     if (in.norm) fi.norm = in.norm + (size_t)k * g.V;
     if (out.norm) fo.norm = out.norm + (size_t)k * g.V;
     Spinor<T> o = dirac_site<P, DAG, T>(g, U, A, fi, blk, r);
+    if constexpr (P == P64) {
+      if (out_df) {  // the FP64 result split into double-float pairs for a df64 recursion
+        store_spinor<PDF, T>(fo, g.Vb, blk, r, o);
+        continue;
+      }
+    }
     store_spinor<P, T>(fo, g.Vb, blk, r, o);
+  }
+}
+
+// ------------------------------------------------------------------------
+// Two threads per site (16-bit storage).  The one-thread form above needs all
+// 128 registers for a site's eight hops, which leaves 16 warps per SM to hide
+// the gathers.  Here thread half hf of a CTA (warp-uniform: threads
+// hf * 128 .. hf * 128 + 127) computes the hops in directions 2 hf and
+// 2 hf + 1 of 128 sites and owns spin components 2 hf, 2 hf + 1 of their
+// results: the partial hop sums of the other two components go to the partner
+// through shared memory (a named barrier of the two warps that hold the same
+// 32 sites), the clover term acts on the owned chiral half alone (it is block
+// diagonal in chirality), and the per-site 16-bit scale of the result is the
+// larger of the two halves' maxima.
+// ------------------------------------------------------------------------
+static constexpr int kPairSites = 128;  // sites per CTA of the two-thread form (256 threads)
+// resident CTAs per SM the two-thread form is compiled for (its register budget)
+#ifndef QCD_PAIR_MIN_CTAS
+#define QCD_PAIR_MIN_CTAS 2
+#endif
+
+// owned half (spins 2 hf, 2 hf + 1) of a 16-bit spinor record without its scale
+// (16-bit words 6 hf .. 6 hf + 5: chunk 2 hf and the hf-th 8-byte half of chunk 1)
+template <int P>
+__device__ __forceinline__ Half<float> load_half16_unscaled(const FieldPtr& f, int Vb, int blk, int r, int hf) {
+  const uint4* d = (const uint4*)f.data + (long long)blk * 3 * Vb + r;
+  const uint4 a = __ldg(d + (long long)(2 * hf) * Vb);
+  const uint2 b = __ldg((const uint2*)(d + Vb) + hf);
+  const uint32_t w[6] = {hf ? b.x : a.x, hf ? b.y : a.y, hf ? a.x : a.z, hf ? a.y : a.w, hf ? a.z : b.x, hf ? a.w : b.y};
+  Half<float> h;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float2 x = to_f2<P>(w[k]);
+    h.c[k / 3][k % 3] = {x.x, x.y};
+  }
+  return h;
+}
+
+// store the owned half with the site's scale (the maximum over both halves)
+template <int P>
+__device__ __forceinline__ void store_half16(const FieldPtr& f, int Vb, int blk, int r, int hf, const Half<float>& h,
+                                             float scale) {
+  typedef typename Storage<P>::real hr;
+  const float inv = scale > 0.f ? 1.0f / scale : 0.f;
+  uint32_t w[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    hr* q = reinterpret_cast<hr*>(&w[k]);
+    q[0] = from_f<P>(h.c[k / 3][k % 3].re * inv);
+    q[1] = from_f<P>(h.c[k / 3][k % 3].im * inv);
+  }
+  uint4* d = (uint4*)f.data + (long long)blk * 3 * Vb + r;
+  if (hf == 0) {
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    *((uint2*)(d + Vb)) = make_uint2(w[4], w[5]);
+    f.norm[(long long)blk * Vb + r] = scale;
+  } else {
+    *((uint2*)(d + Vb) + 1) = make_uint2(w[0], w[1]);
+    d[2 * (long long)Vb] = make_uint4(w[2], w[3], w[4], w[5]);
+  }
+}
+
+template <int P, int DAG, int BS>
+__global__ void __launch_bounds__(2 * kPairSites, QCD_PAIR_MIN_CTAS) dirac_pair_kernel(Geom g0, const void* __restrict__ U, FieldPtr A,
+                                                                  FieldPtr in, FieldPtr out, int nrhs,
+                                                                  const int* __restrict__ mask) {
+  static_assert(P == P16 || P == PB16, "16-bit storage only");
+  __shared__ float xch[2][12][kPairSites];  // [receiving half][real][site]
+  __shared__ float mx[2][kPairSites];
+  Geom g = g0;
+  fix_block_shape<BS>(g);
+  const int hf = threadIdx.x / kPairSites, li = threadIdx.x - hf * kPairSites;
+  const long long s = (long long)blockIdx.x * kPairSites + li;
+  const bool act = s < g.V;
+  const long long sc = act ? s : 0;
+  const int blk = (int)(sc / g.Vb), r = (int)(sc - (long long)blk * g.Vb);
+  int n[4], y[4];
+  block_coords(g, blk, n);
+  {
+    const int packed = __ldg(g.r2y + r);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) y[mu] = ycoord(packed, mu);
+  }
+  const int pair_bar = 1 + (li >> 5);  // named barrier of warps li / 32 and li / 32 + 4
+#pragma unroll 1
+  for (int k = 0; k < nrhs; ++k) {
+    if (mask && !mask[k]) continue;
+    FieldPtr fi = in, fo = out;
+    fi.data = (char*)in.data + (size_t)k * g.V * 3 * 16;
+    fo.data = (char*)out.data + (size_t)k * g.V * 3 * 16;
+    fi.norm = in.norm + (size_t)k * g.V;
+    fo.norm = out.norm + (size_t)k * g.V;
+    Spinor<float> acc;
+    zero(acc);
+    if (hf) {
+      hop_pair<2, P, DAG, float>(g, U, fi, blk, r, y, n, acc);
+      hop_pair<3, P, DAG, float>(g, U, fi, blk, r, y, n, acc);
+    } else {
+      hop_pair<0, P, DAG, float>(g, U, fi, blk, r, y, n, acc);
+      hop_pair<1, P, DAG, float>(g, U, fi, blk, r, y, n, acc);
+    }
+    // hand the partner its components
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const cpx<float> v = acc.c[2 * (1 - hf) + sp][c];
+        xch[1 - hf][6 * sp + 2 * c][li] = v.re;
+        xch[1 - hf][6 * sp + 2 * c + 1][li] = v.im;
+      }
+    asm volatile("bar.sync %0, 64;" ::"r"(pair_bar) : "memory");
+    Half<float> o;
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        o.c[sp][c] = {acc.c[2 * hf + sp][c].re + xch[hf][6 * sp + 2 * c][li],
+                      acc.c[2 * hf + sp][c].im + xch[hf][6 * sp + 2 * c + 1][li]};
+    // clover: chiral block hf on the site's own half
+    {
+      const Half<float> psi = load_half16_unscaled<P>(fi, g.Vb, blk, r, hf);
+      const float ps = __ldg(fi.norm + (long long)blk * g.Vb + r);
+      const uint4* d = (const uint4*)A.data + (long long)blk * 9 * g.Vb + r;
+      const float scl = (A.norm ? __ldg(A.norm + (long long)blk * g.Vb + r) : 1.0f) * ps;
+      uint32_t w[20];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const uint4 v = __ldg(d + (long long)(4 * hf + q) * g.Vb);
+        w[4 * q] = v.x;
+        w[4 * q + 1] = v.y;
+        w[4 * q + 2] = v.z;
+        w[4 * q + 3] = v.w;
+      }
+      float cb[36];
+#pragma unroll
+      for (int q = 0; q < 18; ++q) {
+        const float2 x = to_f2<P>(hf ? w[q + 2] : w[q]);
+        cb[2 * q] = x.x;
+        cb[2 * q + 1] = x.y;
+      }
+      cpx<float> i6[6], o6[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) i6[q] = psi.c[q / 3][q % 3];
+      clover_block_apply(cb, i6, o6);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        cpx<float>& a = o.c[q / 3][q % 3];
+        a = {fmaf(scl, o6[q].re, a.re), fmaf(scl, o6[q].im, a.im)};
+      }
+    }
+    float m = 0.f;
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) m = fmaxf(m, fmaxf(fabsf(o.c[sp][c].re), fabsf(o.c[sp][c].im)));
+    mx[hf][li] = m;
+    asm volatile("bar.sync %0, 64;" ::"r"(pair_bar) : "memory");
+    m = fmaxf(m, mx[1 - hf][li]);
+    if (act) store_half16<P>(fo, g.Vb, blk, r, hf, o, m);
   }
 }
 
@@ -193,10 +360,21 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// r = b - D x (FP64), partial[blockIdx.x] = sum |r|^2 over the CTA
+// r = b - D x (FP64), partial[blockIdx.x] = sum |r|^2 over the CTA; blockIdx.y
+// selects a right-hand side of a batch (fields V sites apart, partial sums ps
+// doubles apart), skipped when masked out
 __global__ void __launch_bounds__(256) residual64_kernel(Geom g, const void* __restrict__ U, FieldPtr A, FieldPtr b,
-                                                         FieldPtr x, FieldPtr r_out, double* partial) {
+                                                         FieldPtr x, FieldPtr r_out, double* partial, long long ps,
+                                                         const int* __restrict__ mask) {
   __shared__ double sh[32];
+  if (mask && !mask[blockIdx.y]) return;
+  {
+    const long long o = (long long)blockIdx.y * g.V * 12;  // double2 elements per FP64 field
+    b.data = (double2*)b.data + o;
+    x.data = (double2*)x.data + o;
+    r_out.data = (double2*)r_out.data + o;
+    partial += blockIdx.y * ps;
+  }
   long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double nrm = 0;
   if (s < g.V) {
@@ -222,9 +400,11 @@ static double bytes_per_site(int prec) {
   return 2 * (24 * 2 + 4) + 4 * 12 * 2 + (72 * 2 + 4);
 }
 
-int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s, int nrhs) {
+int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s, int nrhs, const int* mask) {
   const int prec = in.prec;
-  if (out.prec != prec || in.nreal != 24 || out.nreal != 24 || nrhs < 1) return QCD_ERR_ARG;
+  // FP64 in and double-float out: the FP64 operator with its result split
+  const int out_df = prec == P64 && out.prec == PDF;
+  if ((out.prec != prec && !out_df) || in.nreal != 24 || out.nreal != 24 || nrhs < 1) return QCD_ERR_ARG;
   QCD_TRY(ensure_gauge(c, prec, s));
   QCD_TRY(ensure_clover(c, prec, s));
   const int threads = c->dirac_threads[prec];
@@ -237,11 +417,28 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
   ProfScope ps(c, QCD_KERNEL_DIRAC, s, bytes, 1824.0 * (double)c->V * nrhs);
 #define LAUNCH(PP, BS)                                                                                 \
   if (dagger)                                                                                          \
-    dirac_kernel<PP, 1, BS><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);           \
-  else                                                                                                 \
-    dirac_kernel<PP, 0, BS><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs);
-  // 16-bit storage (FP16, BF16) is issue-bound, so it gets the fixed-shape instantiations
+    dirac_kernel<PP, 1, BS><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs, mask, out_df); \
+  else                                                                                                     \
+    dirac_kernel<PP, 0, BS><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs, mask, out_df);
+  // 16-bit storage (FP16, BF16) is issue-bound, so it gets the fixed-shape
+  // instantiations, and the two-threads-per-site form when the context asks for it
   const int bs = block_shape_id(c->g);
+  if ((prec == P16 || prec == PB16) && c->dirac_tps[prec] == 2) {
+    const unsigned g2 = (unsigned)((c->V + kPairSites - 1) / kPairSites);
+#define LAUNCH2(PP, DD, BB) \
+  dirac_pair_kernel<PP, DD, BB><<<g2, 2 * kPairSites, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs, mask)
+#define LAUNCH2_BS(PP, DD) \
+  if (bs == 1) LAUNCH2(PP, DD, 1); else if (bs == 2) LAUNCH2(PP, DD, 2); else LAUNCH2(PP, DD, 0);
+    if (prec == P16) {
+      if (dagger) { LAUNCH2_BS(P16, 1) } else { LAUNCH2_BS(P16, 0) }
+    } else {
+      if (dagger) { LAUNCH2_BS(PB16, 1) } else { LAUNCH2_BS(PB16, 0) }
+    }
+#undef LAUNCH2_BS
+#undef LAUNCH2
+    QCD_LAUNCHED();
+    return QCD_OK;
+  }
   switch (prec) {
     case P64: LAUNCH(P64, 0); break;
     case P32: LAUNCH(P32, 0); break;
@@ -270,19 +467,21 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
   return QCD_OK;
 }
 
-int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s) {
+int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s,
+               const Batch& B) {
   NvtxRange nv("residual64");
   if (b.prec != P64 || x.prec != P64 || r.prec != P64) return QCD_ERR_ARG;
   QCD_TRY(ensure_gauge(c, P64, s));
   QCD_TRY(ensure_clover(c, P64, s));
   const unsigned grid = (unsigned)((c->V + 255) / 256);
   {
-    ProfScope ps(c, QCD_KERNEL_RESIDUAL, s, (bytes_per_site(P64) + 192) * (double)c->V, 1848.0 * (double)c->V);
-    residual64_kernel<<<grid, 256, 0, s>>>(c->g, c->U[P64], c->A[P64].ptr(), b.ptr(), x.ptr(), r.ptr(),
-                                           part);
+    ProfScope ps(c, QCD_KERNEL_RESIDUAL, s, (bytes_per_site(P64) + 192) * (double)c->V * B.n,
+                 1848.0 * (double)c->V * B.n);
+    residual64_kernel<<<dim3(grid, B.n), 256, 0, s>>>(c->g, c->U[P64], c->A[P64].ptr(), b.ptr(), x.ptr(), r.ptr(),
+                                                       part, B.ps, B.mask);
     QCD_LAUNCHED();
   }
-  return reduce_partials(part, (int)grid, 1, 1, d_norm2, s);
+  return reduce_partials(part, (int)grid, 1, 1, d_norm2, s, B);
 }
 
 // ------------------------------------------------------------------------

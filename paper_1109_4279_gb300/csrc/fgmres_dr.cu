@@ -303,6 +303,7 @@ int fgmres_dr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp) {
       for (auto g : p.w->graphs)
         if (g) cudaGraphExecDestroy(g);
       p.w->graphs.clear();
+      p.w->graph_warm.clear();
       p.w->graph_key = GraphKey();
     }
     p.info.status = p.status;

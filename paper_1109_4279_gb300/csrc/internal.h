@@ -37,7 +37,7 @@ extern std::atomic<long long> g_launches;
   } while (0)
 
 inline int chunks(int prec, int nreal) {
-  int w = prec == P64 ? 2 : (prec == P32 ? 4 : 8);
+  int w = (prec == P64 || prec == PDF) ? 2 : (prec == P32 ? 4 : 8);
   return (nreal + w - 1) / w;
 }
 
@@ -65,6 +65,20 @@ struct SapWork {
   void* faces = nullptr;
   size_t faces_bytes = 0;
   int prec = -1;
+  int nr = 1;  // right-hand sides (entry points that allocate b and x themselves use one) the fields hold (back to back)
+};
+
+// Right-hand sides of one launch, held back to back: the vector fields of RHS
+// r start r field lengths after RHS 0's, its scalars ss doubles and its
+// partial sums ps doubles after RHS 0's.  Kernels run a grid dimension over
+// the right-hand sides; a masked-out RHS is skipped (its outputs keep their
+// previous contents).
+struct Batch {
+  int n = 1;                  // right-hand sides
+  long long ss = 0;           // doubles between consecutive RHS scalar blocks
+  long long ps = 0;           // doubles between consecutive RHS partial-sum blocks
+  const int* mask = nullptr;  // device flags: RHS r runs iff mask[r] != 0 (null: every RHS runs)
+  const int* k = nullptr;     // device per-RHS vector counts (solution update, back substitution)
 };
 
 // What a captured FGCR iteration depends on beyond the workspace's own
@@ -74,31 +88,41 @@ struct SapWork {
 // altered.  A captured graph is replayed only while its key is unchanged.
 struct GraphKey {
   unsigned long long gen = ~0ull;
-  int nkv = -1, precond = -1, ncy = -1, nmr = -1, sap_prec = -1, outer_prec = -1;
+  int nkv = -1, precond = -1, ncy = -1, nmr = -1, sap_prec = -1, outer_prec = -1, nr = -1, rt = -1;
   bool operator==(const GraphKey& o) const {
     return gen == o.gen && nkv == o.nkv && precond == o.precond && ncy == o.ncy && nmr == o.nmr &&
-           sap_prec == o.sap_prec && outer_prec == o.outer_prec;
+           sap_prec == o.sap_prec && outer_prec == o.outer_prec && nr == o.nr && rt == o.rt;
   }
   bool operator!=(const GraphKey& o) const { return !(*this == o); }
 };
 
-// solver work fields of one right-hand side (FP64 internal layout unless
-// stated).  Every buffer a solve touches is allocated by ws_prepare, so the
-// iteration itself never allocates (and can be captured in a CUDA graph).
+// solver work fields of nr right-hand sides (FP64 internal layout unless
+// stated; the fields of the nr right-hand sides back to back).  Every buffer a
+// solve touches is allocated by ws_prepare, so the iteration itself never
+// allocates (and can be captured in a CUDA graph).
 struct Workspace {
   SapWork sap;
   int nkv = 0;
+  int nr = 1;  // right-hand sides (entry points that allocate b and x themselves use one)
   Rec b, x, r, rho, tmp64;
   int rprec = P64;    // precision of rho, phi_k, chi_k: P64, or P32 for the refinement scheme
   std::vector<Rec> phi, chi;
+  // scalars of right-hand side q start q * ss doubles after these (right-hand side 0's)
+  double* d_scal = nullptr;  // nr blocks of ss doubles holding the arrays below
+  long long ss = 0;
   double* d_a1 = nullptr;  // [nkv][nkv] complex, first Gram-Schmidt pass
   double* d_a2 = nullptr;  // [nkv][nkv] complex, second pass
   double* d_cr = nullptr;  // [nkv][3]: |chi_k|^2, (chi_k, rho_k)
   double* d_rn = nullptr;  // [nkv + 8] residual norms
   double* d_gam = nullptr; // [nkv] complex
   double* d_gs = nullptr;  // [nkv][8] Gram-Schmidt norms and pass results
-  double* d_part = nullptr;  // reduction partial sums
-  double* h_pin = nullptr; // pinned host mirror for scalars read back
+  double* d_part = nullptr;  // reduction partial sums, ps doubles per right-hand side
+  long long ps = 0;
+  double* h_pin = nullptr; // pinned host mirror for scalars read back: nr rows of nkv + 8
+  int* d_mask = nullptr;   // per right-hand side: take part in the current launch (batched solves)
+  int* h_mask = nullptr;   // pinned staging of the mask
+  int* d_k = nullptr;      // per right-hand side: Krylov vectors of the finished cycle
+  int* h_k = nullptr;      // pinned staging of those counts
   // FGMRES-DR: Arnoldi basis V (m + 1), preconditioned vectors Z (m), k + 1
   // spare fields for the deflated restart, pinned host copy of H's columns
   std::vector<Rec> drV, drZ, drT;
@@ -114,6 +138,7 @@ struct Workspace {
   // one captured CUDA graph per FGCR iteration index, valid while graph_key
   // equals the key of the current solve (parameters and context generation)
   std::vector<cudaGraphExec_t> graphs;
+  std::vector<char> graph_warm;  // iteration k ran eagerly under graph_key (its kernels are loaded)
   GraphKey graph_key;
 };
 }  // namespace qcd
@@ -136,7 +161,8 @@ struct qcd_ctx {
   qcd::Rec A[4];     // clover (4 + m0 + c_sw term), 72 reals per site
   qcd::Rec Ahat[4];  // SAP block clover: A on even sites, A^-1 on odd sites
   qcd::Workspace* ws = nullptr;
-  std::vector<qcd::Workspace*> batch_ws;  // extra right-hand sides of a multi-RHS solve
+  qcd::Workspace* tile_ws = nullptr;       // right-hand sides solved together by batched launches
+  std::vector<qcd::Workspace*> batch_ws;  // extra right-hand sides of a multi-RHS solve (one workspace each)
   std::vector<cudaStream_t> streams;      // one stream per right-hand side of a batch
   // instrumentation
   bool prof = false;
@@ -144,6 +170,8 @@ struct qcd_ctx {
   std::vector<cudaEvent_t> event_pool;
   // launch shape chosen by the autotuner
   int dirac_threads[4] = {256, 256, 256, 256};  // CTA size of the operator kernel per precision
+  int sap_rt = 0;  // right-hand sides per CTA of batched SAP launches (0: sap_tile's default)
+  int dirac_tps[4] = {1, 1, 1, 1};  // threads per site of the operator kernel (2: 16-bit storage only)
   double* d_scalars = nullptr;  // small device array for coefficients
   double* h_scalars = nullptr;  // pinned host mirror
   // test hooks (qcd_debug_set): budget of the SAP staging wait, and bytes its
@@ -202,9 +230,12 @@ int ensure_clover(qcd_ctx* c, int prec, cudaStream_t s);
 // ---- dirac.cu
 // out = D in (dagger: D^+); fields in one precision
 // nrhs > 1: in/out hold nrhs fields back to back (V sites apart)
-int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s, int nrhs = 1);
-// r = b - D x and |r|^2 partial sums (FP64); optional second output of D x
-int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s);
+// mask (device, nrhs flags, may be null): right-hand sides whose flag is 0 are skipped
+int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s, int nrhs = 1,
+                const int* mask = nullptr);
+// r = b - D x and |r|^2 (FP64), for each right-hand side of B (fields V sites apart)
+int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s,
+               const Batch& B = Batch());
 // even/odd split (FP64): on the sites of parity par,
 //   pre = 1: out = c1 M x + c2 H y;  pre = 0: out = M (c1 x + c2 H y),
 // H the hopping term of D (of D^+ with dagger) from the other parity, M the
@@ -215,8 +246,14 @@ int eo_apply(qcd_ctx* c, const Rec& x, const Rec& y, const Rec& out, int par, in
 int schur_apply(qcd_ctx* c, const Rec& x, const Rec& tmp, const Rec& out, int dagger, cudaStream_t s);
 
 // ---- sap.cu
-int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s);
-int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec, cudaStream_t s);
+// work fields for nr right-hand sides (back to back)
+int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s, int nr = 1);
+// right-hand sides per CTA of a SAP launch over nr of them
+int sap_tile(qcd_ctx* c, int nr);
+// psi = M_SAP eta for each right-hand side of B; rt right-hand sides per CTA
+// share one staging of the block's links and clover (rt < 1: sap_tile)
+int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec, cudaStream_t s,
+              const Batch& B = Batch(), int rt = 0);
 
 // ---- blas.cu: fields of 24 reals per site, R = double (FP64 layout) or
 // float (FP32 layout, the recursion of the mixed-precision scheme).
@@ -225,28 +262,30 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
 // d_out[j] = (v_j, w) for j < k (complex); d_norm (optional) = |w|^2
 template <typename R>
 int blas_multidot(qcd_ctx* c, double* part, const R* const* v, int k, const R* w, double* d_out, cudaStream_t s,
-                  const double* cond = nullptr, double* d_norm = nullptr);
+                  const double* cond = nullptr, double* d_norm = nullptr, const Batch& B = Batch());
 // w -= sum_j coef[j] v_j (coef on device, complex); then d_out[j] = (v_j, w) for j < k
 template <typename R>
 int blas_axpy_dot(qcd_ctx* c, double* part, const R* const* v, int k, const double* d_coef, R* w, double* d_out,
-                  cudaStream_t s);
+                  cudaStream_t s, const Batch& B = Batch());
 // w -= sum_j coef[j] v_j; d_out = {|w|^2, (w, rho)}
 template <typename R>
 int blas_axpy_norm_dot(qcd_ctx* c, double* part, const R* const* v, int k, const double* d_coef, R* w, const R* rho,
-                       double* d_out, cudaStream_t s, const double* cond = nullptr);
+                       double* d_out, cudaStream_t s, const double* cond = nullptr, const Batch& B = Batch());
 // gs = {|chi|^2, pass-1 {|chi'|^2, (chi', rho)}, pass-2 {...}}: picks the final
 // coefficients into cr, chi /= |chi|, rho -= (chi, rho) chi, d_out = |rho|^2
 template <typename R>
 int blas_normalise_update(qcd_ctx* c, double* part, R* chi, R* rho, const double* d_gs, int two_pass, double* d_cr,
-                          double* d_out, cudaStream_t s);
+                          double* d_out, cudaStream_t s, const Batch& B = Batch());
 // x += sum_j gamma_j phi_j (gamma on device)
 template <typename R>
-int blas_multi_axpy(qcd_ctx* c, const R* const* phi, int k, const double* d_gamma, R* x, cudaStream_t s);
+int blas_multi_axpy(qcd_ctx* c, const R* const* phi, int k, const double* d_gamma, R* x, cudaStream_t s,
+                    const Batch& B = Batch());
 // iterative refinement: x64 += sqrt(*d_rn2) sum_j gamma_j phi_j (FP32 phi_j)
 int blas_refine_update(qcd_ctx* c, const float* const* phi, int k, const double* d_gamma, const double* d_rn2,
-                       double* x, cudaStream_t s);
+                       double* x, cudaStream_t s, const Batch& B = Batch());
 // out32 = r64 / sqrt(*d_rn2)
-int blas_demote_normalised(qcd_ctx* c, const double* r, const double* d_rn2, float* out, cudaStream_t s);
+int blas_demote_normalised(qcd_ctx* c, const double* r, const double* d_rn2, float* out, cudaStream_t s,
+                           const Batch& B = Batch());
 // x /= |x| (FP64) with |x|^2 from the Gram-Schmidt results (pass 2 when it
 // ran); *d_hnorm = |x| before the scaling
 int blas_gs_normalise(qcd_ctx* c, double* x, const double* d_gs, int two_pass, double* d_hnorm, cudaStream_t s);
@@ -256,21 +295,38 @@ int blas_cg_update(qcd_ctx* c, double* part, double* x, double* r, const double*
                    const double* d_rr, const double* d_tt, double* d_rr_new, cudaStream_t s);
 int blas_cg_direction(qcd_ctx* c, double* p, const double* r, const double* d_rr_new, const double* d_rr,
                       cudaStream_t s);
+// the double-float recursion (Prec PDF): the same Gram-Schmidt building blocks
+// on fields of float4 (re hi, re lo, im hi, im lo), V * 12 per right-hand side
+int blas_df_multidot(qcd_ctx* c, double* part, const float4* const* v, int k, const float4* w, double* d_out,
+                     cudaStream_t s, const double* cond, double* d_norm, const Batch& B = Batch());
+int blas_df_axpy_norm_dot(qcd_ctx* c, double* part, const float4* const* v, int k, const double* d_coef, float4* w,
+                          const float4* rho, double* d_out, cudaStream_t s, const double* cond,
+                          const Batch& B = Batch());
+int blas_df_normalise_update(qcd_ctx* c, double* part, float4* chi, float4* rho, const double* d_gs, int two_pass,
+                             double* d_cr, double* d_out, cudaStream_t s, const Batch& B = Batch());
+// FP64 field <-> double-float field (same internal layout)
+int blas_df_split(qcd_ctx* c, const double* in, float* out, cudaStream_t s, const Batch& B = Batch());
+int blas_df_join(qcd_ctx* c, const float* in, double* out, cudaStream_t s, const Batch& B = Batch());
 // norm2
 template <typename R>
-int blas_norm2(qcd_ctx* c, double* part, const R* v, double* d_out, cudaStream_t s);
+int blas_norm2(qcd_ctx* c, double* part, const R* v, double* d_out, cudaStream_t s, const Batch& B = Batch());
 // y = g5 x (in place allowed)
 int blas_gamma5(qcd_ctx* c, const double* x, double* y, int nsites_layout, cudaStream_t s);
 // small dense solve of the FGCR triangular system on the device
 int fgcr_backsub(const double* d_a1, const double* d_a2, const double* d_cr, int k, int ld, double* d_gamma,
-                 cudaStream_t s);
+                 cudaStream_t s, const Batch& B = Batch());
 // out[j] = sum_p partials[p * stride + j], j < m (fixed order)
-int reduce_partials(const double* partials, int nparts, int stride, int m, double* out, cudaStream_t s);
+int reduce_partials(const double* partials, int nparts, int stride, int m, double* out, cudaStream_t s,
+                    const Batch& B = Batch());
 
 // ---- solver.cu
 size_t partials_for(long long V);
-int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream_t s);
+// allocate the solver fields and scalars of nr right-hand sides (a change of
+// nr reallocates everything)
+int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream_t s, int nr = 1);
 void ws_release(Workspace& w);
+// the launch descriptor of a workspace's right-hand sides
+Batch batch_of(const Workspace& w, const int* mask);
 // one right-hand side of one lattice, solved in lock step with the others
 struct Problem {
   qcd_ctx* c = nullptr;
@@ -284,9 +340,24 @@ struct Problem {
   bool active = true, cycle_done = false;
   int status = QCD_OK;
 };
-// FGCR (Sec. 4) on all problems in lock step: each iteration is enqueued for
-// every active problem on its own stream (replayed from a CUDA graph when
-// use_graphs), then one host synchronisation checks every residual.
+// right-hand sides of one lattice that share a workspace and are iterated by
+// the same launches (each kernel of an FGCR iteration runs over all of them);
+// rhs[q]->b / ->x view right-hand side q of the workspace's fields
+struct Group {
+  qcd_ctx* c = nullptr;
+  Workspace* w = nullptr;
+  cudaStream_t s = nullptr;
+  std::vector<Problem*> rhs;
+  int rt = 1;  // right-hand sides per CTA of the SAP launches
+  int nr() const { return (int)rhs.size(); }
+};
+// a view of right-hand side q of a workspace field
+Rec rhs_view(const Rec& f, int q, long long V);
+// FGCR (Sec. 4) on all groups in lock step: each iteration is enqueued for
+// every group on its own stream (replayed from a CUDA graph when use_graphs),
+// then one host synchronisation checks every residual.
+int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool use_graphs);
+// FGCR on single-right-hand-side problems (one group each)
 int fgcr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp, bool use_graphs);
 // FGMRES with deflated restarts (Sec. 4), FP64 recursion; problems one after another
 int fgmres_dr_batch(std::vector<Problem>& probs, const qcd_solver_params& sp);

@@ -82,11 +82,11 @@ __global__ void import_kernel(Geom g, const double* __restrict__ lex, FieldPtr o
     v[2 * k + 1] = d.y;
   }
   FieldPtr f = out;
-  const int NC = P == P64 ? 12 : (P == P32 ? 6 : 3);
+  const int NC = (P == P64 || P == PDF) ? 12 : (P == P32 ? 6 : 3);
   f.data = (char*)out.data + (size_t)rhs * field_stride_sites * NC * 16;
   if (out.norm) f.norm = out.norm + (size_t)rhs * field_stride_sites;
-  if constexpr (P == P64) {
-    store_record<P64, 24, double>(f, g.Vb, blk, r, v);
+  if constexpr (P == P64 || P == PDF) {
+    store_record<P, 24, double>(f, g.Vb, blk, r, v);
   } else {
     float w[24];
 #pragma unroll
@@ -104,12 +104,12 @@ __global__ void export_kernel(Geom g, FieldPtr in, double* __restrict__ lex, lon
   int x[4];
   global_coords(g, blk, r, x);
   FieldPtr f = in;
-  const int NC = P == P64 ? 12 : (P == P32 ? 6 : 3);
+  const int NC = (P == P64 || P == PDF) ? 12 : (P == P32 ? 6 : 3);
   f.data = (char*)in.data + (size_t)rhs * field_stride_sites * NC * 16;
   if (in.norm) f.norm = in.norm + (size_t)rhs * field_stride_sites;
   double v[24];
-  if constexpr (P == P64) {
-    load_record<P64, 24, double>(f, g.Vb, blk, r, v);
+  if constexpr (P == P64 || P == PDF) {
+    load_record<P, 24, double>(f, g.Vb, blk, r, v);
   } else {
     float w[24];
     load_record<P, 24, float>(f, g.Vb, blk, r, w);
@@ -126,6 +126,7 @@ int import_spinor(qcd_ctx* c, const double* lex, const Rec& out, int nrhs, cudaS
   dim3 grid((unsigned)((c->V + 255) / 256), nrhs);
   switch (out.prec) {
     case P64: import_kernel<P64><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
+    case PDF: import_kernel<PDF><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
     case P32: import_kernel<P32><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
     case P16: import_kernel<P16><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
     case PB16: import_kernel<PB16><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
@@ -140,6 +141,7 @@ int export_spinor(qcd_ctx* c, const Rec& in, double* lex, int nrhs, cudaStream_t
   dim3 grid((unsigned)((c->V + 255) / 256), nrhs);
   switch (in.prec) {
     case P64: export_kernel<P64><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
+    case PDF: export_kernel<PDF><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
     case P32: export_kernel<P32><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
     case P16: export_kernel<P16><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
     case PB16: export_kernel<PB16><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;

@@ -18,7 +18,7 @@
 
 namespace qcd {
 
-enum Prec : int { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+enum Prec : int { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PDF = 4 };  // PDF: double-float pairs, FP64 layout
 
 // ------------------------------------------------------------------------
 // FP64 <-> FP32 conversion on the integer pipes.  GB300 runs FP64 conversions
@@ -54,6 +54,60 @@ __device__ __forceinline__ double f32_to_f64(float f) {
     return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
   if ((u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);  // +-0
   return (double)f;
+}
+
+// ------------------------------------------------------------------------
+// Double-float ("df64") numbers: x = hi + lo with two FP32 values, |lo| at
+// most half an ulp of hi, a 48-bit significand carried on the FP32 pipes.
+// Built from the error-free transformations: Knuth's TwoSum (s + e = a + b
+// exactly), its Dekker form for |a| >= |b|, and the product split by a fused
+// multiply-add (p + e = a b exactly, e = fma(a, b, -p)).  Used for the Krylov
+// recursion of the solver, whose FP64 form is bound by GB300's FP64 rate.
+// ------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b| (or a = 0)
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+// x + y, with the two error terms folded into one renormalisation
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  s.lo += x.lo + y.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+// FP64 -> df64 (hi = x rounded to FP32, lo = the rest rounded) and back, on
+// the integer pipes except one FP64 subtraction
+__device__ __forceinline__ df df_from_f64(double x) {
+  const float h = f64_to_f32(x);
+  return {h, f64_to_f32(x - f32_to_f64(h))};
+}
+__device__ __forceinline__ double df_to_f64(df x) { return f32_to_f64(x.hi) + f32_to_f64(x.lo); }
+// x y (the lo x lo term, 2^-48 relative, is dropped)
+__device__ __forceinline__ df df_mul(df x, df y) {
+  df p = two_prod(x.hi, y.hi);
+  p.lo = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+// z + x y
+__device__ __forceinline__ df df_fma(df x, df y, df z) {
+  df p = two_prod(x.hi, y.hi);
+  p.lo = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo));
+  df s = two_sum(z.hi, p.hi);
+  s.lo += z.lo + p.lo;
+  return fast_two_sum(s.hi, s.lo);
 }
 
 // ------------------------------------------------------------------------
@@ -407,6 +461,11 @@ struct Storage<P32> {
   static constexpr int per_chunk = 4;
 };
 template <>
+struct Storage<PDF> {  // two double-float reals (hi, lo, hi, lo) per 16-byte chunk
+  typedef float real;
+  static constexpr int per_chunk = 2;
+};
+template <>
 struct Storage<P16> {
   typedef __half real;
   static constexpr int per_chunk = 8;
@@ -457,6 +516,14 @@ __device__ __forceinline__ void load_record(const FieldPtr& f, int Vb, int blk, 
       double2 v = __ldg(d + base + (long long)k * Vb);
       out[2 * k] = (T)v.x;
       out[2 * k + 1] = (T)v.y;
+    }
+  } else if constexpr (P == PDF) {
+    const float4* d = (const float4*)f.data;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const float4 v = __ldg(d + base + (long long)k * Vb);
+      out[2 * k] = (T)df_to_f64(df{v.x, v.y});
+      out[2 * k + 1] = (T)df_to_f64(df{v.z, v.w});
     }
   } else if constexpr (P == P32) {
     const float4* d = (const float4*)f.data;
@@ -516,6 +583,13 @@ __device__ __forceinline__ void store_record(const FieldPtr& f, int Vb, int blk,
     double2* d = (double2*)f.data;
 #pragma unroll
     for (int k = 0; k < NC; ++k) d[base + (long long)k * Vb] = make_double2((double)in[2 * k], (double)in[2 * k + 1]);
+  } else if constexpr (P == PDF) {
+    float4* d = (float4*)f.data;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const df a = df_from_f64((double)in[2 * k]), b = df_from_f64((double)in[2 * k + 1]);
+      d[base + (long long)k * Vb] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
   } else if constexpr (P == P32) {
     float4* d = (float4*)f.data;
 #pragma unroll

@@ -34,6 +34,7 @@ struct SapArgs {
   int nmr;              // MR steps per block
   int read_eta;         // residual source: 1 = eta, 0 = rho_sap
   int io32;             // eta and out are FP32 fields (else FP64)
+  int io_df;            // eta is a double-float field (read as its FP32 high parts); out FP64
   int faces_in;         // add face contributions of the other colour
   int faces_out;        // write this block's face contributions
   int write_rho;        // store the block residual
@@ -50,7 +51,30 @@ struct SapArgs {
   int* err;             // set to 1 if a staging wait timed out
   long long wait_cycles;  // budget of the staging wait (clock cycles)
   int extra_tx;         // bytes the staging barrier expects beyond the copies (0; a test sets more)
+  // right-hand sides: nrhs fields back to back in eta, rho, psi, out and the
+  // face buffers (byte strides below; rho_ns: floats between 16-bit scale
+  // arrays); CTA (x, y) solves block x for right-hand sides y rt .. y rt + rt - 1
+  // in turn, with the block's links and clover staged once
+  int nrhs, rt;
+  const int* mask;      // device flags: right-hand side r is solved iff mask[r] != 0 (null: all)
+  long long eta_rs, rho_rs, rho_ns, psi_rs, out_rs, faces_rs;
 };
+
+// the fields of right-hand side r (computed where used, so that no per-RHS
+// pointer stays live across the block solve)
+__device__ __forceinline__ FieldPtr rhs_eta(const SapArgs& a, int r) {
+  return {(char*)a.eta.data + r * a.eta_rs, nullptr};
+}
+__device__ __forceinline__ FieldPtr rhs_rho(const SapArgs& a, int r) {
+  return {(char*)a.rho.data + r * a.rho_rs, a.rho.norm ? a.rho.norm + r * a.rho_ns : nullptr};
+}
+__device__ __forceinline__ FieldPtr rhs_psi(const SapArgs& a, int r) {
+  return {(char*)a.psi.data + r * a.psi_rs, nullptr};
+}
+__device__ __forceinline__ FieldPtr rhs_out(const SapArgs& a, int r) {
+  return {(char*)a.out.data + r * a.out_rs, nullptr};
+}
+__device__ __forceinline__ void* rhs_faces(const SapArgs& a, int r) { return (char*)a.faces + r * a.faces_rs; }
 
 template <typename T>
 struct FaceChunks {
@@ -67,7 +91,7 @@ __device__ __forceinline__ int face_index(const Geom& g, const int y[4], int mu)
 }
 
 template <typename T>
-__device__ __forceinline__ void face_store(const SapArgs& a, int blk, int f, int q, const Half<T>& h) {
+__device__ __forceinline__ void face_store(const SapArgs& a, void* faces, int blk, int f, int q, const Half<T>& h) {
   T v[12];
 #pragma unroll
   for (int s = 0; s < 2; ++s)
@@ -78,22 +102,22 @@ __device__ __forceinline__ void face_store(const SapArgs& a, int blk, int f, int
     }
   const long long base = (long long)blk * FaceChunks<T>::n * a.F + a.fo[f] + q;
   if constexpr (sizeof(T) == 8) {
-    double2* d = (double2*)a.faces;
+    double2* d = (double2*)faces;
 #pragma unroll
     for (int k = 0; k < 6; ++k) d[base + (long long)k * a.F] = make_double2(v[2 * k], v[2 * k + 1]);
   } else {
-    float4* d = (float4*)a.faces;
+    float4* d = (float4*)faces;
 #pragma unroll
     for (int k = 0; k < 3; ++k) d[base + (long long)k * a.F] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
   }
 }
 
 template <typename T>
-__device__ __forceinline__ Half<T> face_load(const SapArgs& a, int blk, int f, int q) {
+__device__ __forceinline__ Half<T> face_load(const SapArgs& a, const void* faces, int blk, int f, int q) {
   T v[12];
   const long long base = (long long)blk * FaceChunks<T>::n * a.F + a.fo[f] + q;
   if constexpr (sizeof(T) == 8) {
-    const double2* d = (const double2*)a.faces;
+    const double2* d = (const double2*)faces;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       double2 t = d[base + (long long)k * a.F];
@@ -101,7 +125,7 @@ __device__ __forceinline__ Half<T> face_load(const SapArgs& a, int blk, int f, i
       v[2 * k + 1] = t.y;
     }
   } else {
-    const float4* d = (const float4*)a.faces;
+    const float4* d = (const float4*)faces;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       float4 t = d[base + (long long)k * a.F];
@@ -625,6 +649,24 @@ __device__ __forceinline__ void g_half_store(const FieldPtr& f, int Vb, int blk,
   }
 }
 
+// owned half of a double-float spinor field (the FP64 layout with float4
+// chunks (re hi, re lo, im hi, im lo)): the high parts, i.e. the values
+// rounded to FP32 -- what the block solver computes with
+template <typename T>
+__device__ __forceinline__ Half<T> g_half_df(const FieldPtr& f, int Vb, int blk, int r, int hf) {
+  Half<T> h;
+  const float4* d = (const float4*)f.data + ((long long)blk * 12 + 6 * hf) * Vb + r;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 v = d[(long long)k * Vb];
+    if constexpr (sizeof(T) == 8)
+      h.c[k / 3][k % 3] = {f32_to_f64(v.x) + f32_to_f64(v.y), f32_to_f64(v.z) + f32_to_f64(v.w)};
+    else
+      h.c[k / 3][k % 3] = {v.x, v.z};
+  }
+  return h;
+}
+
 // owned half of a 16-bit spinor record ([blk][3 chunks][Vb] uint4 of 8 reals,
 // complex k at chunk k / 4): half hf is chunk 2 hf and the hf-th 8-byte half of
 // chunk 1, scaled by the site's norm
@@ -649,8 +691,8 @@ __device__ __forceinline__ Half<float> g_half16(const FieldPtr& f, int Vb, int b
 // receive the other colour's face contributions at site (blk, r) for the
 // directions of this thread; returns a partial full spinor
 template <typename T, typename ST>
-__device__ __forceinline__ Spinor<T> receive_faces(const SapArgs& a, const ST& st, int blk, int r, const int y[4],
-                                                   const int n[4], int hf) {
+__device__ __forceinline__ Spinor<T> receive_faces(const SapArgs& a, const void* faces, const ST& st, int blk, int r,
+                                                   const int y[4], const int n[4], int hf) {
   const Geom& g = a.g;
   Spinor<T> acc;
   zero(acc);
@@ -662,12 +704,12 @@ __device__ __forceinline__ Spinor<T> receive_faces(const SapArgs& a, const ST& s
     const int nmu = mu == 0 ? n[0] : (mu == 1 ? n[1] : (mu == 2 ? n[2] : n[3]));
     if (ymu == g.b[mu] - 1) {  // from block + mu: U_mu(y) (1 - g) part, projected by the sender
       const int nbk = nmu + 1 < g.nb[mu] ? blk + g.bstr[mu] : blk - (g.nb[mu] - 1) * g.bstr[mu];
-      const Half<T> h = face_load<T>(a, nbk, 2 * mu, face_index(g, y, mu));
+      const Half<T> h = face_load<T>(a, faces, nbk, 2 * mu, face_index(g, y, mu));
       expand_add_rt<-1>(acc, umul(st.link(r, mu), h), T(1), d);
     }
     if (ymu == 0) {  // from block - mu: U^+ (1 + g) part, multiplied by the sender
       const int nbk = nmu > 0 ? blk - g.bstr[mu] : blk + (g.nb[mu] - 1) * g.bstr[mu];
-      const Half<T> w = face_load<T>(a, nbk, 2 * mu + 1, face_index(g, y, mu));
+      const Half<T> w = face_load<T>(a, faces, nbk, 2 * mu + 1, face_index(g, y, mu));
       expand_add_rt<+1>(acc, w, T(1), d);
     }
   }
@@ -677,8 +719,8 @@ __device__ __forceinline__ Spinor<T> receive_faces(const SapArgs& a, const ST& s
 // write the face contributions of the correction chi at site (blk, r) for the
 // directions of this thread
 template <typename T, typename ST>
-__device__ __forceinline__ void send_faces(const SapArgs& a, const ST& st, int blk, int r, const int y[4],
-                                           const int n[4], const Spinor<T>& chi, int hf) {
+__device__ __forceinline__ void send_faces(const SapArgs& a, void* faces, const ST& st, int blk, int r,
+                                           const int y[4], const int n[4], const Spinor<T>& chi, int hf) {
   const Geom& g = a.g;
 #pragma unroll 1
   for (int m = 0; m < 2; ++m) {
@@ -693,7 +735,7 @@ __device__ __forceinline__ void send_faces(const SapArgs& a, const ST& st, int b
       for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) h.c[s][c] = f * h.c[s][c];
-      face_store<T>(a, blk, 2 * mu, face_index(g, y, mu), h);
+      face_store<T>(a, faces, blk, 2 * mu, face_index(g, y, mu), h);
     }
     if (ymu == g.b[mu] - 1) {  // to y = x + mu: 1/2 eta_mu(x) U_mu(x)^+ (1 + g) chi, projected
       const T f = T(0.5) * ((nmu == g.nb[mu] - 1) ? bc_of<T>(g, mu) : T(1));
@@ -702,7 +744,7 @@ __device__ __forceinline__ void send_faces(const SapArgs& a, const ST& st, int b
       for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) w.c[s][c] = f * w.c[s][c];
-      face_store<T>(a, blk, 2 * mu + 1, face_index(g, y, mu), w);
+      face_store<T>(a, faces, blk, 2 * mu + 1, face_index(g, y, mu), w);
     }
   }
 }
@@ -725,7 +767,9 @@ __host__ __device__ __forceinline__ int pairs_per_half(int Vbh) { return (Vbh + 
 
 // VB: the block volume as a compile-time constant (shared-memory and link
 // offsets become immediates, which frees registers), or 0 for any volume
-template <int P, typename T, int VB>
+// TILED: the CTA solves a tile of right-hand sides (the loop below runs over
+// them); otherwise exactly one, right-hand side 0, and the loop folds away
+template <int P, typename T, int VB, bool TILED>
 __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   typedef typename StageFor<P>::type ST;
   constexpr bool kHalf = (P == P16 || P == PB16);
@@ -757,7 +801,15 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
     ++n[3];
   }
 
-  // ---- stage the block's links and clover
+  // right-hand sides of this CTA; a tile with none to solve stages nothing
+  const int rhs0 = TILED ? blockIdx.y * a.rt : 0, rhs1 = TILED ? min(rhs0 + a.rt, a.nrhs) : 1;
+  if (TILED) {
+    bool any = false;
+    for (int rr = rhs0; rr < rhs1; ++rr) any |= (a.mask == nullptr || a.mask[rr] != 0);
+    if (!any) return;
+  }
+
+  // ---- stage the block's links and clover (once for the whole tile)
   if constexpr (kHalf) {
     if (threadIdx.x == 0) {
       mbar_init(bar, 1);
@@ -820,154 +872,170 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
     pkO[1] = hf ? pko[3] : pko[1];
   }
 
-  // ---- residual of the two sites (own halves only: the pair's two threads
-  // read complementary halves)
-  Half<T> rho_e, rho_o;
-  if (a.read_eta && a.io32) {
-    const Half<float> de = g_half<P32, float>(a.eta, Vb, blk, re, hf);
-    const Half<float> dd = g_half<P32, float>(a.eta, Vb, blk, ro, hf);
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        rho_e.c[s][c] = {(T)de.c[s][c].re, (T)de.c[s][c].im};
-        rho_o.c[s][c] = {(T)dd.c[s][c].re, (T)dd.c[s][c].im};
-      }
-  } else if (a.read_eta) {
-    rho_e = g_half<P64, T>(a.eta, Vb, blk, re, hf);
-    rho_o = g_half<P64, T>(a.eta, Vb, blk, ro, hf);
-  } else if constexpr (kHalf) {
-    rho_e = g_half16<P>(a.rho, Vb, blk, re, hf);
-    rho_o = g_half16<P>(a.rho, Vb, blk, ro, hf);
-  } else {
-    rho_e = g_half<P, T>(a.rho, Vb, blk, re, hf);
-    rho_o = g_half<P, T>(a.rho, Vb, blk, ro, hf);
-  }
-  if constexpr (kHalf) {
-    // every thread waits (bounded) for the staging copies; a time-out is made
-    // block-uniform, recorded, and the block is skipped
-    const bool ok = mbar_wait_bounded(bar, a.wait_cycles);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) atomicExch(a.err, 1);
-      mbar_wait_bounded(bar, kWaitCycles);  // let copies still in flight land before the CTA exits
-      return;
-    }
-    expand_links<P>((const unsigned char*)s_r, (unsigned char*)st.base, Vb);
-  }
-  __syncthreads();
-  {  // zero sites of r and t (the 16-bit links' landing zone is consumed by now)
-    typedef typename Chunk<T>::type C;
-    constexpr int NCH = 24 / Chunk<T>::R;
-    if (threadIdx.x < 2 * NCH) {
-      const T z[Chunk<T>::R] = {};
-      C* base = (C*)(threadIdx.x < NCH ? s_r : s_t);
-      base[(threadIdx.x % NCH) * ns + Vbh] = chunk_make(z);
-    }
-  }
-  if (a.faces_in) {
-    rho_e = half_axpy(rho_e, pair_reduce_s(receive_faces<T>(a, st, blk, re, ye, n, hf), hf, i, np, s_x), T(1));
-    __syncthreads();
-    rho_o = half_axpy(rho_o, pair_reduce_s(receive_faces<T>(a, st, blk, ro, yo, n, hf), hf, i, np, s_x), T(1));
-  }
-  // etahat = rho_e - D_eo A_oo^-1 rho_o: first t = A_oo^-1 rho_o
-  if (act) s_half_store(s_t, ns, i, hf, clover_half(st, ro, hf, rho_o));
-  __syncthreads();
-  Half<T> r = half_axpy(rho_e, block_hops<T>(st, ns, re, s_t, pkE, Vbh, hf, i, np, s_x), T(-1));
-  Half<T> x;
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) x.c[s][c] = {T(0), T(0)};
-  if (act) s_half_store(s_r, ns, i, hf, r);
-  __syncthreads();
-
-  // ---- MR on Dhat = A_ee - D_eo A_oo^-1 D_oe, x_e = 0, r = etahat.  Each
-  // step runs two phases through one code path: phase 0 (odd sites)
-  // t = A_oo^-1 D_oe r, phase 1 (even sites) p = A_ee r - D_eo t.
+  bool staged = false;
 #pragma unroll 1
-  for (int step = 0; step < 2 * a.nmr; ++step) {
-    const int ph = step & 1;
-    const int pk2[2] = {ph ? pkE[0] : pkO[0], ph ? pkE[1] : pkO[1]};
-    const Half<T> hq = block_hops<T>(st, ns, ph ? re : ro, ph ? s_t : s_r, pk2, ph ? Vbh : 0, hf, i, np, s_x);
-    const Half<T> cl = clover_half(st, ph ? re : ro, hf, ph ? r : hq);
-    if (ph == 0) {
-      if (act) s_half_store(s_t, ns, i, hf, cl);
-      __syncthreads();
-      continue;
-    }
-    const Half<T> p = half_axpy(cl, hq, T(-1));
-    T pr_re = 0, pr_im = 0, pp = 0;
-    if (act) {
+  for (int rr = rhs0; rr < rhs1; ++rr) {
+    if (TILED && a.mask != nullptr && a.mask[rr] == 0) continue;  // uniform across the CTA
+
+    // ---- residual of the two sites (own halves only: the pair's two threads
+    // read complementary halves)
+    Half<T> rho_e, rho_o;
+    if (a.read_eta && a.io32) {
+      const Half<float> de = g_half<P32, float>(rhs_eta(a, rr), Vb, blk, re, hf);
+      const Half<float> dd = g_half<P32, float>(rhs_eta(a, rr), Vb, blk, ro, hf);
 #pragma unroll
       for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const cpx<T> v = p.c[s][c], w = r.c[s][c];
-          pr_re += v.re * w.re + v.im * w.im;
-          pr_im += v.re * w.im - v.im * w.re;
-          pp += v.re * v.re + v.im * v.im;
+          rho_e.c[s][c] = {(T)de.c[s][c].re, (T)de.c[s][c].im};
+          rho_o.c[s][c] = {(T)dd.c[s][c].re, (T)dd.c[s][c].im};
         }
+    } else if (a.read_eta && a.io_df) {
+      rho_e = g_half_df<T>(rhs_eta(a, rr), Vb, blk, re, hf);
+      rho_o = g_half_df<T>(rhs_eta(a, rr), Vb, blk, ro, hf);
+    } else if (a.read_eta) {
+      rho_e = g_half<P64, T>(rhs_eta(a, rr), Vb, blk, re, hf);
+      rho_o = g_half<P64, T>(rhs_eta(a, rr), Vb, blk, ro, hf);
+    } else if constexpr (kHalf) {
+      rho_e = g_half16<P>(rhs_rho(a, rr), Vb, blk, re, hf);
+      rho_o = g_half16<P>(rhs_rho(a, rr), Vb, blk, ro, hf);
+    } else {
+      rho_e = g_half<P, T>(rhs_rho(a, rr), Vb, blk, re, hf);
+      rho_o = g_half<P, T>(rhs_rho(a, rr), Vb, blk, ro, hf);
     }
-    cta_sum3(pr_re, pr_im, pp, s_red);
-    const T inv = pp > T(0) ? T(1) / pp : T(0);
-    const cpx<T> alpha = {pr_re * inv, pr_im * inv};
+    if (!staged) {
+      if constexpr (kHalf) {
+        // every thread waits (bounded) for the staging copies; a time-out is made
+        // block-uniform, recorded, and the block is skipped
+        const bool ok = mbar_wait_bounded(bar, a.wait_cycles);
+        if (__syncthreads_or(!ok)) {
+          if (threadIdx.x == 0) atomicExch(a.err, 1);
+          mbar_wait_bounded(bar, kWaitCycles);  // let copies still in flight land before the CTA exits
+          return;
+        }
+        expand_links<P>((const unsigned char*)s_r, (unsigned char*)st.base, Vb);
+      }
+      __syncthreads();
+      {  // zero sites of r and t (the 16-bit links' landing zone is consumed by now)
+        typedef typename Chunk<T>::type C;
+        constexpr int NCH = 24 / Chunk<T>::R;
+        if (threadIdx.x < 2 * NCH) {
+          const T z[Chunk<T>::R] = {};
+          C* base = (C*)(threadIdx.x < NCH ? s_r : s_t);
+          base[(threadIdx.x % NCH) * ns + Vbh] = chunk_make(z);
+        }
+      }
+      staged = true;
+    }
+    if (TILED) __syncthreads();  // the previous right-hand side's last reads of r, t and the exchange buffer are done
+    if (a.faces_in) {
+      rho_e = half_axpy(rho_e, pair_reduce_s(receive_faces<T>(a, rhs_faces(a, rr), st, blk, re, ye, n, hf), hf, i, np, s_x),
+                        T(1));
+      __syncthreads();
+      rho_o = half_axpy(rho_o, pair_reduce_s(receive_faces<T>(a, rhs_faces(a, rr), st, blk, ro, yo, n, hf), hf, i, np, s_x),
+                        T(1));
+    }
+    // etahat = rho_e - D_eo A_oo^-1 rho_o: first t = A_oo^-1 rho_o
+    if (act) s_half_store(s_t, ns, i, hf, clover_half(st, ro, hf, rho_o));
+    __syncthreads();
+    Half<T> r = half_axpy(rho_e, block_hops<T>(st, ns, re, s_t, pkE, Vbh, hf, i, np, s_x), T(-1));
+    Half<T> x;
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        x.c[s][c] = cmadd(alpha, r.c[s][c], x.c[s][c]);
-        r.c[s][c] = r.c[s][c] - cmul(alpha, p.c[s][c]);
-      }
+      for (int c = 0; c < 3; ++c) x.c[s][c] = {T(0), T(0)};
     if (act) s_half_store(s_r, ns, i, hf, r);
     __syncthreads();
-  }
 
-  // ---- chi_o = A_oo^-1 (rho_o - D_oe chi_e)
-  if (act) s_half_store(s_r, ns, i, hf, x);
-  __syncthreads();
-  const Half<T> chi_o =
-      clover_half(st, ro, hf, half_axpy(rho_o, block_hops<T>(st, ns, ro, s_r, pkO, 0, hf, i, np, s_x), T(-1)));
-  __syncthreads();
-
-  // ---- outputs: solution, block residual (r on even, 0 on odd), faces
-  constexpr int PS = PsiPrec<P>::value;
-  typedef typename std::conditional<PS == P64, double, float>::type TS;
-  const Spinor<T> x_full = pair_full_s(x, hf, i, np, s_x);
-  const Spinor<T> chio_full = pair_full_s(chi_o, hf, i, np, s_x);
-  const Spinor<T> r_full = pair_full_s(r, hf, i, np, s_x);
-  if (!act) return;
+    // ---- MR on Dhat = A_ee - D_eo A_oo^-1 D_oe, x_e = 0, r = etahat.  Each
+    // step runs two phases through one code path: phase 0 (odd sites)
+    // t = A_oo^-1 D_oe r, phase 1 (even sites) p = A_ee r - D_eo t.
 #pragma unroll 1
-  for (int half = 0; half < 2; ++half) {
-    const int rs = half ? ro : re;
-    const Half<T>& chi = half ? chi_o : x;
-    Half<TS> v;
+    for (int step = 0; step < 2 * a.nmr; ++step) {
+      const int ph = step & 1;
+      const int pk2[2] = {ph ? pkE[0] : pkO[0], ph ? pkE[1] : pkO[1]};
+      const Half<T> hq = block_hops<T>(st, ns, ph ? re : ro, ph ? s_t : s_r, pk2, ph ? Vbh : 0, hf, i, np, s_x);
+      const Half<T> cl = clover_half(st, ph ? re : ro, hf, ph ? r : hq);
+      if (ph == 0) {
+        if (act) s_half_store(s_t, ns, i, hf, cl);
+        __syncthreads();
+        continue;
+      }
+      const Half<T> p = half_axpy(cl, hq, T(-1));
+      T pr_re = 0, pr_im = 0, pp = 0;
+      if (act) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < 2; ++s)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) v.c[s][c] = {(TS)chi.c[s][c].re, (TS)chi.c[s][c].im};
-    if (a.psi_mode == 1 || a.psi_mode == 3) v = half_axpy(v, g_half<PS, TS>(a.psi, Vb, blk, rs, hf), TS(1));
-    if (a.psi_mode <= 1) {
-      g_half_store<PS, TS>(a.psi, Vb, blk, rs, hf, v);
-    } else if (a.io32) {
-      Half<float> fv;
+          for (int c = 0; c < 3; ++c) {
+            const cpx<T> v = p.c[s][c], w = r.c[s][c];
+            pr_re += v.re * w.re + v.im * w.im;
+            pr_im += v.re * w.im - v.im * w.re;
+            pp += v.re * v.re + v.im * v.im;
+          }
+      }
+      cta_sum3(pr_re, pr_im, pp, s_red);
+      const T inv = pp > T(0) ? T(1) / pp : T(0);
+      const cpx<T> alpha = {pr_re * inv, pr_im * inv};
 #pragma unroll
       for (int s = 0; s < 2; ++s)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) fv.c[s][c] = {(float)v.c[s][c].re, (float)v.c[s][c].im};
-      g_half_store<P32, float>(a.out, Vb, blk, rs, hf, fv);
-    } else {
-      g_half_store<P64, TS>(a.out, Vb, blk, rs, hf, v);  // widened on the integer pipes
+        for (int c = 0; c < 3; ++c) {
+          x.c[s][c] = cmadd(alpha, r.c[s][c], x.c[s][c]);
+          r.c[s][c] = r.c[s][c] - cmul(alpha, p.c[s][c]);
+        }
+      if (act) s_half_store(s_r, ns, i, hf, r);
+      __syncthreads();
     }
-  }
-  if (a.write_rho && hf == 0) {
-    store_spinor<P, T>(a.rho, Vb, blk, re, r_full);
-    Spinor<T> z;
-    zero(z);
-    store_spinor<P, T>(a.rho, Vb, blk, ro, z);
-  }
-  if (a.faces_out) {
-    send_faces<T>(a, st, blk, re, ye, n, x_full, hf);
-    send_faces<T>(a, st, blk, ro, yo, n, chio_full, hf);
+
+    // ---- chi_o = A_oo^-1 (rho_o - D_oe chi_e)
+    if (act) s_half_store(s_r, ns, i, hf, x);
+    __syncthreads();
+    const Half<T> chi_o =
+        clover_half(st, ro, hf, half_axpy(rho_o, block_hops<T>(st, ns, ro, s_r, pkO, 0, hf, i, np, s_x), T(-1)));
+    __syncthreads();
+
+    // ---- outputs: solution, block residual (r on even, 0 on odd), faces
+    constexpr int PS = PsiPrec<P>::value;
+    typedef typename std::conditional<PS == P64, double, float>::type TS;
+    const Spinor<T> x_full = pair_full_s(x, hf, i, np, s_x);
+    const Spinor<T> chio_full = pair_full_s(chi_o, hf, i, np, s_x);
+    const Spinor<T> r_full = pair_full_s(r, hf, i, np, s_x);
+    if (act) {
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        const int rs = half ? ro : re;
+        const Half<T>& chi = half ? chi_o : x;
+        Half<TS> v;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v.c[s][c] = {(TS)chi.c[s][c].re, (TS)chi.c[s][c].im};
+        if (a.psi_mode == 1 || a.psi_mode == 3) v = half_axpy(v, g_half<PS, TS>(rhs_psi(a, rr), Vb, blk, rs, hf), TS(1));
+        if (a.psi_mode <= 1) {
+          g_half_store<PS, TS>(rhs_psi(a, rr), Vb, blk, rs, hf, v);
+        } else if (a.io32) {
+          Half<float> fv;
+#pragma unroll
+          for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) fv.c[s][c] = {(float)v.c[s][c].re, (float)v.c[s][c].im};
+          g_half_store<P32, float>(rhs_out(a, rr), Vb, blk, rs, hf, fv);
+        } else {
+          g_half_store<P64, TS>(rhs_out(a, rr), Vb, blk, rs, hf, v);  // widened on the integer pipes
+        }
+      }
+      if (a.write_rho && hf == 0) {
+        store_spinor<P, T>(rhs_rho(a, rr), Vb, blk, re, r_full);
+        Spinor<T> z;
+        zero(z);
+        store_spinor<P, T>(rhs_rho(a, rr), Vb, blk, ro, z);
+      }
+      if (a.faces_out) {
+        send_faces<T>(a, rhs_faces(a, rr), st, blk, re, ye, n, x_full, hf);
+        send_faces<T>(a, rhs_faces(a, rr), st, blk, ro, yo, n, chio_full, hf);
+      }
+    }
   }
 }
 
@@ -983,7 +1051,10 @@ static int sap_vb_key(int Vb) { return Vb == 256 || Vb == 512 ? Vb : 0; }
 
 template <int P, typename T, int VB>
 static int set_smem_attr_vb(size_t smem) {
-  QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P, T, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P, T, VB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  QCD_CUDA(cudaFuncSetAttribute(sap_sweep_kernel<P, T, VB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
   return QCD_OK;
 }
 
@@ -998,29 +1069,32 @@ static int set_smem_attr(const Geom& g, int maxsm) {
   return set_smem_attr_vb<P, T, 0>(smem);
 }
 
-// launch one colour half-sweep; 16-bit block fields of 4^4 and 8 x 4^3 blocks
-// run the instantiation for their volume
-template <int P, typename T>
-static void sap_launch(const Geom& g, unsigned grid, int threads, cudaStream_t s, const SapArgs& a) {
-  const size_t smem = sap_smem_bytes<P, T>(g);
-  if constexpr (P == P16 || P == PB16) {
-    if (sap_vb_key(g.Vb) == 256) {
-      sap_sweep_kernel<P, T, 256><<<grid, threads, smem, s>>>(a);
-      return;
-    }
-    if (sap_vb_key(g.Vb) == 512) {
-      sap_sweep_kernel<P, T, 512><<<grid, threads, smem, s>>>(a);
-      return;
-    }
-  }
-  sap_sweep_kernel<P, T, 0><<<grid, threads, smem, s>>>(a);
+template <int P, typename T, int VB>
+static void sap_launch_vb(dim3 grid, int threads, size_t smem, cudaStream_t s, const SapArgs& a) {
+  if (a.nrhs > 1 || a.mask)
+    sap_sweep_kernel<P, T, VB, true><<<grid, threads, smem, s>>>(a);
+  else
+    sap_sweep_kernel<P, T, VB, false><<<grid, threads, smem, s>>>(a);
 }
 
-// allocate the SAP work fields and set the kernel's shared-memory limit for
-// this geometry (outside any stream capture)
-int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s) {
+// launch one colour half-sweep; 16-bit block fields of 4^4 and 8 x 4^3 blocks
+// run the instantiation for their volume, single right-hand sides the
+// untiled one
+template <int P, typename T>
+static void sap_launch(const Geom& g, dim3 grid, int threads, cudaStream_t s, const SapArgs& a) {
+  const size_t smem = sap_smem_bytes<P, T>(g);
+  if constexpr (P == P16 || P == PB16) {
+    if (sap_vb_key(g.Vb) == 256) return sap_launch_vb<P, T, 256>(grid, threads, smem, s, a);
+    if (sap_vb_key(g.Vb) == 512) return sap_launch_vb<P, T, 512>(grid, threads, smem, s, a);
+  }
+  sap_launch_vb<P, T, 0>(grid, threads, smem, s, a);
+}
+
+// allocate the SAP work fields for nr right-hand sides and set the kernel's
+// shared-memory limit for this geometry (outside any stream capture)
+int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s, int nr) {
   const Geom& g = c->g;
-  if (prec < P64 || prec > PB16) return QCD_ERR_ARG;
+  if (prec < P64 || prec > PB16 || nr < 1) return QCD_ERR_ARG;
   if (g.Vbh > 256) return QCD_ERR_UNSUPPORTED;
   QCD_TRY(ensure_gauge(c, prec, s));
   QCD_TRY(ensure_clover(c, prec, s));
@@ -1033,35 +1107,51 @@ int sap_prepare(qcd_ctx* c, SapWork& w, int prec, cudaStream_t s) {
     case P16: QCD_TRY((set_smem_attr<P16, float>(g, maxsm))); break;
     default: QCD_TRY((set_smem_attr<PB16, float>(g, maxsm))); break;
   }
-  if (w.prec == prec) return QCD_OK;
+  if (w.prec == prec && w.nr == nr) return QCD_OK;
   const bool dbl = prec == P64;
   rec_free(w.rho);
   rec_free(w.psi);
   if (w.faces) cudaFree(w.faces);
   w.faces = nullptr;
   w.prec = -1;
-  QCD_TRY(rec_alloc(w.rho, prec, 24, c->V));
-  QCD_TRY(rec_alloc(w.psi, dbl ? P64 : P32, 24, c->V));
+  w.nr = 0;
+  QCD_TRY(rec_alloc(w.rho, prec, 24, c->V * nr));
+  QCD_TRY(rec_alloc(w.psi, dbl ? P64 : P32, 24, c->V * nr));
   int F = 0;
   for (int mu = 0; mu < 4; ++mu) F += 2 * (g.Vb / g.b[mu]);
-  w.faces_bytes = (size_t)c->nblk * F * 12 * (dbl ? 8 : 4);
+  w.faces_bytes = (size_t)c->nblk * F * 12 * (dbl ? 8 : 4) * nr;
   if (cudaMalloc(&w.faces, w.faces_bytes) != cudaSuccess) {
     cudaGetLastError();
     w.faces = nullptr;
     return QCD_ERR_NOMEM;
   }
   w.prec = prec;
+  w.nr = nr;
   return QCD_OK;
 }
 
-// psi = M_SAP eta (both FP64 or both FP32 fields); allocates nothing once
-// sap_prepare ran for prec
+// right-hand sides per CTA of the SAP launch: the context's tuned value, else
+// the largest tile that still gives every SM four CTAs of work per launch
+int sap_tile(qcd_ctx* c, int nr) {
+  if (nr <= 1) return 1;
+  if (c->sap_rt > 0) return c->sap_rt < nr ? c->sap_rt : nr;
+  const long long per_rhs = c->nblk / 2;
+  int rt = 1;
+  while (rt < nr && per_rhs * ((nr + 2 * rt - 1) / (2 * rt)) >= 4 * 152) rt *= 2;
+  return rt;
+}
+
+// psi = M_SAP eta (both FP64 or both FP32 fields) for every right-hand side of
+// B (fields V sites apart; B.mask skips right-hand sides); allocates nothing
+// once sap_prepare ran for prec and B.n
 int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec,
-              cudaStream_t s) {
+              cudaStream_t s, const Batch& B, int rt) {
   const Geom& g = c->g;
-  if (eta64.prec != psi64.prec || (eta64.prec != P64 && eta64.prec != P32)) return QCD_ERR_ARG;
-  if (ncy < 1 || nmr < 0) return QCD_ERR_ARG;
-  if (w.prec != prec) QCD_TRY(sap_prepare(c, w, prec, s));
+  const bool df_in = eta64.prec == PDF && psi64.prec == P64;
+  if (!df_in && (eta64.prec != psi64.prec || (eta64.prec != P64 && eta64.prec != P32))) return QCD_ERR_ARG;
+  if (ncy < 1 || nmr < 0 || B.n < 1) return QCD_ERR_ARG;
+  if (w.prec != prec || w.nr != B.n) QCD_TRY(sap_prepare(c, w, prec, s, B.n));
+  if (rt < 1) rt = sap_tile(c, B.n);
   const bool dbl = prec == P64;
   SapArgs a;
   a.g = g;
@@ -1069,6 +1159,7 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
   a.U = c->U[prec];
   a.Ahat = c->Ahat[prec].ptr();
   a.io32 = eta64.prec == P32;
+  a.io_df = df_in;
   a.eta = eta64.ptr();
   a.rho = w.rho.ptr();
   a.psi = w.psi.ptr();
@@ -1085,14 +1176,27 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
     off += g.Vb / g.b[mu];
   }
   a.F = off;
-  const unsigned grid = (unsigned)(c->nblk / 2);
+  a.nrhs = B.n;
+  a.rt = rt;
+  a.mask = B.mask;
+  a.eta_rs = (long long)c->V * (a.io32 ? 96 : 192);
+  a.out_rs = a.eta_rs;
+  a.rho_rs = (long long)c->V * chunks(prec, 24) * 16;
+  a.rho_ns = w.rho.norm ? c->V : 0;
+  a.psi_rs = (long long)c->V * (dbl ? 192 : 96);
+  a.faces_rs = (long long)c->nblk * a.F * 12 * (dbl ? 8 : 4);
+  const dim3 grid((unsigned)(c->nblk / 2), (unsigned)((B.n + rt - 1) / rt));
   const int threads = 2 * pairs_per_half(g.Vbh);  // two threads per site pair, halves warp-aligned
   // flops (the 1320 + 504 convention): per solved site the Schur operator
   // costs about one D per MR step, plus about one more D for the source and
   // the back-substitution
-  const double flops = (double)(nmr + 1) * 1824.0 * (double)c->V / 2.0;
+  const double flops = (double)(nmr + 1) * 1824.0 * (double)c->V / 2.0 * B.n;
   const double sb = dbl ? 8 : (prec == P32 ? 4 : 2);
-  const double bytes = (double)c->V / 2 * (4 * (dbl ? 18 : 12) * sb + 72 * sb + 2 * 24 * sb + 2 * 24 * (dbl ? 8 : 4));
+  // algorithmic bytes: links and clover of the solved blocks once per tile,
+  // residual and solution in and out per right-hand side
+  const double tiles = (double)((B.n + rt - 1) / rt);
+  const double bytes = (double)c->V / 2 *
+                       ((4 * (dbl ? 18 : 12) * sb + 72 * sb) * tiles + (2 * 24 * sb + 2 * 24 * (dbl ? 8 : 4)) * B.n);
   for (int cy = 0; cy < ncy; ++cy)
     for (int colour = 0; colour < 2; ++colour) {
       const int h = 2 * cy + colour;

@@ -48,17 +48,25 @@ def test_full_size_sap(orc, full):
     assert rel(psi, ref) < 5e-3
 
 
-def test_full_size_solve(orc, full):
-    """The benchmarked solve (FP16 block fields, FP64 recursion, tolerance
-    1e-10): its true residual, recomputed with the oracle's operator, and its
-    solution against the oracle's (unpreconditioned FP64 GCR(16) to 1e-12)."""
+@pytest.fixture(scope="module")
+def full_solution(orc, full):
+    """The oracle's solution: unpreconditioned FP64 GCR(16) to 1e-12."""
     U, A, b, lat = full
-    x, info = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec="f16", outer_prec="f64")
+    x_or, _, _, conv, res_or = orc.fgcr(DIMS, U, A, AP, b, nkv=16, tol=1e-12, max_restarts=400)
+    assert conv and res_or <= 1e-12
+    return x_or
+
+
+@pytest.mark.parametrize("outer_prec", ["f64", "df64"])
+def test_full_size_solve(orc, full, full_solution, outer_prec):
+    """The benchmarked solve (FP16 block fields, tolerance 1e-10) with the FP64
+    and the double-float recursion: its true residual, recomputed with the
+    oracle's operator, and its solution against the oracle's."""
+    U, A, b, lat = full
+    x, info = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec="f16", outer_prec=outer_prec)
     assert info[0]["status"] == 0
     x = x.cpu().numpy()
     res = np.linalg.norm(b - orc.apply_D(DIMS, U, A, AP, x)) / np.linalg.norm(b)
     assert res <= 1.05e-10
     assert abs(res - info[0]["true_residual"]) < 1e-12
-    x_or, _, _, conv, res_or = orc.fgcr(DIMS, U, A, AP, b, nkv=16, tol=1e-12, max_restarts=400)
-    assert conv and res_or <= 1e-12
-    assert rel(x, x_or) < 1e-8
+    assert rel(x, full_solution) < 1e-8

@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 AP = synth.ANTIPERIODIC_T
-TOL_D = {"f64": 1e-12, "f32": 1e-5, "f16": 5e-3, "bf16": 5e-3}
+TOL_D = {"f64": 1e-12, "f32": 1e-5, "f16": 5e-3, "bf16": 5e-3, "df64": 1e-12}
 
 
 def _setup(dims, block, eps, seed, m0, csw, bc=AP):
@@ -41,7 +41,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[0])))
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16", "df64"])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_dirac_parity(orc, case, prec, dagger):
     dims, block, eps, seed, m0, csw, bc = case
@@ -129,13 +129,16 @@ def _oracle_residual(orc, dims, U, A, b, x):
     return np.linalg.norm(r) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("sap_prec", ["f64", "f32", "f16"])
-def test_solve_44_matches_oracle(orc, sap_prec):
-    """The 4^4 workload: SAP (2^4 blocks, 4 MR steps, 4 cycles) + FGCR(16)."""
+@pytest.mark.parametrize("sap_prec,outer_prec", [("f64", "f64"), ("f32", "f64"), ("f16", "f64"), ("f64", "df64"),
+                                                  ("f16", "df64")])
+def test_solve_44_matches_oracle(orc, sap_prec, outer_prec):
+    """The 4^4 workload: SAP (2^4 blocks, 4 MR steps, 4 cycles) + FGCR(16),
+    with the FP64 or the double-float recursion."""
     w = synth.WORKLOADS["4^4 fp64"]
     dims = w["dims"]
     lat, U, A, b = _setup(dims, w["block"], w["eps"], w["seed"], w["m0"], w["csw"])
-    x, info = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec=sap_prec, ncy=4, nmr=4, nkv=16)
+    x, info = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec=sap_prec, ncy=4, nmr=4, nkv=16,
+                        outer_prec=outer_prec)
     x = x.cpu().numpy()
     assert info[0]["status"] == 0 and info[0]["true_residual"] <= 1e-10
     assert _oracle_residual(orc, dims, U, A, b, x) <= 1.05e-10
@@ -237,6 +240,27 @@ def test_resident_field_multi_rhs(orc, prec):
         assert rel(out[k], orc.apply_D(dims, U, A, AP, b[k])) < TOL_D[prec]
     binding.qcd_field_free(fi)
     binding.qcd_field_free(fo)
+    lat.close()
+
+
+@pytest.mark.parametrize("sap_prec", ["f16", "bf16"])
+def test_solve_16x32_df64_recursion(orc, solved_16x32, sap_prec):
+    """The double-float recursion (Gram-Schmidt, dots and updates on pairs of
+    FP32 values, FP64 operator, FP64 restart residual and solution): true
+    residual below 1e-10 and the oracle's solution to 1e-8."""
+    w, U, A, b, x_or = solved_16x32
+    dims = w["dims"]
+    from paper_1109_4279_gb300 import binding
+    lat = binding.Lattice(dims, w["block"], w["m0"], w["csw"])
+    lat.load_gauge(torch.from_numpy(U).cuda())
+    x, info = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec=sap_prec, outer_prec="df64")
+    assert info[0]["status"] == 0, info
+    x = x.cpu().numpy()
+    assert _oracle_residual(orc, dims, U, A, b, x) <= 1.05e-10
+    assert rel(x, x_or) < 1e-8
+    # the same iteration count as the FP64 recursion
+    _, info64 = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec=sap_prec, outer_prec="f64")
+    assert abs(info64[0]["iterations"] - info[0]["iterations"]) <= 1
     lat.close()
 
 
