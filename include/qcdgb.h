@@ -67,9 +67,8 @@ extern "C" {
 #define QCD_PREC_F16 2   /* IEEE FP16 storage with a per-site FP32 scale, FP32 arithmetic */
 #define QCD_PREC_BF16 3  /* bfloat16 storage with a per-site FP32 scale, FP32 arithmetic */
 #define QCD_PREC_DF64 4  /* double-float: pairs of FP32 values (hi + lo, a 48-bit significand) computed
-                            with error-free transformations on the FP32 units; the FGCR recursion
-                            (outer_prec) and the result of qcd_apply_D (an FP64 apply, result stored
-                            as pairs) only */
+                            with error-free transformations on the FP32 units; for the FGCR recursion
+                            (outer_prec) and qcd_apply_D only */
 
 /* preconditioners */
 #define QCD_PRECOND_NONE 0  /* plain GCR */
@@ -106,9 +105,10 @@ typedef struct {
     int sap_prec;      /* precision of the SAP block fields: QCD_PREC_F64/F32/F16/BF16 */
     int outer_prec;    /* precision of the FGCR recursion (Sec. 4):
                           QCD_PREC_F64 (default): rho, phi_k, chi_k = D phi_k, Gram-Schmidt and dots in FP64;
-                          QCD_PREC_DF64: chi_k = D phi_k by the FP64 operator, rho, chi_k, the Gram-Schmidt
-                          dots and updates in double-float arithmetic on the FP32 units (GB300 runs FP64 at
-                          1/64 of its FP32 rate); phi_k, the solution update and the restart residual FP64;
+                          QCD_PREC_DF64: rho, phi_k, chi_k = D phi_k (links and clover as pairs too), the
+                          Gram-Schmidt dots and updates and the solution increment in double-float arithmetic
+                          on the FP32 units (GB300 runs FP64 at 1/64 of its FP32 rate); the solution and the
+                          restart residual r = b - D x in FP64;
                           QCD_PREC_F32: iterative refinement -- each restart cycle runs the whole recursion
                           in FP32 on the normalised residual r / |r| until its residual has dropped by
                           inner_tol (or the target is met), then the FP32 correction is added to the FP64
@@ -181,8 +181,9 @@ int qcd_build_clover(qcd_ctx* ctx, void* stream);
  * in/out: device pointers to nrhs * (V, 4, 3) complex128 (must not alias).
  * prec: QCD_PREC_F64 applies in FP64; F32/F16/BF16 convert the input to that
  * storage, apply with FP32 arithmetic and convert the result back;
- * QCD_PREC_DF64 applies in FP64 and passes the result through the
- * double-float storage of the df64 recursion.
+ * QCD_PREC_DF64 converts the input to double-float pairs and applies the
+ * double-float operator of the df64 recursion (FP32 units, about 2^-46
+ * relative rounding), converting the result back.
  * Errors: QCD_ERR_STATE, QCD_ERR_ARG.
  */
 int qcd_apply_D(qcd_ctx* ctx, const double* in, double* out, int dagger, int prec, int nrhs, void* stream);

@@ -164,7 +164,7 @@ void qcd_destroy(qcd_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   workspace_free(c);
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < 5; ++p) {
     if (c->U[p]) cudaFree(c->U[p]);
     rec_free(c->A[p]);
     rec_free(c->Ahat[p]);
@@ -212,7 +212,7 @@ int qcd_apply_D(qcd_ctx* c, const double* in, double* out, int dagger, int prec,
   if (!c->clover_built) return QCD_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   Rec a, b;
-  int st = rec_alloc(a, prec == PDF ? P64 : prec, 24, c->V * nrhs);
+  int st = rec_alloc(a, prec, 24, c->V * nrhs);
   if (st == QCD_OK) st = rec_alloc(b, prec, 24, c->V * nrhs);
   if (st == QCD_OK) st = import_spinor(c, in, a, nrhs, s);
   if (st == QCD_OK) st = dirac_apply(c, a, b, dagger, s, nrhs);

@@ -410,19 +410,6 @@ __global__ void backsub_kernel(const double* a1, const double* a2, const double*
 // multiply-add instead of one FP64 fused multiply-add, on pipes 64 times
 // faster.  Per-thread sums go to FP64 for the CTA and grid reductions.
 // ------------------------------------------------------------------------
-struct dfacc {
-  float s, c;  // running sum, collected lower-order terms
-};
-
-// a += x y for double-floats x = (xh, xl), y = (yh, yl)
-__device__ __forceinline__ void acc_prod(dfacc& a, float xh, float xl, float yh, float yl) {
-  const df p = two_prod(xh, yh);
-  const df t = two_sum(a.s, p.hi);
-  a.s = t.hi;
-  a.c += t.lo + fmaf(xh, yl, fmaf(xl, yh, p.lo));
-}
-__device__ __forceinline__ double acc_value(const dfacc& a) { return f32_to_f64(a.s) + f32_to_f64(a.c); }
-__device__ __forceinline__ df acc_df(const dfacc& a) { return two_sum(a.s, a.c); }
 
 // (re, im) += conj(a) b
 __device__ __forceinline__ void df_dot_acc(const float4& a, const float4& b, dfacc& re, dfacc& im) {
@@ -551,6 +538,36 @@ __global__ void __launch_bounds__(kBlasThreads)
     df_nrm_acc(r, acc[0]);
   }
   df_reduce_store<1>(acc, part);
+}
+
+// x64 += sum_j g_j phi_j with double-float phi_j: the sum formed in
+// double-float arithmetic, added to the FP64 solution once (one FP64 addition
+// per real instead of 4 k fused multiply-adds)
+template <int K>
+__global__ void __launch_bounds__(kBlasThreads)
+    df_update_kernel(VecList<float4> vl, int k, const double* __restrict__ gam, double2* __restrict__ x, long long n,
+                     BatchDev bd, int koff) {
+  if (rhs_skipped(bd)) return;
+  const long long ro = blockIdx.y * bd.vs;
+  x += ro;
+  gam += blockIdx.y * bd.ss;
+  if (bd.k) k = min(k, max(0, bd.k[blockIdx.y] - koff));
+  df gr[K], gi[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    gr[j] = j < k ? df_from_f64(gam[2 * j]) : df{0.f, 0.f};
+    gi[j] = j < k ? df_from_f64(gam[2 * j + 1]) : df{0.f, 0.f};
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    dfacc tr = {0.f, 0.f}, ti = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j < k) df_cmul_acc(gr[j], gi[j], __ldg(vl.v[j] + ro + i), tr, ti);
+    double2 v = x[i];
+    v.x += acc_value(tr);
+    v.y += acc_value(ti);
+    x[i] = v;
+  }
 }
 
 // out = the double-float split of an FP64 field (same element order)
@@ -945,6 +962,29 @@ int blas_df_normalise_update(qcd_ctx* c, double* part, float4* chi, float4* rho,
     QCD_LAUNCHED();
   }
   return reduce_partials(part, (int)grid, 1, 1, d_out, s, B);
+}
+
+int blas_df_update(qcd_ctx* c, const float4* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s,
+                   const Batch& B) {
+  const long long n = c->V * 12;
+  const unsigned grid = blas_grid(n);
+  const dim3 g2(grid, B.n);
+  const BatchDev bd = dev_of(B, n);
+  int done = 0;
+  while (done < k) {
+    const int kk = k - done < 16 ? k - done : 16;
+    auto vl = make_df_list(phi + done, kk);
+    ProfScope ps(c, QCD_KERNEL_BLAS, s, 16.0 * (double)n * (kk + 2) * B.n, 8.0 * c->V * 12 * kk * B.n);
+    if (kk <= 4)
+      df_update_kernel<4><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, n, bd, done);
+    else if (kk <= 8)
+      df_update_kernel<8><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, n, bd, done);
+    else
+      df_update_kernel<16><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, n, bd, done);
+    QCD_LAUNCHED();
+    done += kk;
+  }
+  return QCD_OK;
 }
 
 int blas_df_split(qcd_ctx* c, const double* in, float* out, cudaStream_t s, const Batch& B) {

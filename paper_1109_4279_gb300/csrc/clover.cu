@@ -196,7 +196,7 @@ __global__ void clover_build_kernel(Geom g, const double2* __restrict__ U64, dou
 int build_clover(qcd_ctx* c, cudaStream_t s) {
   if (!c->gauge_loaded) return QCD_ERR_STATE;
   ++c->gen;  // every clover record is reallocated
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < 5; ++p) {
     rec_free(c->A[p]);
     rec_free(c->Ahat[p]);
   }

@@ -346,6 +346,231 @@ __global__ void __launch_bounds__(2 * kPairSites, QCD_PAIR_MIN_CTAS) dirac_pair_
   }
 }
 
+// ------------------------------------------------------------------------
+// The operator in double-float arithmetic: spinors, links (all 18 reals) and
+// clover as (hi, lo) pairs of FP32 values (the FP64 layouts with float4 =
+// (re hi, re lo, im hi, im lo) per complex number), computed on the FP32
+// units with error-free transformations.  Every output real is a double-float
+// running sum (dfacc); a hop's projection adds pairs by TwoSum, its SU(3)
+// product accumulates exact FP32 products and their cross terms, its
+// expansion and the -1/2 (a power of two) are exact.  About 12 FP32 operations
+// per real multiply-add in place of one FP64 fused multiply-add, on units 64
+// times faster on GB300; the result agrees with the FP64 operator to about
+// 2^-46 relative.
+// ------------------------------------------------------------------------
+struct cdf {
+  df re, im;
+};
+__device__ __forceinline__ cdf cdf_of(const float4& v) { return {{v.x, v.y}, {v.z, v.w}}; }
+// x + y without the final renormalisation (a valid double-float operand)
+__device__ __forceinline__ df dsum(df x, df y) {
+  df t = two_sum(x.hi, y.hi);
+  t.lo += x.lo + y.lo;
+  return t;
+}
+__device__ __forceinline__ cdf cplus(const cdf& x, const cdf& y) { return {dsum(x.re, y.re), dsum(x.im, y.im)}; }
+__device__ __forceinline__ cdf cminus(const cdf& x, const cdf& y) {
+  return {dsum(x.re, df_neg(y.re)), dsum(x.im, df_neg(y.im))};
+}
+__device__ __forceinline__ cdf ctimes_i(const cdf& z) { return {df_neg(z.im), z.re}; }   // i z
+__device__ __forceinline__ cdf ctimes_mi(const cdf& z) { return {z.im, df_neg(z.re)}; }  // -i z
+
+// (ar, ai) += u h and (ar, ai) += conj(u) h
+__device__ __forceinline__ void cmac_df(dfacc& ar, dfacc& ai, const cdf& u, const cdf& h) {
+  acc_prod(ar, u.re.hi, u.re.lo, h.re.hi, h.re.lo);
+  acc_prod(ar, -u.im.hi, -u.im.lo, h.im.hi, h.im.lo);
+  acc_prod(ai, u.re.hi, u.re.lo, h.im.hi, h.im.lo);
+  acc_prod(ai, u.im.hi, u.im.lo, h.re.hi, h.re.lo);
+}
+__device__ __forceinline__ void cjmac_df(dfacc& ar, dfacc& ai, const cdf& u, const cdf& h) {
+  acc_prod(ar, u.re.hi, u.re.lo, h.re.hi, h.re.lo);
+  acc_prod(ar, u.im.hi, u.im.lo, h.im.hi, h.im.lo);
+  acc_prod(ai, u.re.hi, u.re.lo, h.im.hi, h.im.lo);
+  acc_prod(ai, -u.im.hi, -u.im.lo, h.re.hi, h.re.lo);
+}
+
+struct SpinAcc {
+  dfacc re[4][3], im[4][3];
+};
+
+// acc[s][c] += f z for f = +-1/2 (exact) and a lazily summed z = (zr, zi)
+__device__ __forceinline__ void acc_cadd(SpinAcc& a, int s, int c, float f, const dfacc& zr, const dfacc& zi) {
+  acc_add(a.re[s][c], f * zr.s, f * zr.c);
+  acc_add(a.im[s][c], f * zi.s, f * zi.c);
+}
+// acc[s][c] += f i z
+__device__ __forceinline__ void acc_cadd_i(SpinAcc& a, int s, int c, float f, const dfacc& zr, const dfacc& zi) {
+  acc_add(a.re[s][c], -f * zi.s, -f * zi.c);
+  acc_add(a.im[s][c], f * zr.s, f * zr.c);
+}
+
+// the projection of project<MU, S> on double-float spinors
+template <int MU, int S>
+__device__ __forceinline__ void project_df(const cdf (&p)[4][3], cdf (&h)[2][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (MU == 0) {
+      h[0][a] = S > 0 ? cminus(p[0][a], p[2][a]) : cplus(p[0][a], p[2][a]);
+      h[1][a] = S > 0 ? cminus(p[1][a], p[3][a]) : cplus(p[1][a], p[3][a]);
+    } else if (MU == 1) {
+      h[0][a] = cplus(p[0][a], S > 0 ? ctimes_mi(p[3][a]) : ctimes_i(p[3][a]));
+      h[1][a] = cplus(p[1][a], S > 0 ? ctimes_mi(p[2][a]) : ctimes_i(p[2][a]));
+    } else if (MU == 2) {
+      h[0][a] = S > 0 ? cminus(p[0][a], p[3][a]) : cplus(p[0][a], p[3][a]);
+      h[1][a] = S > 0 ? cplus(p[1][a], p[2][a]) : cminus(p[1][a], p[2][a]);
+    } else {
+      h[0][a] = cplus(p[0][a], S > 0 ? ctimes_mi(p[2][a]) : ctimes_i(p[2][a]));
+      h[1][a] = cplus(p[1][a], S > 0 ? ctimes_i(p[3][a]) : ctimes_mi(p[3][a]));
+    }
+  }
+}
+
+// acc += coef [w ; S B^+ w] (the expansion of expand_add<MU, S>) for the
+// lazily summed w = (wr, wi)
+template <int MU, int S>
+__device__ __forceinline__ void expand_df(SpinAcc& acc, const dfacc (&wr)[2][3], const dfacc (&wi)[2][3], float coef) {
+  const float f = S > 0 ? coef : -coef;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc_cadd(acc, 0, a, coef, wr[0][a], wi[0][a]);
+    acc_cadd(acc, 1, a, coef, wr[1][a], wi[1][a]);
+    if (MU == 0) {
+      acc_cadd(acc, 2, a, -f, wr[0][a], wi[0][a]);
+      acc_cadd(acc, 3, a, -f, wr[1][a], wi[1][a]);
+    } else if (MU == 1) {
+      acc_cadd_i(acc, 2, a, f, wr[1][a], wi[1][a]);
+      acc_cadd_i(acc, 3, a, f, wr[0][a], wi[0][a]);
+    } else if (MU == 2) {
+      acc_cadd(acc, 2, a, f, wr[1][a], wi[1][a]);
+      acc_cadd(acc, 3, a, -f, wr[0][a], wi[0][a]);
+    } else {
+      acc_cadd_i(acc, 2, a, f, wr[0][a], wi[0][a]);
+      acc_cadd_i(acc, 3, a, -f, wr[1][a], wi[1][a]);
+    }
+  }
+}
+
+__device__ __forceinline__ void load_spinor_df(const FieldPtr& f, int Vb, int blk, int r, cdf (&p)[4][3]) {
+  const float4* d = (const float4*)f.data + (long long)blk * 12 * Vb + r;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) p[k / 3][k % 3] = cdf_of(__ldg(d + (long long)k * Vb));
+}
+
+// one direction's two hops of the double-float operator (as hop_pair)
+template <int MU, int DAG>
+__device__ __forceinline__ void hop_pair_df(const Geom& g, const float4* __restrict__ U, const FieldPtr& in, int blk,
+                                            int r, const int y[4], const int n[4], SpinAcc& acc) {
+  constexpr int SF = DAG ? +1 : -1;
+#pragma unroll
+  for (int dir = 0; dir < 2; ++dir) {
+    const Nbr nb = neighbour(g, blk, y, n, MU, dir == 0 ? +1 : -1);
+    cdf h[2][3];
+    {
+      cdf p[4][3];
+      load_spinor_df(in, g.Vb, nb.blk, nb.r, p);
+      if (dir == 0)
+        project_df<MU, SF>(p, h);
+      else
+        project_df<MU, -SF>(p, h);
+    }
+    // the link of the forward hop is the site's own, of the backward hop the neighbour's
+    const float4* d = U + ((long long)((dir == 0 ? blk : nb.blk) * 4 + MU) * 9) * g.Vb + (dir == 0 ? r : nb.r);
+    dfacc wr[2][3], wi[2][3];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) wr[sp][a] = wi[sp][a] = dfacc{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        // forward: w_a += U_ab h_b; backward: w_a += conj(U_ba) h_b
+        const cdf u = cdf_of(__ldg(d + (long long)(dir == 0 ? 3 * a + b : 3 * b + a) * g.Vb));
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+          if (dir == 0)
+            cmac_df(wr[sp][a], wi[sp][a], u, h[sp][b]);
+          else
+            cjmac_df(wr[sp][a], wi[sp][a], u, h[sp][b]);
+        }
+      }
+    const float coef = nb.wrap ? -0.5f * g.bcf[MU] : -0.5f;
+    if (dir == 0)
+      expand_df<MU, SF>(acc, wr, wi, coef);
+    else
+      expand_df<MU, -SF>(acc, wr, wi, coef);
+  }
+}
+
+template <int DAG>
+__global__ void __launch_bounds__(256, 2) dirac_df_kernel(Geom g, const float4* __restrict__ U, FieldPtr A, FieldPtr in,
+                                                       FieldPtr out, int nrhs, const int* __restrict__ mask) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
+  int n[4], y[4];
+  block_coords(g, blk, n);
+  {
+    const int packed = __ldg(g.r2y + r);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) y[mu] = ycoord(packed, mu);
+  }
+#pragma unroll 1
+  for (int k = 0; k < nrhs; ++k) {
+    if (mask && !mask[k]) continue;
+    FieldPtr fi = in, fo = out;
+    fi.data = (char*)in.data + (size_t)k * g.V * 12 * 16;
+    fo.data = (char*)out.data + (size_t)k * g.V * 12 * 16;
+    SpinAcc acc;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc.re[sp][c] = acc.im[sp][c] = dfacc{0.f, 0.f};
+    hop_pair_df<0, DAG>(g, U, fi, blk, r, y, n, acc);
+    hop_pair_df<1, DAG>(g, U, fi, blk, r, y, n, acc);
+    hop_pair_df<2, DAG>(g, U, fi, blk, r, y, n, acc);
+    hop_pair_df<3, DAG>(g, U, fi, blk, r, y, n, acc);
+    // clover: two Hermitian 6x6 chiral blocks (6 diagonal reals, then the 15
+    // upper off-diagonal elements), record chunk 18 hb + j = reals 36 hb + 2 j, + 1
+    {
+      cdf psi[4][3];
+      load_spinor_df(fi, g.Vb, blk, r, psi);
+      const float4* ca = (const float4*)A.data + (long long)blk * 36 * g.Vb + r;
+#pragma unroll
+      for (int hb = 0; hb < 2; ++hb) {
+#pragma unroll
+        for (int i = 0; i < 6; i += 2) {  // diagonal reals i, i + 1
+          const float4 dv = __ldg(ca + (long long)(18 * hb + i / 2) * g.Vb);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int ii = i + q, sp = 2 * hb + ii / 3, c = ii % 3;
+            const float dh = q ? dv.z : dv.x, dl = q ? dv.w : dv.y;
+            acc_prod(acc.re[sp][c], dh, dl, psi[sp][c].re.hi, psi[sp][c].re.lo);
+            acc_prod(acc.im[sp][c], dh, dl, psi[sp][c].im.hi, psi[sp][c].im.lo);
+          }
+        }
+        int kk = 3;
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int j = i + 1; j < 6; ++j) {
+            const cdf a = cdf_of(__ldg(ca + (long long)(18 * hb + kk) * g.Vb));
+            ++kk;
+            const int si = 2 * hb + i / 3, ci = i % 3, sj = 2 * hb + j / 3, cj = j % 3;
+            cmac_df(acc.re[si][ci], acc.im[si][ci], a, psi[sj][cj]);
+            cjmac_df(acc.re[sj][cj], acc.im[sj][cj], a, psi[si][ci]);
+          }
+      }
+    }
+    float4* o = (float4*)fo.data + (long long)blk * 12 * g.Vb + r;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const df re = acc_df(acc.re[q / 3][q % 3]), im = acc_df(acc.im[q / 3][q % 3]);
+      o[(long long)q * g.Vb] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+  }
+}
+
 // deterministic block sum of a double: warp shuffles, then warps in order
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll
@@ -402,6 +627,22 @@ static double bytes_per_site(int prec) {
 
 int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s, int nrhs, const int* mask) {
   const int prec = in.prec;
+  if (prec == PDF) {  // double-float in and out: the double-float operator
+    if (out.prec != PDF || in.nreal != 24 || out.nreal != 24 || nrhs < 1) return QCD_ERR_ARG;
+    QCD_TRY(ensure_gauge(c, PDF, s));
+    QCD_TRY(ensure_clover(c, PDF, s));
+    const int threads = c->dirac_threads[PDF];
+    const unsigned grid = (unsigned)((c->V + threads - 1) / threads);
+    ProfScope ps(c, QCD_KERNEL_DIRAC, s, (bytes_per_site(P64) + 2 * 192.0) * (double)c->V * nrhs,
+                 1824.0 * (double)c->V * nrhs);
+    const float4* U = (const float4*)c->U[PDF];
+    if (dagger)
+      dirac_df_kernel<1><<<grid, threads, 0, s>>>(c->g, U, c->A[PDF].ptr(), in.ptr(), out.ptr(), nrhs, mask);
+    else
+      dirac_df_kernel<0><<<grid, threads, 0, s>>>(c->g, U, c->A[PDF].ptr(), in.ptr(), out.ptr(), nrhs, mask);
+    QCD_LAUNCHED();
+    return QCD_OK;
+  }
   // FP64 in and double-float out: the FP64 operator with its result split
   const int out_df = prec == P64 && out.prec == PDF;
   if ((out.prec != prec && !out_df) || in.nreal != 24 || out.nreal != 24 || nrhs < 1) return QCD_ERR_ARG;

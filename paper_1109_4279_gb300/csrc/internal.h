@@ -156,10 +156,12 @@ struct qcd_ctx {
   long long V = 0;
   int nblk = 0;
   bool gauge_loaded = false, clover_built = false;
-  void* U[4] = {nullptr, nullptr, nullptr, nullptr};  // gauge in each precision (lazy)
-  size_t U_bytes[4] = {0, 0, 0, 0};
-  qcd::Rec A[4];     // clover (4 + m0 + c_sw term), 72 reals per site
-  qcd::Rec Ahat[4];  // SAP block clover: A on even sites, A^-1 on odd sites
+  // gauge field and clover in each storage precision (built lazily); index
+  // PDF: the double-float copies of the df64 operator
+  void* U[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t U_bytes[5] = {0, 0, 0, 0, 0};
+  qcd::Rec A[5];     // clover (4 + m0 + c_sw term), 72 reals per site
+  qcd::Rec Ahat[5];  // SAP block clover: A on even sites, A^-1 on odd sites
   qcd::Workspace* ws = nullptr;
   qcd::Workspace* tile_ws = nullptr;       // right-hand sides solved together by batched launches
   std::vector<qcd::Workspace*> batch_ws;  // extra right-hand sides of a multi-RHS solve (one workspace each)
@@ -169,9 +171,9 @@ struct qcd_ctx {
   qcd::Timer timers[QCD_KERNEL_COUNT];
   std::vector<cudaEvent_t> event_pool;
   // launch shape chosen by the autotuner
-  int dirac_threads[4] = {256, 256, 256, 256};  // CTA size of the operator kernel per precision
+  int dirac_threads[5] = {256, 256, 256, 256, 256};  // CTA size of the operator kernel per precision
   int sap_rt = 0;  // right-hand sides per CTA of batched SAP launches (0: sap_tile's default)
-  int dirac_tps[4] = {1, 1, 1, 1};  // threads per site of the operator kernel (2: 16-bit storage only)
+  int dirac_tps[5] = {1, 1, 1, 1, 1};  // threads per site of the operator kernel (2: 16-bit storage only)
   double* d_scalars = nullptr;  // small device array for coefficients
   double* h_scalars = nullptr;  // pinned host mirror
   // test hooks (qcd_debug_set): budget of the SAP staging wait, and bytes its
@@ -304,6 +306,9 @@ int blas_df_axpy_norm_dot(qcd_ctx* c, double* part, const float4* const* v, int 
                           const Batch& B = Batch());
 int blas_df_normalise_update(qcd_ctx* c, double* part, float4* chi, float4* rho, const double* d_gs, int two_pass,
                              double* d_cr, double* d_out, cudaStream_t s, const Batch& B = Batch());
+// x (FP64) += sum_j gamma_j phi_j for double-float phi_j (B.k: per-RHS counts)
+int blas_df_update(qcd_ctx* c, const float4* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s,
+                   const Batch& B = Batch());
 // FP64 field <-> double-float field (same internal layout)
 int blas_df_split(qcd_ctx* c, const double* in, float* out, cudaStream_t s, const Batch& B = Batch());
 int blas_df_join(qcd_ctx* c, const float* in, double* out, cudaStream_t s, const Batch& B = Batch());

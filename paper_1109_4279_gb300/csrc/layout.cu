@@ -200,7 +200,7 @@ int load_gauge_device(qcd_ctx* c, const double* lex_dev, cudaStream_t s) {
       return QCD_ERR_NOMEM;
     }
   }
-  for (int p = 1; p < 4; ++p)
+  for (int p = 1; p < 5; ++p)
     if (c->U[p]) {
       cudaFree(c->U[p]);
       c->U[p] = nullptr;
@@ -251,13 +251,22 @@ __global__ void gauge_compress_kernel(Geom g, const double2* __restrict__ U64, v
   }
 }
 
+// FP64 links -> double-float pairs (element by element, same layout)
+__global__ void gauge_split_kernel(const double2* __restrict__ in, float4* __restrict__ out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = in[i];
+  const df a = df_from_f64(v.x), b = df_from_f64(v.y);
+  out[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
 int ensure_gauge(qcd_ctx* c, int prec, cudaStream_t s) {
   if (!c->gauge_loaded) return QCD_ERR_STATE;
   if (c->U[prec]) return QCD_OK;
   ++c->gen;
-  size_t bytes = (size_t)c->V * (prec == P64 ? GaugeLayout<P64>::bytes_per_site
-                                             : (prec == P32 ? GaugeLayout<P32>::bytes_per_site
-                                                            : GaugeLayout<P16>::bytes_per_site));
+  size_t bytes = (size_t)c->V * ((prec == P64 || prec == PDF) ? GaugeLayout<P64>::bytes_per_site
+                                 : (prec == P32 ? GaugeLayout<P32>::bytes_per_site
+                                                : GaugeLayout<P16>::bytes_per_site));
   if (cudaMalloc(&c->U[prec], bytes) != cudaSuccess) {
     c->U[prec] = nullptr;
     return QCD_ERR_NOMEM;
@@ -269,6 +278,11 @@ int ensure_gauge(qcd_ctx* c, int prec, cudaStream_t s) {
     case P32: gauge_compress_kernel<P32><<<grid, 256, 0, s>>>(c->g, U64, c->U[prec]); break;
     case P16: gauge_compress_kernel<P16><<<grid, 256, 0, s>>>(c->g, U64, c->U[prec]); break;
     case PB16: gauge_compress_kernel<PB16><<<grid, 256, 0, s>>>(c->g, U64, c->U[prec]); break;
+    case PDF: {  // all 18 reals of every link as double-float pairs, FP64 order
+      const long long n = c->V * 4 * 9;
+      gauge_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U64, (float4*)c->U[prec], n);
+      break;
+    }
     default: return QCD_ERR_ARG;
   }
   QCD_LAUNCHED();
@@ -283,7 +297,7 @@ __global__ void convert_kernel(int Vb, long long V, FieldPtr in, FieldPtr out) {
   long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= V) return;
   int blk = (int)(s / Vb), r = (int)(s - (long long)blk * Vb);
-  if constexpr (PI == P64 && PO == P64) {
+  if constexpr (PI == P64 && (PO == P64 || PO == PDF)) {
     double v[N];
     load_record<PI, N, double>(in, Vb, blk, r, v);
     store_record<PO, N, double>(out, Vb, blk, r, v);
@@ -319,7 +333,7 @@ static int convert_n(qcd_ctx* c, const Rec& in, const Rec& out, cudaStream_t s) 
     QCD_LAUNCHED();                                                      \
     return QCD_OK;                                                                     \
   }
-  CV(P64, P64) CV(P64, P32) CV(P64, P16) CV(P64, PB16)
+  CV(P64, P64) CV(P64, P32) CV(P64, P16) CV(P64, PB16) CV(P64, PDF)
   CV(P32, P64) CV(P32, P32) CV(P32, P16) CV(P32, PB16)
   CV(P16, P64) CV(P16, P32) CV(PB16, P64) CV(PB16, P32)
 #undef CV

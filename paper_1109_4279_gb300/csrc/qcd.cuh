@@ -110,6 +110,29 @@ __device__ __forceinline__ df df_fma(df x, df y, df z) {
   return fast_two_sum(s.hi, s.lo);
 }
 
+// A double-float running sum for long dot products: the high parts of the
+// terms are added by TwoSum, every lower-order term (a product's rounding
+// error, the cross terms, the sums' errors) is collected in c.  Neither part
+// is renormalised until the value is read.
+struct dfacc {
+  float s, c;
+};
+// a += x y for double-floats x = (xh, xl), y = (yh, yl) (xl yl dropped)
+__device__ __forceinline__ void acc_prod(dfacc& a, float xh, float xl, float yh, float yl) {
+  const df p = two_prod(xh, yh);
+  const df t = two_sum(a.s, p.hi);
+  a.s = t.hi;
+  a.c += t.lo + fmaf(xh, yl, fmaf(xl, yh, p.lo));
+}
+// a += (hi, lo)
+__device__ __forceinline__ void acc_add(dfacc& a, float hi, float lo) {
+  const df t = two_sum(a.s, hi);
+  a.s = t.hi;
+  a.c += t.lo + lo;
+}
+__device__ __forceinline__ double acc_value(const dfacc& a) { return f32_to_f64(a.s) + f32_to_f64(a.c); }
+__device__ __forceinline__ df acc_df(const dfacc& a) { return two_sum(a.s, a.c); }
+
 // ------------------------------------------------------------------------
 // complex arithmetic
 // ------------------------------------------------------------------------

@@ -34,7 +34,7 @@ struct SapArgs {
   int nmr;              // MR steps per block
   int read_eta;         // residual source: 1 = eta, 0 = rho_sap
   int io32;             // eta and out are FP32 fields (else FP64)
-  int io_df;            // eta is a double-float field (read as its FP32 high parts); out FP64
+  int io_df;            // eta and out are double-float fields (eta read as its FP32 high parts)
   int faces_in;         // add face contributions of the other colour
   int faces_out;        // write this block's face contributions
   int write_rho;        // store the block residual
@@ -667,6 +667,23 @@ __device__ __forceinline__ Half<T> g_half_df(const FieldPtr& f, int Vb, int blk,
   return h;
 }
 
+// store an owned half into a double-float field: FP32 values are exact high
+// parts (low parts 0); FP64 values are split
+template <typename T>
+__device__ __forceinline__ void g_half_store_df(const FieldPtr& f, int Vb, int blk, int r, int hf, const Half<T>& h) {
+  float4* d = (float4*)f.data + ((long long)blk * 12 + 6 * hf) * Vb + r;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const cpx<T> v = h.c[k / 3][k % 3];
+    if constexpr (sizeof(T) == 8) {
+      const df a = df_from_f64(v.re), b = df_from_f64(v.im);
+      d[(long long)k * Vb] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    } else {
+      d[(long long)k * Vb] = make_float4(v.re, 0.f, v.im, 0.f);
+    }
+  }
+}
+
 // owned half of a 16-bit spinor record ([blk][3 chunks][Vb] uint4 of 8 reals,
 // complex k at chunk k / 4): half hf is chunk 2 hf and the hf-th 8-byte half of
 // chunk 1, scaled by the site's norm
@@ -1014,6 +1031,8 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
         if (a.psi_mode == 1 || a.psi_mode == 3) v = half_axpy(v, g_half<PS, TS>(rhs_psi(a, rr), Vb, blk, rs, hf), TS(1));
         if (a.psi_mode <= 1) {
           g_half_store<PS, TS>(rhs_psi(a, rr), Vb, blk, rs, hf, v);
+        } else if (a.io_df) {
+          g_half_store_df<TS>(rhs_out(a, rr), Vb, blk, rs, hf, v);
         } else if (a.io32) {
           Half<float> fv;
 #pragma unroll
@@ -1147,7 +1166,7 @@ int sap_tile(qcd_ctx* c, int nr) {
 int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec,
               cudaStream_t s, const Batch& B, int rt) {
   const Geom& g = c->g;
-  const bool df_in = eta64.prec == PDF && psi64.prec == P64;
+  const bool df_in = eta64.prec == PDF && psi64.prec == PDF;
   if (!df_in && (eta64.prec != psi64.prec || (eta64.prec != P64 && eta64.prec != P32))) return QCD_ERR_ARG;
   if (ncy < 1 || nmr < 0 || B.n < 1) return QCD_ERR_ARG;
   if (w.prec != prec || w.nr != B.n) QCD_TRY(sap_prepare(c, w, prec, s, B.n));
@@ -1179,7 +1198,7 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
   a.nrhs = B.n;
   a.rt = rt;
   a.mask = B.mask;
-  a.eta_rs = (long long)c->V * (a.io32 ? 96 : 192);
+  a.eta_rs = (long long)c->V * (a.io32 ? 96 : 192);  // FP64 and double-float fields: 192 B per site
   a.out_rs = a.eta_rs;
   a.rho_rs = (long long)c->V * chunks(prec, 24) * 16;
   a.rho_ns = w.rho.norm ? c->V : 0;

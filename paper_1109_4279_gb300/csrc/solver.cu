@@ -99,9 +99,7 @@ static void fields_free(Workspace& w) {
 int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream_t s, int nr) {
   const int nkv = sp.nkv;
   const int rprec = sp.outer_prec == P32 ? P32 : (sp.outer_prec == PDF ? PDF : P64);
-  // phi_k (the preconditioner's output, the operator's input) is FP64 in the
-  // double-float recursion: the FP64 operator and solution update read it
-  const int pprec = rprec == PDF ? P64 : rprec;
+  const int pprec = rprec;  // phi_k: the preconditioner's output, the operator's input
   if (nr < 1) return QCD_ERR_ARG;
   if (w.nr != nr) {  // the number of right-hand sides changes: reallocate every field
     fields_free(w);
@@ -160,7 +158,7 @@ int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream
   }
   QCD_TRY(ensure_gauge(c, P64, s));
   QCD_TRY(ensure_clover(c, P64, s));
-  if (rprec == P32) {
+  if (rprec != P64) {  // the outer operator's links and clover in the recursion's precision
     QCD_TRY(ensure_gauge(c, rprec, s));
     QCD_TRY(ensure_clover(c, rprec, s));
   }
@@ -253,8 +251,6 @@ static int enqueue_iteration(Group& G, const qcd_solver_params& sp, int k) {
   if (sp.precond == QCD_PRECOND_SAP) {
     NvtxRange nv("sap");
     QCD_TRY(sap_apply(c, w.sap, w.rho, w.phi[k], sp.ncy, sp.nmr, sp.sap_prec, s, B, G.rt));
-  } else if (w.rprec == PDF) {
-    QCD_TRY(blas_df_join(c, (const float*)w.rho.data, (double*)w.phi[k].data, s, batch_of(w, nullptr)));
   } else {
     QCD_CUDA(cudaMemcpyAsync(w.phi[k].data, w.rho.data, w.rho.bytes, cudaMemcpyDeviceToDevice, s));
   }
@@ -540,6 +536,10 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
         for (int j = 0; j < kmax; ++j) phi_p[j] = (const float*)w.phi[j].data;
         const double* rn2 = w.d_rn + w.nkv + (cycles == 0 ? 1 : 2);
         st = blas_refine_update(G.c, phi_p, kmax, w.d_gam, rn2, (double*)w.x.data, G.s, B);
+      } else if (st == QCD_OK && w.rprec == PDF) {
+        const float4* phi_p[64];
+        for (int j = 0; j < kmax; ++j) phi_p[j] = (const float4*)w.phi[j].data;
+        st = blas_df_update(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B);
       } else if (st == QCD_OK) {
         const double* phi_p[64];
         for (int j = 0; j < kmax; ++j) phi_p[j] = (const double*)w.phi[j].data;
