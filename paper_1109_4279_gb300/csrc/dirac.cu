@@ -404,107 +404,20 @@ __device__ __forceinline__ void acc_cadd_i(SpinAcc& a, int s, int c, float f, co
   acc_add(a.im[s][c], f * zr.s, f * zr.c);
 }
 
-// the projection of project<MU, S> on double-float spinors
-template <int MU, int S>
-__device__ __forceinline__ void project_df(const cdf (&p)[4][3], cdf (&h)[2][3]) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (MU == 0) {
-      h[0][a] = S > 0 ? cminus(p[0][a], p[2][a]) : cplus(p[0][a], p[2][a]);
-      h[1][a] = S > 0 ? cminus(p[1][a], p[3][a]) : cplus(p[1][a], p[3][a]);
-    } else if (MU == 1) {
-      h[0][a] = cplus(p[0][a], S > 0 ? ctimes_mi(p[3][a]) : ctimes_i(p[3][a]));
-      h[1][a] = cplus(p[1][a], S > 0 ? ctimes_mi(p[2][a]) : ctimes_i(p[2][a]));
-    } else if (MU == 2) {
-      h[0][a] = S > 0 ? cminus(p[0][a], p[3][a]) : cplus(p[0][a], p[3][a]);
-      h[1][a] = S > 0 ? cplus(p[1][a], p[2][a]) : cminus(p[1][a], p[2][a]);
-    } else {
-      h[0][a] = cplus(p[0][a], S > 0 ? ctimes_mi(p[2][a]) : ctimes_i(p[2][a]));
-      h[1][a] = cplus(p[1][a], S > 0 ? ctimes_i(p[3][a]) : ctimes_mi(p[3][a]));
-    }
-  }
+// z times a phase +-1 or +-i: (im ? i z : z) * sg
+__device__ __forceinline__ cdf cphase(const cdf& z, bool im, float sg) {
+  const df re = im ? df_neg(z.im) : z.re, imv = im ? z.re : z.im;
+  return {{sg * re.hi, sg * re.lo}, {sg * imv.hi, sg * imv.lo}};
 }
 
-// acc += coef [w ; S B^+ w] (the expansion of expand_add<MU, S>) for the
-// lazily summed w = (wr, wi)
-template <int MU, int S>
-__device__ __forceinline__ void expand_df(SpinAcc& acc, const dfacc (&wr)[2][3], const dfacc (&wi)[2][3], float coef) {
-  const float f = S > 0 ? coef : -coef;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    acc_cadd(acc, 0, a, coef, wr[0][a], wi[0][a]);
-    acc_cadd(acc, 1, a, coef, wr[1][a], wi[1][a]);
-    if (MU == 0) {
-      acc_cadd(acc, 2, a, -f, wr[0][a], wi[0][a]);
-      acc_cadd(acc, 3, a, -f, wr[1][a], wi[1][a]);
-    } else if (MU == 1) {
-      acc_cadd_i(acc, 2, a, f, wr[1][a], wi[1][a]);
-      acc_cadd_i(acc, 3, a, f, wr[0][a], wi[0][a]);
-    } else if (MU == 2) {
-      acc_cadd(acc, 2, a, f, wr[1][a], wi[1][a]);
-      acc_cadd(acc, 3, a, -f, wr[0][a], wi[0][a]);
-    } else {
-      acc_cadd_i(acc, 2, a, f, wr[0][a], wi[0][a]);
-      acc_cadd_i(acc, 3, a, -f, wr[1][a], wi[1][a]);
-    }
-  }
-}
-
-__device__ __forceinline__ void load_spinor_df(const FieldPtr& f, int Vb, int blk, int r, cdf (&p)[4][3]) {
-  const float4* d = (const float4*)f.data + (long long)blk * 12 * Vb + r;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) p[k / 3][k % 3] = cdf_of(__ldg(d + (long long)k * Vb));
-}
-
-// one direction's two hops of the double-float operator (as hop_pair)
-template <int MU, int DAG>
-__device__ __forceinline__ void hop_pair_df(const Geom& g, const float4* __restrict__ U, const FieldPtr& in, int blk,
-                                            int r, const int y[4], const int n[4], SpinAcc& acc) {
-  constexpr int SF = DAG ? +1 : -1;
-#pragma unroll
-  for (int dir = 0; dir < 2; ++dir) {
-    const Nbr nb = neighbour(g, blk, y, n, MU, dir == 0 ? +1 : -1);
-    cdf h[2][3];
-    {
-      cdf p[4][3];
-      load_spinor_df(in, g.Vb, nb.blk, nb.r, p);
-      if (dir == 0)
-        project_df<MU, SF>(p, h);
-      else
-        project_df<MU, -SF>(p, h);
-    }
-    // the link of the forward hop is the site's own, of the backward hop the neighbour's
-    const float4* d = U + ((long long)((dir == 0 ? blk : nb.blk) * 4 + MU) * 9) * g.Vb + (dir == 0 ? r : nb.r);
-    dfacc wr[2][3], wi[2][3];
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) wr[sp][a] = wi[sp][a] = dfacc{0.f, 0.f};
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        // forward: w_a += U_ab h_b; backward: w_a += conj(U_ba) h_b
-        const cdf u = cdf_of(__ldg(d + (long long)(dir == 0 ? 3 * a + b : 3 * b + a) * g.Vb));
-#pragma unroll
-        for (int sp = 0; sp < 2; ++sp) {
-          if (dir == 0)
-            cmac_df(wr[sp][a], wi[sp][a], u, h[sp][b]);
-          else
-            cjmac_df(wr[sp][a], wi[sp][a], u, h[sp][b]);
-        }
-      }
-    const float coef = nb.wrap ? -0.5f * g.bcf[MU] : -0.5f;
-    if (dir == 0)
-      expand_df<MU, SF>(acc, wr, wi, coef);
-    else
-      expand_df<MU, -SF>(acc, wr, wi, coef);
-  }
-}
-
+// The eight hops share one loop body (direction, projection sign and link
+// conjugation chosen at run time), and the two clover blocks another: the
+// double-float arithmetic is long, and unrolled over every hop it would not
+// fit the instruction cache.
 template <int DAG>
-__global__ void __launch_bounds__(256, 2) dirac_df_kernel(Geom g, const float4* __restrict__ U, FieldPtr A, FieldPtr in,
-                                                       FieldPtr out, int nrhs, const int* __restrict__ mask) {
+__global__ void __launch_bounds__(256, 2) dirac_df_kernel(Geom g, const float4* __restrict__ U, FieldPtr A,
+                                                          FieldPtr in, FieldPtr out, int nrhs,
+                                                          const int* __restrict__ mask) {
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   const int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
@@ -515,54 +428,139 @@ __global__ void __launch_bounds__(256, 2) dirac_df_kernel(Geom g, const float4* 
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) y[mu] = ycoord(packed, mu);
   }
+  // the eight neighbours: blocks, sites and boundary signs (hop h: mu = h / 2,
+  // forward for even h), computed with compile-time directions
+  int nbk[8], nbr[8];
+  float coef[8];
+#pragma unroll
+  for (int h = 0; h < 8; ++h) {
+    const Nbr nb = neighbour(g, blk, y, n, h / 2, (h & 1) ? -1 : +1);
+    nbk[h] = nb.blk;
+    nbr[h] = nb.r;
+    coef[h] = nb.wrap ? -0.5f * g.bcf[h / 2] : -0.5f;
+  }
+  constexpr float SF = DAG ? 1.f : -1.f;  // D: (1 - g) psi(x + mu); D^+: (1 + g) psi(x + mu)
 #pragma unroll 1
   for (int k = 0; k < nrhs; ++k) {
     if (mask && !mask[k]) continue;
-    FieldPtr fi = in, fo = out;
-    fi.data = (char*)in.data + (size_t)k * g.V * 12 * 16;
-    fo.data = (char*)out.data + (size_t)k * g.V * 12 * 16;
+    const float4* fin = (const float4*)in.data + (size_t)k * g.V * 12;
+    float4* fout = (float4*)out.data + (size_t)k * g.V * 12;
     SpinAcc acc;
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc.re[sp][c] = acc.im[sp][c] = dfacc{0.f, 0.f};
-    hop_pair_df<0, DAG>(g, U, fi, blk, r, y, n, acc);
-    hop_pair_df<1, DAG>(g, U, fi, blk, r, y, n, acc);
-    hop_pair_df<2, DAG>(g, U, fi, blk, r, y, n, acc);
-    hop_pair_df<3, DAG>(g, U, fi, blk, r, y, n, acc);
-    // clover: two Hermitian 6x6 chiral blocks (6 diagonal reals, then the 15
-    // upper off-diagonal elements), record chunk 18 hb + j = reals 36 hb + 2 j, + 1
-    {
-      cdf psi[4][3];
-      load_spinor_df(fi, g.Vb, blk, r, psi);
-      const float4* ca = (const float4*)A.data + (long long)blk * 36 * g.Vb + r;
+#pragma unroll 1
+    for (int h = 0; h < 8; ++h) {
+      const int mu = h >> 1, bwd = h & 1;
+      // select this hop's neighbour from the unrolled table without indexing it
+      int hb = nbk[0], hr = nbr[0];
+      float cf = coef[0];
 #pragma unroll
-      for (int hb = 0; hb < 2; ++hb) {
-#pragma unroll
-        for (int i = 0; i < 6; i += 2) {  // diagonal reals i, i + 1
-          const float4 dv = __ldg(ca + (long long)(18 * hb + i / 2) * g.Vb);
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int ii = i + q, sp = 2 * hb + ii / 3, c = ii % 3;
-            const float dh = q ? dv.z : dv.x, dl = q ? dv.w : dv.y;
-            acc_prod(acc.re[sp][c], dh, dl, psi[sp][c].re.hi, psi[sp][c].re.lo);
-            acc_prod(acc.im[sp][c], dh, dl, psi[sp][c].im.hi, psi[sp][c].im.lo);
-          }
+      for (int q = 1; q < 8; ++q)
+        if (h == q) {
+          hb = nbk[q];
+          hr = nbr[q];
+          cf = coef[q];
         }
-        int kk = 3;
+      // chiral-basis projection (1 + S g_mu): h_i = p_i + S ph_i p_{sigma_i}, with
+      // sigma = (2, 3) or (3, 2) and phases -1 / -i (see SpinDir)
+      const bool swap = mu == 1 || mu == 2;
+      const bool im0 = mu == 1 || mu == 3, im1 = im0;
+      const float sg0 = -1.f, sg1 = (mu >= 2) ? 1.f : -1.f;
+      const float S = bwd ? -SF : SF;
+      cdf hh[2][3];
+      {
+        const float4* d = fin + (long long)hb * 12 * g.Vb + hr;
 #pragma unroll
-        for (int i = 0; i < 6; ++i)
+        for (int a = 0; a < 3; ++a) {
+          const cdf p0 = cdf_of(__ldg(d + (long long)a * g.Vb)), p1 = cdf_of(__ldg(d + (long long)(3 + a) * g.Vb));
+          const cdf p2 = cdf_of(__ldg(d + (long long)(6 + a) * g.Vb)), p3 = cdf_of(__ldg(d + (long long)(9 + a) * g.Vb));
+          hh[0][a] = cplus(p0, cphase(swap ? p3 : p2, im0, S * sg0));
+          hh[1][a] = cplus(p1, cphase(swap ? p2 : p3, im1, S * sg1));
+        }
+      }
+      // w = U h (forward, the site's link) or U^+ h (backward, the neighbour's link)
+      const float4* ud = U + ((long long)((bwd ? hb : blk) * 4 + mu) * 9) * g.Vb + (bwd ? hr : r);
+      const float cj = bwd ? -1.f : 1.f;
+      dfacc wr[2][3], wi[2][3];
 #pragma unroll
-          for (int j = i + 1; j < 6; ++j) {
-            const cdf a = cdf_of(__ldg(ca + (long long)(18 * hb + kk) * g.Vb));
-            ++kk;
-            const int si = 2 * hb + i / 3, ci = i % 3, sj = 2 * hb + j / 3, cj = j % 3;
-            cmac_df(acc.re[si][ci], acc.im[si][ci], a, psi[sj][cj]);
-            cjmac_df(acc.re[sj][cj], acc.im[sj][cj], a, psi[si][ci]);
-          }
+      for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) wr[sp][a] = wi[sp][a] = dfacc{0.f, 0.f};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          cdf u = cdf_of(__ldg(ud + (long long)(bwd ? 3 * b + a : 3 * a + b) * g.Vb));
+          u.im = {cj * u.im.hi, cj * u.im.lo};
+#pragma unroll
+          for (int sp = 0; sp < 2; ++sp) cmac_df(wr[sp][a], wi[sp][a], u, hh[sp][b]);
+        }
+      // acc += cf [w ; S B^+ w]: B^+ w has components conj(ph_i) w_i on spins sigma_i
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        acc_cadd(acc, 0, a, cf, wr[0][a], wi[0][a]);
+        acc_cadd(acc, 1, a, cf, wr[1][a], wi[1][a]);
+        // l_i = S cf conj(ph_i) w_i: conj of a real phase is itself, of -i is +i
+        const float f0 = S * cf * (im0 ? -sg0 : sg0), f1 = S * cf * (im1 ? -sg1 : sg1);
+        dfacc l0r = wr[0][a], l0i = wi[0][a], l1r = wr[1][a], l1i = wi[1][a];
+        if (im0) {  // times i: (re, im) -> (-im, re)
+          l0r = {-wi[0][a].s, -wi[0][a].c};
+          l0i = wr[0][a];
+          l1r = {-wi[1][a].s, -wi[1][a].c};
+          l1i = wr[1][a];
+        }
+        acc_cadd(acc, 2, a, swap ? f1 : f0, swap ? l1r : l0r, swap ? l1i : l0i);
+        acc_cadd(acc, 3, a, swap ? f0 : f1, swap ? l0r : l1r, swap ? l0i : l1i);
       }
     }
-    float4* o = (float4*)fo.data + (long long)blk * 12 * g.Vb + r;
+    // clover: two Hermitian 6x6 chiral blocks (6 diagonal reals, then the 15
+    // upper off-diagonal elements), record chunk 18 hb + j = reals 36 hb + 2 j, + 1
+    const float4* ca = (const float4*)A.data + (long long)blk * 36 * g.Vb + r;
+    const float4* psid = fin + (long long)blk * 12 * g.Vb + r;
+#pragma unroll 1
+    for (int hb = 0; hb < 2; ++hb) {
+      cdf psi[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) psi[i] = cdf_of(__ldg(psid + (long long)(6 * hb + i) * g.Vb));
+      dfacc tr[6], ti[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) tr[i] = ti[i] = dfacc{0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < 6; i += 2) {  // diagonal reals i, i + 1
+        const float4 dv = __ldg(ca + (long long)(18 * hb + i / 2) * g.Vb);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int ii = i + q;
+          const float dh = q ? dv.z : dv.x, dl = q ? dv.w : dv.y;
+          acc_prod(tr[ii], dh, dl, psi[ii].re.hi, psi[ii].re.lo);
+          acc_prod(ti[ii], dh, dl, psi[ii].im.hi, psi[ii].im.lo);
+        }
+      }
+      int kk = 3;
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 6; ++j) {
+          const cdf a = cdf_of(__ldg(ca + (long long)(18 * hb + kk) * g.Vb));
+          ++kk;
+          cmac_df(tr[i], ti[i], a, psi[j]);
+          cjmac_df(tr[j], ti[j], a, psi[i]);
+        }
+      // into spins 2 hb, 2 hb + 1
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        if (hb == 0) {
+          acc_add(acc.re[i / 3][i % 3], tr[i].s, tr[i].c);
+          acc_add(acc.im[i / 3][i % 3], ti[i].s, ti[i].c);
+        } else {
+          acc_add(acc.re[2 + i / 3][i % 3], tr[i].s, tr[i].c);
+          acc_add(acc.im[2 + i / 3][i % 3], ti[i].s, ti[i].c);
+        }
+      }
+    }
+    float4* o = fout + (long long)blk * 12 * g.Vb + r;
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
       const df re = acc_df(acc.re[q / 3][q % 3]), im = acc_df(acc.im[q / 3][q % 3]);
