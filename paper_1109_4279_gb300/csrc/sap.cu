@@ -583,11 +583,17 @@ __device__ __forceinline__ void cta_sum3(T& a, T& b, T& c, T* red) {
     red[3 * w + 2] = c;
   }
   __syncthreads();
-  a = b = c = T(0);
-  for (int k = 0; k < nw; ++k) {
-    a += red[3 * k];
-    b += red[3 * k + 1];
-    c += red[3 * k + 2];
+  // lane k of every warp takes warp k's partial sums; a butterfly over the
+  // lanes leaves every thread the totals, summed in the same order everywhere
+  const int l = threadIdx.x & 31;
+  a = l < nw ? red[3 * l] : T(0);
+  b = l < nw ? red[3 * l + 1] : T(0);
+  c = l < nw ? red[3 * l + 2] : T(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
   }
   // no closing barrier: red is written again only after later barriers
 }
@@ -1051,8 +1057,17 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
         store_spinor<P, T>(rhs_rho(a, rr), Vb, blk, ro, z);
       }
       if (a.faces_out) {
-        send_faces<T>(a, rhs_faces(a, rr), st, blk, re, ye, n, x_full, hf);
-        send_faces<T>(a, rhs_faces(a, rr), st, blk, ro, yo, n, chio_full, hf);
+        // the coordinates again (cheaper than keeping 12 registers through the MR steps)
+        int n2[4], ye2[4], yo2[4];
+        block_coords(g, blk, n2);
+        const int pe = g.r2y[re], po = g.r2y[ro];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          ye2[mu] = ycoord(pe, mu);
+          yo2[mu] = ycoord(po, mu);
+        }
+        send_faces<T>(a, rhs_faces(a, rr), st, blk, re, ye2, n2, x_full, hf);
+        send_faces<T>(a, rhs_faces(a, rr), st, blk, ro, yo2, n2, chio_full, hf);
       }
     }
   }
