@@ -285,9 +285,10 @@ int qcd_hmc_trajectory(qcd_ctx* ctx, double* U, double* pi, const double* eta, d
 
 /*
  * Pick, by timing on the device, the fastest launch shape of the operator
- * kernel for each storage precision of this context -- CTA size, and for
- * 16-bit storage one or two threads per site -- and, for nrhs > 1, the
- * right-hand-side tile of the batched SAP sweep (timed on FP16 block fields);
+ * kernel for each storage precision of this context (double-float included)
+ * -- CTA size, and for 16-bit storage one or two threads per site -- and, for
+ * nrhs > 1, the right-hand-side tile of the batched SAP sweep (timed on FP16
+ * block fields);
  * keep the choices in the context (see qcd_set_launch, qcd_set_sap_tile).
  * nrhs: right-hand sides per call the tuning should reflect (the operator
  * timing applies that many operators back to back).  cache_path (may be
@@ -316,13 +317,14 @@ int qcd_tune_block(const qcd_params* p, const double* U, const double* b, int is
 
 /*
  * Launch shapes (what qcd_autotune chooses), for callers that pin them:
- * qcd_set_launch sets, for storage precision prec, the operator kernel's CTA
- * size `threads` (a multiple of 32, 32..1024) and its threads per site `tps`:
- * 1, or 2 for 16-bit storage (QCD_PREC_F16 / BF16: two threads share a site,
- * each taking two of the four directions and half of the spin components, in
- * CTAs of 256; QCD_ERR_UNSUPPORTED for FP32/FP64).  qcd_get_launch reads the
- * current shape.  qcd_set_sap_tile sets how many right-hand sides one CTA of a
- * batched SAP sweep solves with one staging of its block's fields (1..64; 0
+ * qcd_set_launch sets, for storage precision prec (QCD_PREC_F64 .. DF64), the
+ * operator kernel's CTA size `threads` (a multiple of 32, 32..1024; at most
+ * 256 for DF64) and its threads per site `tps`: 1, or 2 for 16-bit storage
+ * (QCD_PREC_F16 / BF16: two threads share a site, each taking two of the four
+ * directions and half of the spin components, in CTAs of 256;
+ * QCD_ERR_UNSUPPORTED otherwise).  qcd_get_launch reads the current shape.
+ * qcd_set_sap_tile sets how many right-hand sides one CTA of a batched SAP
+ * sweep solves with one staging of its block's fields (1..64; 0
  * restores the default: the largest tile that keeps four CTAs per SM);
  * qcd_get_sap_tile returns the tile a solve of nrhs right-hand sides uses.
  * Results do not depend on any of these.

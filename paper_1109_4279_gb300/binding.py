@@ -340,6 +340,7 @@ def qcd_set_launch(ctx, prec, threads, tps=1):
 
 
 def qcd_get_launch(ctx, prec):
+    """(threads, threads per site) of the operator for one precision."""
     t, p = ctypes.c_int(), ctypes.c_int()
     check(lib().qcd_get_launch(ctx, PREC[prec], ctypes.byref(t), ctypes.byref(p)), "qcd_get_launch")
     return t.value, p.value

@@ -687,10 +687,11 @@ int qcd_sap_apply_n(qcd_ctx* c, const double* eta, double* psi, int nrhs, int rt
 }
 
 int qcd_set_launch(qcd_ctx* c, int prec, int threads, int tps) {
-  if (!c || prec < 0 || prec > 3) return QCD_ERR_ARG;
+  if (!c || prec < 0 || prec > 4) return QCD_ERR_ARG;
   if (tps != 1 && tps != 2) return QCD_ERR_ARG;
   if (tps == 2 && prec != QCD_PREC_F16 && prec != QCD_PREC_BF16) return QCD_ERR_UNSUPPORTED;
-  if (threads < 32 || threads > 1024 || threads % 32) return QCD_ERR_ARG;
+  // the double-float operator is compiled for CTAs of at most 256 threads
+  if (threads < 32 || threads > (prec == QCD_PREC_DF64 ? 256 : 1024) || threads % 32) return QCD_ERR_ARG;
   ++c->gen;  // captured graphs hold the launch shape
   c->dirac_threads[prec] = threads;
   c->dirac_tps[prec] = tps;
@@ -698,7 +699,7 @@ int qcd_set_launch(qcd_ctx* c, int prec, int threads, int tps) {
 }
 
 int qcd_get_launch(const qcd_ctx* c, int prec, int* threads, int* tps) {
-  if (!c || prec < 0 || prec > 3) return QCD_ERR_ARG;
+  if (!c || prec < 0 || prec > 4) return QCD_ERR_ARG;
   if (threads) *threads = c->dirac_tps[prec] == 2 ? 256 : c->dirac_threads[prec];
   if (tps) *tps = c->dirac_tps[prec];
   return QCD_OK;

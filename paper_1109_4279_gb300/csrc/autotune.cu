@@ -35,15 +35,16 @@ static std::string tune_key(qcd_ctx* c, int nrhs) {
 }
 
 // The cache holds one entry per line:
-//   "key": [t64, t32, t16, tb16, tps16, tpsb16, sap_rt],
-// the operator's CTA size per precision, the threads per site of the 16-bit
-// operators, and the SAP right-hand-side tile (0: default)
-static constexpr int kTuneFields = 7;
+//   "key": [t64, t32, t16, tb16, tdf, tps16, tpsb16, sap_rt],
+// the operator's CTA size per precision (double-float last), the threads per
+// site of the 16-bit operators and the SAP right-hand-side tile (0: default)
+static constexpr int kTuneFields = 8;
 
 static bool tune_valid(const int v[kTuneFields]) {
   for (int i = 0; i < 4; ++i)
     if (v[i] != 128 && v[i] != 256 && v[i] != 512) return false;
-  return (v[4] == 1 || v[4] == 2) && (v[5] == 1 || v[5] == 2) && v[6] >= 0 && v[6] <= 64;
+  if (v[4] != 128 && v[4] != 256) return false;
+  return (v[5] == 1 || v[5] == 2) && (v[6] == 1 || v[6] == 2) && v[7] >= 0 && v[7] <= 64;
 }
 
 static bool cache_lookup(const char* path, const std::string& key, int out[kTuneFields]) {
@@ -57,8 +58,8 @@ static bool cache_lookup(const char* path, const std::string& key, int out[kTune
     const size_t lb = line.find('[', p), rb = line.find(']', p);
     if (lb == std::string::npos || rb == std::string::npos) return false;
     int v[kTuneFields];
-    if (sscanf(line.c_str() + lb + 1, "%d , %d , %d , %d , %d , %d , %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
-               &v[6]) != kTuneFields)
+    if (sscanf(line.c_str() + lb + 1, "%d , %d , %d , %d , %d , %d , %d , %d", &v[0], &v[1], &v[2], &v[3], &v[4],
+               &v[5], &v[6], &v[7]) != kTuneFields)
       return false;
     if (!tune_valid(v)) return false;
     for (int i = 0; i < kTuneFields; ++i) out[i] = v[i];
@@ -91,11 +92,11 @@ static void cache_store(const char* path, const std::string& key, const int v[kT
 }
 
 static void tune_apply(qcd_ctx* c, const int v[kTuneFields]) {
-  for (int p = 0; p < 4; ++p) c->dirac_threads[p] = v[p];
-  c->dirac_tps[P64] = c->dirac_tps[P32] = 1;
-  c->dirac_tps[P16] = v[4];
-  c->dirac_tps[PB16] = v[5];
-  c->sap_rt = v[6];
+  for (int p = 0; p < 5; ++p) c->dirac_threads[p] = v[p];
+  c->dirac_tps[P64] = c->dirac_tps[P32] = c->dirac_tps[PDF] = 1;
+  c->dirac_tps[P16] = v[5];
+  c->dirac_tps[PB16] = v[6];
+  c->sap_rt = v[7];
 }
 
 // mean ms of reps calls of f() after one warm-up, CUDA events on s
@@ -124,7 +125,7 @@ extern "C" int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
   if (!c || nrhs < 1) return QCD_ERR_ARG;
   if (!c->clover_built) return QCD_ERR_STATE;
   const std::string key = tune_key(c, nrhs);
-  int best[kTuneFields] = {256, 256, 256, 256, 1, 1, 0};
+  int best[kTuneFields] = {256, 256, 256, 256, 256, 1, 1, 0};
   ++c->gen;  // the operator's launch shape changes under captured graphs
   if (cache_lookup(cache_path, key, best)) {
     tune_apply(c, best);
@@ -135,16 +136,16 @@ extern "C" int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
   const bool prof = c->prof;
   c->prof = false;
   int st = QCD_OK;
-  // operator: CTA size with one thread per site, and for 16-bit storage the
+  // operator: CTA size with one thread per site, for 16-bit storage also the
   // two-threads-per-site form
   const int cand[4][2] = {{128, 1}, {256, 1}, {512, 1}, {256, 2}};
-  for (int p = P64; p <= PB16 && st == QCD_OK; ++p) {
+  for (int p = P64; p <= PDF && st == QCD_OK; ++p) {
     Rec a, b;
     st = rec_alloc(a, p, 24, c->V * nrhs);
     if (st == QCD_OK) st = rec_alloc(b, p, 24, c->V * nrhs);
     if (st == QCD_OK && cudaMemsetAsync(a.data, 0, a.bytes, s) != cudaSuccess) st = QCD_ERR_CUDA;
     float best_ms = 1e30f;
-    const int ncand = (p == P16 || p == PB16) ? 4 : 3;
+    const int ncand = (p == P16 || p == PB16) ? 4 : (p == PDF ? 2 : 3);
     for (int k = 0; k < ncand && st == QCD_OK; ++k) {
       c->dirac_threads[p] = cand[k][0];
       c->dirac_tps[p] = cand[k][1];
@@ -152,11 +153,11 @@ extern "C" int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
       if (st == QCD_OK && ms < best_ms) {
         best_ms = ms;
         best[p] = cand[k][0];
-        if (p >= P16) best[4 + (p - P16)] = cand[k][1];
+        if (p == P16 || p == PB16) best[5 + (p - P16)] = cand[k][1];
       }
     }
     c->dirac_threads[p] = best[p];
-    c->dirac_tps[p] = p >= P16 ? best[4 + (p - P16)] : 1;
+    c->dirac_tps[p] = (p == P16 || p == PB16) ? best[5 + (p - P16)] : 1;
     rec_free(a);
     rec_free(b);
   }
@@ -177,7 +178,7 @@ extern "C" int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
         const float ms = time_ms(s, 2, [&] { return sap_apply(c, w, eta, psi, 4, 4, P16, s, B, rts[k]); }, &s2);
         if (s2 == QCD_OK && ms < best_ms) {
           best_ms = ms;
-          best[6] = rts[k];
+          best[7] = rts[k];
         }
       }
     }
@@ -190,7 +191,7 @@ extern "C" int qcd_autotune(qcd_ctx* c, int nrhs, const char* cache_path) {
     if (w.faces) cudaFree(w.faces);
     cudaGetLastError();
   }
-  c->sap_rt = best[6];
+  c->sap_rt = best[7];
   c->prof = prof;
   cudaStreamSynchronize(s);
   cudaStreamDestroy(s);

@@ -28,17 +28,17 @@ def test_autotune_cache_and_parity(orc, tmp_path):
     entries = json.load(open(cache))
     assert len(entries) == 1
     (key, vals), = entries.items()
-    # CTA sizes of the four precisions, threads per site of the two 16-bit
-    # operators, SAP right-hand-side tile (0: one right-hand side, default)
-    assert "16x16" in key and len(vals) == 7
-    assert all(v in (128, 256, 512) for v in vals[:4]) and vals[4] in (1, 2) and vals[5] in (1, 2)
-    assert vals[6] == 0
-    assert B.qcd_get_launch(lat.ctx, "f16")[1] == vals[4]
+    # CTA sizes of the five precisions (double-float last), threads per site
+    # of the two 16-bit operators, SAP right-hand-side tile (0: default)
+    assert "16x16" in key and len(vals) == 8
+    assert all(v in (128, 256, 512) for v in vals[:4]) and vals[4] in (128, 256)
+    assert vals[5] in (1, 2) and vals[6] in (1, 2) and vals[7] == 0
+    assert B.qcd_get_launch(lat.ctx, "f16")[:2] == (vals[2] if vals[5] == 1 else 256, vals[5])
     B.qcd_autotune(lat.ctx, 1, cache)  # second call applies the cached entry
     assert json.load(open(cache)) == entries
     A = orc.clover(dims, U, 0.0, 1.5)
     ref = orc.apply_D(dims, U, A, AP, b)
-    for prec, tol in (("f64", 1e-12), ("f32", 1e-5), ("f16", 5e-3)):
+    for prec, tol in (("f64", 1e-12), ("f32", 1e-5), ("f16", 5e-3), ("df64", 1e-12)):
         out = lat.apply_D(torch.from_numpy(b).cuda(), prec=prec).cpu().numpy()
         assert rel(out, ref) < tol
     lat.close()
@@ -99,8 +99,8 @@ def test_autotune_sap_tile_for_many_rhs(tmp_path):
     cache = str(tmp_path / "tune12.json")
     B.qcd_autotune(lat.ctx, 12, cache)
     (key, vals), = json.load(open(cache)).items()
-    assert "nrhs12" in key and vals[6] in (1, 2, 3, 4, 6, 8, 12)
-    assert B.qcd_get_sap_tile(lat.ctx, 12) == vals[6]
+    assert "nrhs12" in key and vals[7] in (1, 2, 3, 4, 6, 8, 12)
+    assert B.qcd_get_sap_tile(lat.ctx, 12) == vals[7]
     B.qcd_set_sap_tile(lat.ctx, 5)
     assert B.qcd_get_sap_tile(lat.ctx, 12) == 5 and B.qcd_get_sap_tile(lat.ctx, 3) == 3
     B.qcd_set_sap_tile(lat.ctx, 0)
