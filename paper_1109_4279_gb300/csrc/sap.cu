@@ -247,22 +247,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, long long budget)
 }
 
 // issue the bulk copies of a block's 16-bit links (to `links`) and clover
-// blocks with their scales (to `clover`), thread 0 only
+// blocks with their scales (to `clover`) on the barrier: every lane of warp 0
+// calls this, lane 0 adds the expected bytes and lane c issues pieces c,
+// c + 32, ... of at most 16 KB
 template <int P>
 __device__ __forceinline__ void stage_issue(const SapArgs& a, int blk, unsigned char* links, unsigned char* clover,
                                             uint64_t* bar) {
-  const int Vb = a.g.Vb;
+  const int Vb = a.g.Vb, lane = threadIdx.x & 31;
   const unsigned char* srcs[3] = {(const unsigned char*)a.U + (size_t)blk * 96 * Vb,
                                   (const unsigned char*)a.Ahat.data + (size_t)blk * 144 * Vb,
                                   (const unsigned char*)(a.Ahat.norm + (size_t)blk * Vb)};
   unsigned char* dsts[3] = {links, clover, clover + 144 * Vb};
   const uint32_t sizes[3] = {(uint32_t)(96 * Vb), (uint32_t)(144 * Vb), (uint32_t)(4 * Vb)};
-  mbar_expect_tx(bar, sizes[0] + sizes[1] + sizes[2] + (uint32_t)a.extra_tx);
-  for (int k = 0; k < 3; ++k)
-    for (uint32_t o = 0; o < sizes[k]; o += 16384) {
-      const uint32_t n = sizes[k] - o < 16384 ? sizes[k] - o : 16384;
+  if (lane == 0) mbar_expect_tx(bar, sizes[0] + sizes[1] + sizes[2] + (uint32_t)a.extra_tx);
+  __syncwarp();
+  int c0 = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int nk = (int)((sizes[k] + 16383) / 16384);
+    for (int c = (lane - c0 % 32 + 32) % 32; c < nk; c += 32) {
+      const uint32_t o = (uint32_t)c * 16384, n = sizes[k] - o < 16384 ? sizes[k] - o : 16384;
       bulk_copy_g2s(dsts[k] + o, srcs[k] + o, n, bar);
     }
+    c0 += nk;
+  }
 }
 
 // rebuild the compressed 16-bit links of the landing zone (rows 0-1, layout of
@@ -712,7 +720,10 @@ __device__ __forceinline__ Half<float> g_half16(const FieldPtr& f, int Vb, int b
 }
 
 // receive the other colour's face contributions at site (blk, r) for the
-// directions of this thread; returns a partial full spinor
+// directions of this thread; returns a partial full spinor.  A site lies on at
+// most one face per direction (block extents are at least 2), so one read per
+// direction serves both kinds of face, and a warp waits for one read per
+// direction however its sites split between the kinds.
 template <typename T, typename ST>
 __device__ __forceinline__ Spinor<T> receive_faces(const SapArgs& a, const void* faces, const ST& st, int blk, int r,
                                                    const int y[4], const int n[4], int hf) {
@@ -725,16 +736,17 @@ __device__ __forceinline__ Spinor<T> receive_faces(const SapArgs& a, const void*
     const SpinDir<T> d = spin_dir<T>(mu);
     const int ymu = mu == 0 ? y[0] : (mu == 1 ? y[1] : (mu == 2 ? y[2] : y[3]));
     const int nmu = mu == 0 ? n[0] : (mu == 1 ? n[1] : (mu == 2 ? n[2] : n[3]));
-    if (ymu == g.b[mu] - 1) {  // from block + mu: U_mu(y) (1 - g) part, projected by the sender
-      const int nbk = nmu + 1 < g.nb[mu] ? blk + g.bstr[mu] : blk - (g.nb[mu] - 1) * g.bstr[mu];
-      const Half<T> h = face_load<T>(a, faces, nbk, 2 * mu, face_index(g, y, mu));
+    // up: from block + mu, U_mu(y) (1 - g) part, projected by the sender;
+    // down: from block - mu, U^+ (1 + g) part, multiplied by the sender
+    const bool up = ymu == g.b[mu] - 1, down = ymu == 0;
+    if (!up && !down) continue;
+    const int nbk = up ? (nmu + 1 < g.nb[mu] ? blk + g.bstr[mu] : blk - (g.nb[mu] - 1) * g.bstr[mu])
+                       : (nmu > 0 ? blk - g.bstr[mu] : blk + (g.nb[mu] - 1) * g.bstr[mu]);
+    const Half<T> h = face_load<T>(a, faces, nbk, up ? 2 * mu : 2 * mu + 1, face_index(g, y, mu));
+    if (up)
       expand_add_rt<-1>(acc, umul(st.link(r, mu), h), T(1), d);
-    }
-    if (ymu == 0) {  // from block - mu: U^+ (1 + g) part, multiplied by the sender
-      const int nbk = nmu > 0 ? blk - g.bstr[mu] : blk + (g.nb[mu] - 1) * g.bstr[mu];
-      const Half<T> w = face_load<T>(a, faces, nbk, 2 * mu + 1, face_index(g, y, mu));
-      expand_add_rt<+1>(acc, w, T(1), d);
-    }
+    else
+      expand_add_rt<+1>(acc, h, T(1), d);
   }
   return acc;
 }
@@ -834,10 +846,9 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
 
   // ---- stage the block's links and clover (once for the whole tile)
   if constexpr (kHalf) {
-    if (threadIdx.x == 0) {
-      mbar_init(bar, 1);
-      stage_issue<P>(a, blk, (unsigned char*)s_r, (unsigned char*)st.base + 144 * Vb, bar);
-    }
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();  // every thread sees the initialised barrier before it waits on it
+    if (threadIdx.x < 32) stage_issue<P>(a, blk, (unsigned char*)s_r, (unsigned char*)st.base + 144 * Vb, bar);
   } else {
     for (int r = threadIdx.x; r < Vb; r += blockDim.x) {
 #pragma unroll 1
@@ -865,7 +876,9 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
   const bool act = i < Vbh;
   const int re = act ? i : 0, ro = Vbh + re;
 
-  // ---- in-block neighbour tables of the two sites, own directions only
+  // ---- in-block neighbour tables of the two sites, own directions only.
+  // In-block lexicographic sites 2m and 2m + 1 differ only in y3 (b3 is even),
+  // hence in parity, so a site's rank among its parity is j >> 1: no table.
   int ye[4], yo[4];
   {
     const int pe = __ldg(g.r2y + re), po = __ldg(g.r2y + ro);
@@ -882,10 +895,10 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
     int pke[4], pko[4];
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-      const int ef = ye[mu] + 1 < g.b[mu] ? __ldg(g.j2r + je + g.ystr[mu]) - Vbh : Vbh;
-      const int eb = ye[mu] > 0 ? __ldg(g.j2r + je - g.ystr[mu]) - Vbh : Vbh;
-      const int of = yo[mu] + 1 < g.b[mu] ? __ldg(g.j2r + jo + g.ystr[mu]) : Vbh;
-      const int ob = yo[mu] > 0 ? __ldg(g.j2r + jo - g.ystr[mu]) : Vbh;
+      const int ef = ye[mu] + 1 < g.b[mu] ? (je + g.ystr[mu]) >> 1 : Vbh;
+      const int eb = ye[mu] > 0 ? (je - g.ystr[mu]) >> 1 : Vbh;
+      const int of = yo[mu] + 1 < g.b[mu] ? (jo + g.ystr[mu]) >> 1 : Vbh;
+      const int ob = yo[mu] > 0 ? (jo - g.ystr[mu]) >> 1 : Vbh;
       pke[mu] = ef | (eb << 16);
       pko[mu] = of | (ob << 16);
     }
