@@ -7,8 +7,9 @@ side; SAP (4 MR steps, 4 cycles; block shape 4^4 or 8x4x4x4 chosen by the
 autotuner) with FP16 block fields and FP32 arithmetic; FGCR(16) whose
 recursion (outer operator, Gram-Schmidt, dots, updates) runs in double-float
 arithmetic on the FP32 units (--outer-prec df64, the default; f64 runs it in
-native FP64), with the solution and the restart residual in FP64.  A step is
-one complete solve from x = 0 to a true FP64 residual <= 1e-10.
+native FP64), with the solution in FP64 and the restart residual r = b - D x
+formed in FP64 from a double-float D x.  A step is one complete solve from
+x = 0 to a true residual <= 1e-10.
 
 Every vector of the solve (403 MB each in FP64) and the gauge/clover fields
 exceed the 129 MB L2, so no flush is needed between steps.
@@ -63,7 +64,7 @@ def sap_src_sha():
         with open(os.path.join(ROOT, "paper_1109_4279_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
-DTYPE = {(sp, op): "%s recursion (f64 residual and solution at restarts) + %s SAP arithmetic on %s SAP storage"
+DTYPE = {(sp, op): "%s recursion (f64 solution; f64 restart residual, its D x in df64 with the df64 recursion) + %s SAP arithmetic on %s SAP storage"
                    % ({"df64": "df64 (double-float: FP32 pairs with error-free transforms, chi = D phi included)"}.get(op, op),
                       "f64" if sp == "f64" else "f32", sp)
          for sp in ("f64", "f32", "f16", "bf16") for op in ("f64", "f32", "df64")}
@@ -736,7 +737,7 @@ def main():
     ap.add_argument("--outer-prec", choices=["f64", "df64", "f32"], default="df64",
                     help="FGCR recursion precision: f64 (Gram-Schmidt, dots, chi = D phi and the update in FP64), "
                          "df64 (the same recursion, chi = D phi included, in double-float arithmetic on the FP32 "
-                         "units; FP64 solution and restart residual) or f32 (the paper's iterative-refinement split, FP64 only "
+                         "units; FP64 solution, restart residual b - D x in FP64 with D x in double-float) or f32 (the paper's iterative-refinement split, FP64 only "
                          "at restarts)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -107,8 +107,10 @@ typedef struct {
                           QCD_PREC_F64 (default): rho, phi_k, chi_k = D phi_k, Gram-Schmidt and dots in FP64;
                           QCD_PREC_DF64: rho, phi_k, chi_k = D phi_k (links and clover as pairs too), the
                           Gram-Schmidt dots and updates and the solution increment in double-float arithmetic
-                          on the FP32 units (GB300 runs FP64 at 1/64 of its FP32 rate); the solution and the
-                          restart residual r = b - D x in FP64;
+                          on the FP32 units (GB300 runs FP64 at 1/64 of its FP32 rate); the solution in FP64,
+                          the restart residual r = b - D x in FP64 from D x in double-float arithmetic (x split
+                          into pairs; about 1e-13 |x| of rounding in r, which leaves |r| exact to far below
+                          any tolerance);
                           QCD_PREC_F32: iterative refinement -- each restart cycle runs the whole recursion
                           in FP32 on the normalised residual r / |r| until its residual has dropped by
                           inner_tol (or the target is met), then the FP32 correction is added to the FP64

@@ -414,6 +414,180 @@ __device__ __forceinline__ cdf cphase(const cdf& z, bool im, float sg) {
 // conjugation chosen at run time), and the two clover blocks another: the
 // double-float arithmetic is long, and unrolled over every hop it would not
 // fit the instruction cache.
+// what a double-float hop needs to find its neighbour: the site's in-block
+// lexicographic index, its packed local coordinates (8 bits each), its block
+// coordinates (16 bits each) and its parity; kept in five registers (a table
+// of the eight neighbours would take 24 and make the kernel spill), the
+// neighbours are computed per hop
+struct DfSite {
+  int j, py, pn01, pn23, par;
+};
+
+__device__ __forceinline__ DfSite df_site_info(const Geom& g, int blk, int r) {
+  int n[4];
+  block_coords(g, blk, n);
+  DfSite d;
+  d.py = __ldg(g.r2y + r);
+  d.pn01 = n[0] | (n[1] << 16);
+  d.pn23 = n[2] | (n[3] << 16);
+  d.j = 0;
+  d.par = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    d.j += ycoord(d.py, mu) * g.ystr[mu];
+    d.par += ycoord(d.py, mu);
+  }
+  d.par &= 1;
+  return d;
+}
+
+// neighbour of hop h (mu = h / 2, forward for even h): block, site and the
+// hop's coefficient -1/2 (times the boundary sign where it wraps around)
+__device__ __forceinline__ void df_hop_nbr(const Geom& g, int blk, const DfSite& d, int h, int& hb, int& hr,
+                                           float& cf) {
+  const int mu = h >> 1;
+  const int ymu = ycoord(d.py, mu), nmu = ((mu < 2 ? d.pn01 : d.pn23) >> (16 * (mu & 1))) & 0xffff;
+  const int b = g.b[mu], ys = g.ystr[mu], nb = g.nb[mu], bs = g.bstr[mu];
+  int j = d.j;
+  bool wrap = false;
+  hb = blk;
+  if ((h & 1) == 0) {
+    if (ymu + 1 < b) {
+      j += ys;
+    } else {
+      j -= (b - 1) * ys;
+      wrap = nmu + 1 == nb;
+      hb += wrap ? -(nb - 1) * bs : bs;
+    }
+  } else {
+    if (ymu > 0) {
+      j -= ys;
+    } else {
+      j += (b - 1) * ys;
+      wrap = nmu == 0;
+      hb += wrap ? (nb - 1) * bs : -bs;
+    }
+  }
+  hr = (d.par ^ 1) * g.Vbh + (j >> 1);  // even block extents: rank among the parity is j >> 1
+  cf = wrap ? -0.5f * g.bcf[mu] : -0.5f;
+}
+
+// (D psi)(x) (D^+ with DAG) at site (blk, r) of the double-float field fin,
+// into the double-float accumulators acc
+template <int DAG>
+__device__ __forceinline__ void df_site(const Geom& g, const float4* __restrict__ U, const FieldPtr& A,
+                                        const float4* __restrict__ fin, int blk, int r, const DfSite& ds,
+                                        SpinAcc& acc) {
+  constexpr float SF = DAG ? 1.f : -1.f;  // D: (1 - g) psi(x + mu); D^+: (1 + g) psi(x + mu)
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc.re[sp][c] = acc.im[sp][c] = dfacc{0.f, 0.f};
+#pragma unroll 1
+  for (int h = 0; h < 8; ++h) {
+    const int mu = h >> 1, bwd = h & 1;
+    int hb, hr;
+    float cf;
+    df_hop_nbr(g, blk, ds, h, hb, hr, cf);
+    // chiral-basis projection (1 + S g_mu): h_i = p_i + S ph_i p_{sigma_i}, with
+    // sigma = (2, 3) or (3, 2) and phases -1 / -i (see SpinDir)
+    const bool swap = mu == 1 || mu == 2;
+    const bool im0 = mu == 1 || mu == 3, im1 = im0;
+    const float sg0 = -1.f, sg1 = (mu >= 2) ? 1.f : -1.f;
+    const float S = bwd ? -SF : SF;
+    cdf hh[2][3];
+    {
+      const float4* d = fin + (long long)hb * 12 * g.Vb + hr;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const cdf p0 = cdf_of(__ldg(d + (long long)a * g.Vb)), p1 = cdf_of(__ldg(d + (long long)(3 + a) * g.Vb));
+        const cdf p2 = cdf_of(__ldg(d + (long long)(6 + a) * g.Vb)), p3 = cdf_of(__ldg(d + (long long)(9 + a) * g.Vb));
+        hh[0][a] = cplus(p0, cphase(swap ? p3 : p2, im0, S * sg0));
+        hh[1][a] = cplus(p1, cphase(swap ? p2 : p3, im1, S * sg1));
+      }
+    }
+    // w = U h (forward, the site's link) or U^+ h (backward, the neighbour's link)
+    const float4* ud = U + ((long long)((bwd ? hb : blk) * 4 + mu) * 9) * g.Vb + (bwd ? hr : r);
+    const float cj = bwd ? -1.f : 1.f;
+    dfacc wr[2][3], wi[2][3];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) wr[sp][a] = wi[sp][a] = dfacc{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        cdf u = cdf_of(__ldg(ud + (long long)(bwd ? 3 * b + a : 3 * a + b) * g.Vb));
+        u.im = {cj * u.im.hi, cj * u.im.lo};
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) cmac_df(wr[sp][a], wi[sp][a], u, hh[sp][b]);
+      }
+    // acc += cf [w ; S B^+ w]: B^+ w has components conj(ph_i) w_i on spins sigma_i
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc_cadd(acc, 0, a, cf, wr[0][a], wi[0][a]);
+      acc_cadd(acc, 1, a, cf, wr[1][a], wi[1][a]);
+      // l_i = S cf conj(ph_i) w_i: conj of a real phase is itself, of -i is +i
+      const float f0 = S * cf * (im0 ? -sg0 : sg0), f1 = S * cf * (im1 ? -sg1 : sg1);
+      dfacc l0r = wr[0][a], l0i = wi[0][a], l1r = wr[1][a], l1i = wi[1][a];
+      if (im0) {  // times i: (re, im) -> (-im, re)
+        l0r = {-wi[0][a].s, -wi[0][a].c};
+        l0i = wr[0][a];
+        l1r = {-wi[1][a].s, -wi[1][a].c};
+        l1i = wr[1][a];
+      }
+      acc_cadd(acc, 2, a, swap ? f1 : f0, swap ? l1r : l0r, swap ? l1i : l0i);
+      acc_cadd(acc, 3, a, swap ? f0 : f1, swap ? l0r : l1r, swap ? l0i : l1i);
+    }
+  }
+  // clover: two Hermitian 6x6 chiral blocks (6 diagonal reals, then the 15
+  // upper off-diagonal elements), record chunk 18 hb + j = reals 36 hb + 2 j, + 1
+  const float4* ca = (const float4*)A.data + (long long)blk * 36 * g.Vb + r;
+  const float4* psid = fin + (long long)blk * 12 * g.Vb + r;
+#pragma unroll 1
+  for (int hb = 0; hb < 2; ++hb) {
+    cdf psi[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) psi[i] = cdf_of(__ldg(psid + (long long)(6 * hb + i) * g.Vb));
+    dfacc tr[6], ti[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) tr[i] = ti[i] = dfacc{0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 6; i += 2) {  // diagonal reals i, i + 1
+      const float4 dv = __ldg(ca + (long long)(18 * hb + i / 2) * g.Vb);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int ii = i + q;
+        const float dh = q ? dv.z : dv.x, dl = q ? dv.w : dv.y;
+        acc_prod(tr[ii], dh, dl, psi[ii].re.hi, psi[ii].re.lo);
+        acc_prod(ti[ii], dh, dl, psi[ii].im.hi, psi[ii].im.lo);
+      }
+    }
+    int kk = 3;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        const cdf a = cdf_of(__ldg(ca + (long long)(18 * hb + kk) * g.Vb));
+        ++kk;
+        cmac_df(tr[i], ti[i], a, psi[j]);
+        cjmac_df(tr[j], ti[j], a, psi[i]);
+      }
+    // into spins 2 hb, 2 hb + 1
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      if (hb == 0) {
+        acc_add(acc.re[i / 3][i % 3], tr[i].s, tr[i].c);
+        acc_add(acc.im[i / 3][i % 3], ti[i].s, ti[i].c);
+      } else {
+        acc_add(acc.re[2 + i / 3][i % 3], tr[i].s, tr[i].c);
+        acc_add(acc.im[2 + i / 3][i % 3], ti[i].s, ti[i].c);
+      }
+    }
+  }
+}
+
 template <int DAG>
 __global__ void __launch_bounds__(256, 2) dirac_df_kernel(Geom g, const float4* __restrict__ U, FieldPtr A,
                                                           FieldPtr in, FieldPtr out, int nrhs,
@@ -421,145 +595,14 @@ __global__ void __launch_bounds__(256, 2) dirac_df_kernel(Geom g, const float4* 
   const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   const int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
-  int n[4], y[4];
-  block_coords(g, blk, n);
-  {
-    const int packed = __ldg(g.r2y + r);
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) y[mu] = ycoord(packed, mu);
-  }
-  // the eight neighbours: blocks, sites and boundary signs (hop h: mu = h / 2,
-  // forward for even h), computed with compile-time directions
-  int nbk[8], nbr[8];
-  float coef[8];
-#pragma unroll
-  for (int h = 0; h < 8; ++h) {
-    const Nbr nb = neighbour(g, blk, y, n, h / 2, (h & 1) ? -1 : +1);
-    nbk[h] = nb.blk;
-    nbr[h] = nb.r;
-    coef[h] = nb.wrap ? -0.5f * g.bcf[h / 2] : -0.5f;
-  }
-  constexpr float SF = DAG ? 1.f : -1.f;  // D: (1 - g) psi(x + mu); D^+: (1 + g) psi(x + mu)
+  const DfSite ds = df_site_info(g, blk, r);
 #pragma unroll 1
   for (int k = 0; k < nrhs; ++k) {
     if (mask && !mask[k]) continue;
     const float4* fin = (const float4*)in.data + (size_t)k * g.V * 12;
     float4* fout = (float4*)out.data + (size_t)k * g.V * 12;
     SpinAcc acc;
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc.re[sp][c] = acc.im[sp][c] = dfacc{0.f, 0.f};
-#pragma unroll 1
-    for (int h = 0; h < 8; ++h) {
-      const int mu = h >> 1, bwd = h & 1;
-      // select this hop's neighbour from the unrolled table without indexing it
-      int hb = nbk[0], hr = nbr[0];
-      float cf = coef[0];
-#pragma unroll
-      for (int q = 1; q < 8; ++q)
-        if (h == q) {
-          hb = nbk[q];
-          hr = nbr[q];
-          cf = coef[q];
-        }
-      // chiral-basis projection (1 + S g_mu): h_i = p_i + S ph_i p_{sigma_i}, with
-      // sigma = (2, 3) or (3, 2) and phases -1 / -i (see SpinDir)
-      const bool swap = mu == 1 || mu == 2;
-      const bool im0 = mu == 1 || mu == 3, im1 = im0;
-      const float sg0 = -1.f, sg1 = (mu >= 2) ? 1.f : -1.f;
-      const float S = bwd ? -SF : SF;
-      cdf hh[2][3];
-      {
-        const float4* d = fin + (long long)hb * 12 * g.Vb + hr;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const cdf p0 = cdf_of(__ldg(d + (long long)a * g.Vb)), p1 = cdf_of(__ldg(d + (long long)(3 + a) * g.Vb));
-          const cdf p2 = cdf_of(__ldg(d + (long long)(6 + a) * g.Vb)), p3 = cdf_of(__ldg(d + (long long)(9 + a) * g.Vb));
-          hh[0][a] = cplus(p0, cphase(swap ? p3 : p2, im0, S * sg0));
-          hh[1][a] = cplus(p1, cphase(swap ? p2 : p3, im1, S * sg1));
-        }
-      }
-      // w = U h (forward, the site's link) or U^+ h (backward, the neighbour's link)
-      const float4* ud = U + ((long long)((bwd ? hb : blk) * 4 + mu) * 9) * g.Vb + (bwd ? hr : r);
-      const float cj = bwd ? -1.f : 1.f;
-      dfacc wr[2][3], wi[2][3];
-#pragma unroll
-      for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) wr[sp][a] = wi[sp][a] = dfacc{0.f, 0.f};
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          cdf u = cdf_of(__ldg(ud + (long long)(bwd ? 3 * b + a : 3 * a + b) * g.Vb));
-          u.im = {cj * u.im.hi, cj * u.im.lo};
-#pragma unroll
-          for (int sp = 0; sp < 2; ++sp) cmac_df(wr[sp][a], wi[sp][a], u, hh[sp][b]);
-        }
-      // acc += cf [w ; S B^+ w]: B^+ w has components conj(ph_i) w_i on spins sigma_i
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        acc_cadd(acc, 0, a, cf, wr[0][a], wi[0][a]);
-        acc_cadd(acc, 1, a, cf, wr[1][a], wi[1][a]);
-        // l_i = S cf conj(ph_i) w_i: conj of a real phase is itself, of -i is +i
-        const float f0 = S * cf * (im0 ? -sg0 : sg0), f1 = S * cf * (im1 ? -sg1 : sg1);
-        dfacc l0r = wr[0][a], l0i = wi[0][a], l1r = wr[1][a], l1i = wi[1][a];
-        if (im0) {  // times i: (re, im) -> (-im, re)
-          l0r = {-wi[0][a].s, -wi[0][a].c};
-          l0i = wr[0][a];
-          l1r = {-wi[1][a].s, -wi[1][a].c};
-          l1i = wr[1][a];
-        }
-        acc_cadd(acc, 2, a, swap ? f1 : f0, swap ? l1r : l0r, swap ? l1i : l0i);
-        acc_cadd(acc, 3, a, swap ? f0 : f1, swap ? l0r : l1r, swap ? l0i : l1i);
-      }
-    }
-    // clover: two Hermitian 6x6 chiral blocks (6 diagonal reals, then the 15
-    // upper off-diagonal elements), record chunk 18 hb + j = reals 36 hb + 2 j, + 1
-    const float4* ca = (const float4*)A.data + (long long)blk * 36 * g.Vb + r;
-    const float4* psid = fin + (long long)blk * 12 * g.Vb + r;
-#pragma unroll 1
-    for (int hb = 0; hb < 2; ++hb) {
-      cdf psi[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) psi[i] = cdf_of(__ldg(psid + (long long)(6 * hb + i) * g.Vb));
-      dfacc tr[6], ti[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) tr[i] = ti[i] = dfacc{0.f, 0.f};
-#pragma unroll
-      for (int i = 0; i < 6; i += 2) {  // diagonal reals i, i + 1
-        const float4 dv = __ldg(ca + (long long)(18 * hb + i / 2) * g.Vb);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int ii = i + q;
-          const float dh = q ? dv.z : dv.x, dl = q ? dv.w : dv.y;
-          acc_prod(tr[ii], dh, dl, psi[ii].re.hi, psi[ii].re.lo);
-          acc_prod(ti[ii], dh, dl, psi[ii].im.hi, psi[ii].im.lo);
-        }
-      }
-      int kk = 3;
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = i + 1; j < 6; ++j) {
-          const cdf a = cdf_of(__ldg(ca + (long long)(18 * hb + kk) * g.Vb));
-          ++kk;
-          cmac_df(tr[i], ti[i], a, psi[j]);
-          cjmac_df(tr[j], ti[j], a, psi[i]);
-        }
-      // into spins 2 hb, 2 hb + 1
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        if (hb == 0) {
-          acc_add(acc.re[i / 3][i % 3], tr[i].s, tr[i].c);
-          acc_add(acc.im[i / 3][i % 3], ti[i].s, ti[i].c);
-        } else {
-          acc_add(acc.re[2 + i / 3][i % 3], tr[i].s, tr[i].c);
-          acc_add(acc.im[2 + i / 3][i % 3], ti[i].s, ti[i].c);
-        }
-      }
-    }
+    df_site<DAG>(g, U, A, fin, blk, r, ds, acc);
     float4* o = fout + (long long)blk * 12 * g.Vb + r;
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
@@ -581,6 +624,40 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   if (threadIdx.x == 0)
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
   return t;
+}
+
+// r = b - D x with x given as its double-float split: D x in double-float
+// arithmetic (as dirac_df_kernel), the difference and |r|^2 in FP64;
+// partial[blockIdx.x] = sum |r|^2 over the CTA, blockIdx.y a right-hand side
+// of a batch (fields V sites apart, partial sums ps doubles apart)
+__global__ void __launch_bounds__(256, 2) residual_df_kernel(Geom g, const float4* __restrict__ U, FieldPtr A,
+                                                             FieldPtr b, FieldPtr x, FieldPtr r_out, double* partial,
+                                                             long long ps, const int* __restrict__ mask) {
+  __shared__ double sh[32];
+  if (mask && !mask[blockIdx.y]) return;
+  const long long o = (long long)blockIdx.y * g.V * 12;  // double2 / float4 elements per field
+  const double2* bb = (const double2*)b.data + o;
+  const float4* xx = (const float4*)x.data + o;
+  double2* rr = (double2*)r_out.data + o;
+  partial += blockIdx.y * ps;
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double nrm = 0;
+  if (s < g.V) {
+    const int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
+    SpinAcc acc;
+    df_site<0>(g, U, A, xx, blk, r, df_site_info(g, blk, r), acc);
+    const long long e = (long long)blk * 12 * g.Vb + r;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const double2 bv = __ldg(bb + e + (long long)q * g.Vb);
+      const double2 v = make_double2(bv.x - df_to_f64(acc_df(acc.re[q / 3][q % 3])),
+                                     bv.y - df_to_f64(acc_df(acc.im[q / 3][q % 3])));
+      rr[e + (long long)q * g.Vb] = v;
+      nrm = fma(v.x, v.x, fma(v.y, v.y, nrm));
+    }
+  }
+  const double t = block_sum(nrm, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
 // r = b - D x (FP64), partial[blockIdx.x] = sum |r|^2 over the CTA; blockIdx.y
@@ -718,6 +795,25 @@ int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& 
                  1848.0 * (double)c->V * B.n);
     residual64_kernel<<<dim3(grid, B.n), 256, 0, s>>>(c->g, c->U[P64], c->A[P64].ptr(), b.ptr(), x.ptr(), r.ptr(),
                                                        part, B.ps, B.mask);
+    QCD_LAUNCHED();
+  }
+  return reduce_partials(part, (int)grid, 1, 1, d_norm2, s, B);
+}
+
+int residual_df(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, const Rec& tmp, double* d_norm2,
+                cudaStream_t s, const Batch& B) {
+  NvtxRange nv("residual_df");
+  if (b.prec != P64 || x.prec != P64 || r.prec != P64 || tmp.prec != PDF || tmp.bytes < (size_t)c->V * 192 * B.n)
+    return QCD_ERR_ARG;
+  QCD_TRY(ensure_gauge(c, PDF, s));
+  QCD_TRY(ensure_clover(c, PDF, s));
+  QCD_TRY(blas_df_split(c, (const double*)x.data, (float*)tmp.data, s, B));
+  const unsigned grid = (unsigned)((c->V + 255) / 256);
+  {
+    ProfScope ps(c, QCD_KERNEL_RESIDUAL, s, (bytes_per_site(P64) + 192) * (double)c->V * B.n,
+                 1848.0 * (double)c->V * B.n);
+    residual_df_kernel<<<dim3(grid, B.n), 256, 0, s>>>(c->g, (const float4*)c->U[PDF], c->A[PDF].ptr(), b.ptr(),
+                                                        tmp.ptr(), r.ptr(), part, B.ps, B.mask);
     QCD_LAUNCHED();
   }
   return reduce_partials(part, (int)grid, 1, 1, d_norm2, s, B);

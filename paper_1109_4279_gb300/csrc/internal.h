@@ -238,6 +238,11 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
 // r = b - D x and |r|^2 (FP64), for each right-hand side of B (fields V sites apart)
 int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s,
                const Batch& B = Batch());
+// the same residual with D x in double-float arithmetic (x split into tmp, a
+// double-float field of B.n right-hand sides); the FGCR restart of the
+// double-float recursion
+int residual_df(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, const Rec& tmp, double* d_norm2,
+                cudaStream_t s, const Batch& B = Batch());
 // even/odd split (FP64): on the sites of parity par,
 //   pre = 1: out = c1 M x + c2 H y;  pre = 0: out = M (c1 x + c2 H y),
 // H the hopping term of D (of D^+ with dagger) from the other parity, M the

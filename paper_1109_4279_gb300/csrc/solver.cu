@@ -407,7 +407,9 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
         st = QCD_ERR_CUDA;
       for (int q = 0; q < G.nr() && st == QCD_OK; ++q) w.h_pin[q * hp + w.nkv + 1] = w.h_pin[q * hp + w.nkv];
     } else {
-      st = residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 1, G.s, batch_of(w, nullptr));
+      st = w.rprec == PDF ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.phi[0], w.d_rn + w.nkv + 1, G.s,
+                                        batch_of(w, nullptr))
+                          : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 1, G.s, batch_of(w, nullptr));
       if (st == QCD_OK) st = read_rn(w, w.nkv + 1, G.s);
     }
     if (st != QCD_OK) group_fail(G, st);
@@ -545,7 +547,9 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
         for (int j = 0; j < kmax; ++j) phi_p[j] = (const double*)w.phi[j].data;
         st = blas_multi_axpy<double>(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B);
       }
-      if (st == QCD_OK) st = residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 2, G.s, B);
+      if (st == QCD_OK)  // (phi_0 is free: the update above was its last use)
+        st = w.rprec == PDF ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.phi[0], w.d_rn + w.nkv + 2, G.s, B)
+                            : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 2, G.s, B);
       if (st == QCD_OK) st = read_rn(w, w.nkv + 2, G.s);
       if (st == QCD_OK && cudaMemcpyAsync(&w.h_pin[w.nkv + 3], (const double*)(G.c->d_scalars + 128), dsz,
                                           cudaMemcpyDeviceToHost, G.s) != cudaSuccess)
