@@ -338,6 +338,8 @@ def run_comparisons(args, lat, w, U, b_t, sp_main, main_ms):
     variants = [("sap_%s_outer_%s" % (sp_, op_), dict(sap_prec=sp_, outer_prec=op_))
                 for sp_, op_ in (("f16", "f64"), ("f16", "df64"), ("bf16", "df64"), ("f16", "f32"), ("f32", "f32"),
                                  ("bf16", "f32"), ("f32", "f64"), ("f64", "f64"))]
+    # the double-float recursion with its restart residual entirely in FP64
+    variants.append(("sap_f16_outer_df64_residual_f64", dict(sap_prec="f16", outer_prec="df64", residual_prec="f64")))
     variants.append(("fgmres_dr_16_4_sap_f16_outer_f64", dict(solver="fgmres_dr", ndefl=4, sap_prec="f16")))
     variants.append(("gcr_f64_unpreconditioned", dict(precond="none", max_restarts=400)))
     variants.append(("cgne_f64", dict(solver="cg")))

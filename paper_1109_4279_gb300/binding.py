@@ -45,7 +45,7 @@ class SolverParams(ctypes.Structure):
                 ("precond", ctypes.c_int), ("ncy", ctypes.c_int), ("nmr", ctypes.c_int),
                 ("sap_prec", ctypes.c_int), ("outer_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("solver", ctypes.c_int), ("ndefl", ctypes.c_int), ("cg_fallback", ctypes.c_int),
-                ("cg_max_iter", ctypes.c_int), ("zero_guess", ctypes.c_int)]
+                ("cg_max_iter", ctypes.c_int), ("zero_guess", ctypes.c_int), ("residual_prec", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -144,7 +144,7 @@ def solver_params(**kw) -> SolverParams:
     sp = SolverParams()
     lib().qcd_solver_defaults(ctypes.byref(sp))
     for k, v in kw.items():
-        if k in ("sap_prec", "outer_prec") and isinstance(v, str):
+        if k in ("sap_prec", "outer_prec", "residual_prec") and isinstance(v, str):
             v = PREC[v]
         if k == "precond" and isinstance(v, str):
             v = PRECOND[v]

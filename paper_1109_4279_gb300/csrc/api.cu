@@ -112,6 +112,7 @@ void qcd_solver_defaults(qcd_solver_params* sp) {
   sp->cg_fallback = 0;
   sp->cg_max_iter = 20000;
   sp->zero_guess = 0;
+  sp->residual_prec = QCD_PREC_DF64;
 }
 
 const char* qcd_status_string(int st) {

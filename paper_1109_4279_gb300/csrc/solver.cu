@@ -364,6 +364,9 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
   if (sp.precond != QCD_PRECOND_NONE && sp.precond != QCD_PRECOND_SAP) return QCD_ERR_ARG;
   if (sp.outer_prec != P64 && sp.outer_prec != P32 && sp.outer_prec != PDF) return QCD_ERR_ARG;
   if (sp.outer_prec == P32 && !(sp.inner_tol > 0 && sp.inner_tol < 1)) return QCD_ERR_ARG;
+  if (sp.residual_prec != P64 && sp.residual_prec != PDF) return QCD_ERR_ARG;
+  // restart residuals of the double-float recursion from a double-float D x unless FP64 is asked for
+  const bool res_df = sp.outer_prec == PDF && sp.residual_prec == PDF;
   if (sp.precond == QCD_PRECOND_SAP && (sp.ncy < 1 || sp.nmr < 0 || sp.sap_prec < P64 || sp.sap_prec > PB16))
     return QCD_ERR_ARG;
   const size_t dsz = sizeof(double);
@@ -407,9 +410,8 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
         st = QCD_ERR_CUDA;
       for (int q = 0; q < G.nr() && st == QCD_OK; ++q) w.h_pin[q * hp + w.nkv + 1] = w.h_pin[q * hp + w.nkv];
     } else {
-      st = w.rprec == PDF ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.phi[0], w.d_rn + w.nkv + 1, G.s,
-                                        batch_of(w, nullptr))
-                          : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 1, G.s, batch_of(w, nullptr));
+      st = res_df ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.phi[0], w.d_rn + w.nkv + 1, G.s, batch_of(w, nullptr))
+                  : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 1, G.s, batch_of(w, nullptr));
       if (st == QCD_OK) st = read_rn(w, w.nkv + 1, G.s);
     }
     if (st != QCD_OK) group_fail(G, st);
@@ -548,8 +550,8 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
         st = blas_multi_axpy<double>(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B);
       }
       if (st == QCD_OK)  // (phi_0 is free: the update above was its last use)
-        st = w.rprec == PDF ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.phi[0], w.d_rn + w.nkv + 2, G.s, B)
-                            : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 2, G.s, B);
+        st = res_df ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.phi[0], w.d_rn + w.nkv + 2, G.s, B)
+                    : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 2, G.s, B);
       if (st == QCD_OK) st = read_rn(w, w.nkv + 2, G.s);
       if (st == QCD_OK && cudaMemcpyAsync(&w.h_pin[w.nkv + 3], (const double*)(G.c->d_scalars + 128), dsz,
                                           cudaMemcpyDeviceToHost, G.s) != cudaSuccess)

@@ -60,7 +60,7 @@ def test_solver_params_layout_matches_header(lib):
     lib.qcd_solver_defaults(ctypes.byref(sp))
     assert (sp.tol, sp.nkv, sp.max_restarts, sp.precond, sp.ncy, sp.nmr) == (1e-10, 16, 100, 1, 4, 4)
     assert (sp.sap_prec, sp.outer_prec, sp.inner_tol, sp.solver, sp.ndefl) == (1, 0, 1e-5, 0, 4)
-    assert (sp.cg_fallback, sp.cg_max_iter, sp.zero_guess) == (0, 20000, 0)
+    assert (sp.cg_fallback, sp.cg_max_iter, sp.zero_guess, sp.residual_prec) == (0, 20000, 0, 4)
     assert ctypes.sizeof(binding.SolverParams) == 72  # LP64 layout of the C structure
 
 

@@ -243,22 +243,26 @@ def test_resident_field_multi_rhs(orc, prec):
     lat.close()
 
 
-@pytest.mark.parametrize("sap_prec", ["f16", "bf16"])
-def test_solve_16x32_df64_recursion(orc, solved_16x32, sap_prec):
-    """The double-float recursion (Gram-Schmidt, dots and updates on pairs of
-    FP32 values, FP64 operator, FP64 restart residual and solution): true
-    residual below 1e-10 and the oracle's solution to 1e-8."""
+@pytest.mark.parametrize("sap_prec,residual_prec", [("f16", "df64"), ("bf16", "df64"), ("f16", "f64")])
+def test_solve_16x32_df64_recursion(orc, solved_16x32, sap_prec, residual_prec):
+    """The double-float recursion (chi = D phi, Gram-Schmidt, dots and updates
+    on pairs of FP32 values, FP64 solution), with the restart residual's D x
+    in double-float arithmetic (the default) or in FP64: true residual below
+    1e-10, the reported residual equal to the oracle's recomputed one, the
+    oracle's solution to 1e-8 and the FP64 recursion's iteration count."""
     w, U, A, b, x_or = solved_16x32
     dims = w["dims"]
     from paper_1109_4279_gb300 import binding
     lat = binding.Lattice(dims, w["block"], w["m0"], w["csw"])
     lat.load_gauge(torch.from_numpy(U).cuda())
-    x, info = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec=sap_prec, outer_prec="df64")
+    x, info = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec=sap_prec, outer_prec="df64",
+                        residual_prec=residual_prec)
     assert info[0]["status"] == 0, info
     x = x.cpu().numpy()
-    assert _oracle_residual(orc, dims, U, A, b, x) <= 1.05e-10
+    res = _oracle_residual(orc, dims, U, A, b, x)
+    assert res <= 1.05e-10
+    assert abs(res - info[0]["true_residual"]) < 1e-13
     assert rel(x, x_or) < 1e-8
-    # the same iteration count as the FP64 recursion
     _, info64 = lat.solve(torch.from_numpy(b).cuda(), tol=1e-10, sap_prec=sap_prec, outer_prec="f64")
     assert abs(info64[0]["iterations"] - info[0]["iterations"]) <= 1
     lat.close()
