@@ -570,6 +570,51 @@ __global__ void __launch_bounds__(kBlasThreads)
   }
 }
 
+// the same update from FP32 phi_j (FP32-exact preconditioner outputs): each
+// float4 of a phi field holds complexes 2 c, 2 c + 1 of site (blk, r) -- chunk
+// (blk * 6 + c) Vb + r -- which are elements (blk * 12 + 2 c) Vb + r and the next
+// chunk row of x; the products are those of the double-float form with zero
+// low parts
+template <int K>
+__global__ void __launch_bounds__(kBlasThreads)
+    df_update32_kernel(VecList<float4> vl, int k, const double* __restrict__ gam, double2* __restrict__ x,
+                       long long nchunk, int Vb, BatchDev bd, int koff) {
+  if (rhs_skipped(bd)) return;
+  const long long ro = blockIdx.y * (bd.vs / 2);  // phi: half the float4 elements of an x-sized field
+  x += blockIdx.y * bd.vs;
+  gam += blockIdx.y * bd.ss;
+  if (bd.k) k = min(k, max(0, bd.k[blockIdx.y] - koff));
+  df gr[K], gi[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    gr[j] = j < k ? df_from_f64(gam[2 * j]) : df{0.f, 0.f};
+    gi[j] = j < k ? df_from_f64(gam[2 * j + 1]) : df{0.f, 0.f};
+  }
+  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < nchunk;
+       m += (long long)gridDim.x * blockDim.x) {
+    const long long t = m / Vb;
+    const int r = (int)(m - t * Vb), cc = (int)(t % 6);
+    const long long blk = t / 6;
+    const long long i0 = (blk * 12 + 2 * cc) * Vb + r;
+    dfacc tr0 = {0.f, 0.f}, ti0 = {0.f, 0.f}, tr1 = {0.f, 0.f}, ti1 = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j < k) {
+        const float4 p = __ldg(vl.v[j] + ro + m);
+        df_cmul_acc(gr[j], gi[j], make_float4(p.x, 0.f, p.y, 0.f), tr0, ti0);
+        df_cmul_acc(gr[j], gi[j], make_float4(p.z, 0.f, p.w, 0.f), tr1, ti1);
+      }
+    double2 v = x[i0];
+    v.x += acc_value(tr0);
+    v.y += acc_value(ti0);
+    x[i0] = v;
+    v = x[i0 + Vb];
+    v.x += acc_value(tr1);
+    v.y += acc_value(ti1);
+    x[i0 + Vb] = v;
+  }
+}
+
 // out = the double-float split of an FP64 field (same element order)
 __global__ void __launch_bounds__(kBlasThreads)
     df_split_kernel(const double2* __restrict__ in, float4* __restrict__ out, long long n, BatchDev bd) {
@@ -981,6 +1026,30 @@ int blas_df_update(qcd_ctx* c, const float4* const* phi, int k, const double* d_
       df_update_kernel<8><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, n, bd, done);
     else
       df_update_kernel<16><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, n, bd, done);
+    QCD_LAUNCHED();
+    done += kk;
+  }
+  return QCD_OK;
+}
+
+int blas_df_update32(qcd_ctx* c, const float4* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s,
+                     const Batch& B) {
+  const long long n = c->V * 12, nchunk = c->V * 6;
+  const dim3 g2(blas_grid(nchunk), B.n);
+  const BatchDev bd = dev_of(B, n);
+  const int Vb = c->g.Vb;
+  int done = 0;
+  while (done < k) {
+    const int kk = k - done < 16 ? k - done : 16;
+    auto vl = make_df_list(phi + done, kk);
+    ProfScope ps(c, QCD_KERNEL_BLAS, s, (8.0 * kk + 32.0) * (double)n * B.n, 8.0 * c->V * 12 * kk * B.n);
+    if (kk <= 4)
+      df_update32_kernel<4><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, nchunk, Vb, bd, done);
+    else if (kk <= 8)
+      df_update32_kernel<8><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, nchunk, Vb, bd, done);
+    else
+      df_update32_kernel<16><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, nchunk, Vb, bd,
+                                                          done);
     QCD_LAUNCHED();
     done += kk;
   }

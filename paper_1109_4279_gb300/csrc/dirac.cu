@@ -472,9 +472,23 @@ __device__ __forceinline__ void df_hop_nbr(const Geom& g, int blk, const DfSite&
   cf = wrap ? -0.5f * g.bcf[mu] : -0.5f;
 }
 
-// (D psi)(x) (D^+ with DAG) at site (blk, r) of the double-float field fin,
-// into the double-float accumulators acc
-template <int DAG>
+// complex q (= 3 spin + colour) of site (blk, r) of a spinor field as a
+// double-float pair: from a double-float field (chunk q holds re hi, re lo, im
+// hi, im lo) or, IN32, from an FP32 field (chunk q / 2 holds complexes 2 (q / 2)
+// and 2 (q / 2) + 1; the low parts are 0)
+template <bool IN32>
+__device__ __forceinline__ cdf df_load(const float4* __restrict__ f, int Vb, int blk, int r, int q) {
+  if constexpr (IN32) {
+    const float2 v = __ldg((const float2*)(f + ((long long)blk * 6 + (q >> 1)) * Vb + r) + (q & 1));
+    return cdf{df{v.x, 0.f}, df{v.y, 0.f}};
+  } else {
+    return cdf_of(__ldg(f + ((long long)blk * 12 + q) * Vb + r));
+  }
+}
+
+// (D psi)(x) (D^+ with DAG) at site (blk, r) of the field fin (double-float,
+// or FP32 with IN32), into the double-float accumulators acc
+template <int DAG, bool IN32 = false>
 __device__ __forceinline__ void df_site(const Geom& g, const float4* __restrict__ U, const FieldPtr& A,
                                         const float4* __restrict__ fin, int blk, int r, const DfSite& ds,
                                         SpinAcc& acc) {
@@ -497,11 +511,10 @@ __device__ __forceinline__ void df_site(const Geom& g, const float4* __restrict_
     const float S = bwd ? -SF : SF;
     cdf hh[2][3];
     {
-      const float4* d = fin + (long long)hb * 12 * g.Vb + hr;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const cdf p0 = cdf_of(__ldg(d + (long long)a * g.Vb)), p1 = cdf_of(__ldg(d + (long long)(3 + a) * g.Vb));
-        const cdf p2 = cdf_of(__ldg(d + (long long)(6 + a) * g.Vb)), p3 = cdf_of(__ldg(d + (long long)(9 + a) * g.Vb));
+        const cdf p0 = df_load<IN32>(fin, g.Vb, hb, hr, a), p1 = df_load<IN32>(fin, g.Vb, hb, hr, 3 + a);
+        const cdf p2 = df_load<IN32>(fin, g.Vb, hb, hr, 6 + a), p3 = df_load<IN32>(fin, g.Vb, hb, hr, 9 + a);
         hh[0][a] = cplus(p0, cphase(swap ? p3 : p2, im0, S * sg0));
         hh[1][a] = cplus(p1, cphase(swap ? p2 : p3, im1, S * sg1));
       }
@@ -544,12 +557,11 @@ __device__ __forceinline__ void df_site(const Geom& g, const float4* __restrict_
   // clover: two Hermitian 6x6 chiral blocks (6 diagonal reals, then the 15
   // upper off-diagonal elements), record chunk 18 hb + j = reals 36 hb + 2 j, + 1
   const float4* ca = (const float4*)A.data + (long long)blk * 36 * g.Vb + r;
-  const float4* psid = fin + (long long)blk * 12 * g.Vb + r;
 #pragma unroll 1
   for (int hb = 0; hb < 2; ++hb) {
     cdf psi[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) psi[i] = cdf_of(__ldg(psid + (long long)(6 * hb + i) * g.Vb));
+    for (int i = 0; i < 6; ++i) psi[i] = df_load<IN32>(fin, g.Vb, blk, r, 6 * hb + i);
     dfacc tr[6], ti[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) tr[i] = ti[i] = dfacc{0.f, 0.f};
@@ -588,7 +600,10 @@ __device__ __forceinline__ void df_site(const Geom& g, const float4* __restrict_
   }
 }
 
-template <int DAG>
+//
+// IN32: the input is an FP32 field (an FP32-exact operand, e.g. a preconditioner
+// output), read at half the bytes; the arithmetic is the same
+template <int DAG, bool IN32>
 __global__ void __launch_bounds__(256, 2) dirac_df_kernel(Geom g, const float4* __restrict__ U, FieldPtr A,
                                                           FieldPtr in, FieldPtr out, int nrhs,
                                                           const int* __restrict__ mask) {
@@ -599,10 +614,10 @@ __global__ void __launch_bounds__(256, 2) dirac_df_kernel(Geom g, const float4* 
 #pragma unroll 1
   for (int k = 0; k < nrhs; ++k) {
     if (mask && !mask[k]) continue;
-    const float4* fin = (const float4*)in.data + (size_t)k * g.V * 12;
+    const float4* fin = (const float4*)in.data + (size_t)k * g.V * (IN32 ? 6 : 12);
     float4* fout = (float4*)out.data + (size_t)k * g.V * 12;
     SpinAcc acc;
-    df_site<DAG>(g, U, A, fin, blk, r, ds, acc);
+    df_site<DAG, IN32>(g, U, A, fin, blk, r, ds, acc);
     float4* o = fout + (long long)blk * 12 * g.Vb + r;
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
@@ -702,19 +717,30 @@ static double bytes_per_site(int prec) {
 
 int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStream_t s, int nrhs, const int* mask) {
   const int prec = in.prec;
-  if (prec == PDF) {  // double-float in and out: the double-float operator
+  if (prec == PDF || (prec == P32 && out.prec == PDF)) {
+    // the double-float operator: double-float in and out, or an FP32 input
+    // (FP32-exact operand) with a double-float result
     if (out.prec != PDF || in.nreal != 24 || out.nreal != 24 || nrhs < 1) return QCD_ERR_ARG;
     QCD_TRY(ensure_gauge(c, PDF, s));
     QCD_TRY(ensure_clover(c, PDF, s));
+    const bool in32 = prec == P32;
     const int threads = c->dirac_threads[PDF];
     const unsigned grid = (unsigned)((c->V + threads - 1) / threads);
-    ProfScope ps(c, QCD_KERNEL_DIRAC, s, (bytes_per_site(P64) + 2 * 192.0) * (double)c->V * nrhs,
+    // algorithmic bytes: links and clover as pairs (576 + 576), spinor out 192, in 192 or 96
+    ProfScope ps(c, QCD_KERNEL_DIRAC, s, (1344.0 + (in32 ? 96.0 : 192.0)) * (double)c->V * nrhs,
                  1824.0 * (double)c->V * nrhs);
     const float4* U = (const float4*)c->U[PDF];
-    if (dagger)
-      dirac_df_kernel<1><<<grid, threads, 0, s>>>(c->g, U, c->A[PDF].ptr(), in.ptr(), out.ptr(), nrhs, mask);
-    else
-      dirac_df_kernel<0><<<grid, threads, 0, s>>>(c->g, U, c->A[PDF].ptr(), in.ptr(), out.ptr(), nrhs, mask);
+    const FieldPtr A = c->A[PDF].ptr();
+    if (in32) {
+      if (dagger)
+        dirac_df_kernel<1, true><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs, mask);
+      else
+        dirac_df_kernel<0, true><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs, mask);
+    } else if (dagger) {
+      dirac_df_kernel<1, false><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs, mask);
+    } else {
+      dirac_df_kernel<0, false><<<grid, threads, 0, s>>>(c->g, U, A, in.ptr(), out.ptr(), nrhs, mask);
+    }
     QCD_LAUNCHED();
     return QCD_OK;
   }

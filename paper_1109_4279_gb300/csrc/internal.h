@@ -105,7 +105,8 @@ struct Workspace {
   int nkv = 0;
   int nr = 1;  // right-hand sides (entry points that allocate b and x themselves use one)
   Rec b, x, r, rho, tmp64;
-  int rprec = P64;    // precision of rho, phi_k, chi_k: P64, or P32 for the refinement scheme
+  int rprec = P64;    // precision of rho and chi_k: P64, P32 (refinement scheme) or PDF (double-float)
+  int pprec = P64;    // precision of phi_k: rprec, but P32 with the double-float recursion and SAP
   std::vector<Rec> phi, chi;
   // scalars of right-hand side q start q * ss doubles after these (right-hand side 0's)
   double* d_scal = nullptr;  // nr blocks of ss doubles holding the arrays below
@@ -314,6 +315,10 @@ int blas_df_normalise_update(qcd_ctx* c, double* part, float4* chi, float4* rho,
 // x (FP64) += sum_j gamma_j phi_j for double-float phi_j (B.k: per-RHS counts)
 int blas_df_update(qcd_ctx* c, const float4* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s,
                    const Batch& B = Batch());
+// the same with FP32 phi_j (FP32-exact fields: the SAP outputs of the
+// double-float recursion), read at half the bytes
+int blas_df_update32(qcd_ctx* c, const float4* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s,
+                     const Batch& B = Batch());
 // FP64 field <-> double-float field (same internal layout)
 int blas_df_split(qcd_ctx* c, const double* in, float* out, cudaStream_t s, const Batch& B = Batch());
 int blas_df_join(qcd_ctx* c, const float* in, double* out, cudaStream_t s, const Batch& B = Batch());

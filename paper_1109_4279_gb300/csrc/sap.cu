@@ -35,6 +35,7 @@ struct SapArgs {
   int read_eta;         // residual source: 1 = eta, 0 = rho_sap
   int io32;             // eta and out are FP32 fields (else FP64)
   int io_df;            // eta and out are double-float fields (eta read as its FP32 high parts)
+  int out32;            // with io_df: out is an FP32 field instead (the block solution is FP32-exact)
   int faces_in;         // add face contributions of the other colour
   int faces_out;        // write this block's face contributions
   int write_rho;        // store the block residual
@@ -1050,9 +1051,9 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
         if (a.psi_mode == 1 || a.psi_mode == 3) v = half_axpy(v, g_half<PS, TS>(rhs_psi(a, rr), Vb, blk, rs, hf), TS(1));
         if (a.psi_mode <= 1) {
           g_half_store<PS, TS>(rhs_psi(a, rr), Vb, blk, rs, hf, v);
-        } else if (a.io_df) {
+        } else if (a.io_df && !a.out32) {
           g_half_store_df<TS>(rhs_out(a, rr), Vb, blk, rs, hf, v);
-        } else if (a.io32) {
+        } else if (a.io32 || a.out32) {
           Half<float> fv;
 #pragma unroll
           for (int s = 0; s < 2; ++s)
@@ -1194,7 +1195,9 @@ int sap_tile(qcd_ctx* c, int nr) {
 int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int ncy, int nmr, int prec,
               cudaStream_t s, const Batch& B, int rt) {
   const Geom& g = c->g;
-  const bool df_in = eta64.prec == PDF && psi64.prec == PDF;
+  // a double-float source with a double-float or an FP32 result (FP32 holds the
+  // FP32 block solution exactly)
+  const bool df_in = eta64.prec == PDF && (psi64.prec == PDF || psi64.prec == P32);
   if (!df_in && (eta64.prec != psi64.prec || (eta64.prec != P64 && eta64.prec != P32))) return QCD_ERR_ARG;
   if (ncy < 1 || nmr < 0 || B.n < 1) return QCD_ERR_ARG;
   if (w.prec != prec || w.nr != B.n) QCD_TRY(sap_prepare(c, w, prec, s, B.n));
@@ -1207,6 +1210,7 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
   a.Ahat = c->Ahat[prec].ptr();
   a.io32 = eta64.prec == P32;
   a.io_df = df_in;
+  a.out32 = df_in && psi64.prec == P32;
   a.eta = eta64.ptr();
   a.rho = w.rho.ptr();
   a.psi = w.psi.ptr();
@@ -1227,7 +1231,7 @@ int sap_apply(qcd_ctx* c, SapWork& w, const Rec& eta64, const Rec& psi64, int nc
   a.rt = rt;
   a.mask = B.mask;
   a.eta_rs = (long long)c->V * (a.io32 ? 96 : 192);  // FP64 and double-float fields: 192 B per site
-  a.out_rs = a.eta_rs;
+  a.out_rs = (long long)c->V * (a.io32 || a.out32 ? 96 : 192);
   a.rho_rs = (long long)c->V * chunks(prec, 24) * 16;
   a.rho_ns = w.rho.norm ? c->V : 0;
   a.psi_rs = (long long)c->V * (dbl ? 192 : 96);

@@ -99,7 +99,9 @@ static void fields_free(Workspace& w) {
 int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream_t s, int nr) {
   const int nkv = sp.nkv;
   const int rprec = sp.outer_prec == P32 ? P32 : (sp.outer_prec == PDF ? PDF : P64);
-  const int pprec = rprec;  // phi_k: the preconditioner's output, the operator's input
+  // phi_k, the preconditioner's output and the operator's input: with the
+  // double-float recursion the SAP output is FP32-exact and is kept in FP32
+  const int pprec = (rprec == PDF && sp.precond == QCD_PRECOND_SAP) ? P32 : rprec;
   if (nr < 1) return QCD_ERR_ARG;
   if (w.nr != nr) {  // the number of right-hand sides changes: reallocate every field
     fields_free(w);
@@ -108,7 +110,7 @@ int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream
   const long long Vn = c->V * nr;
   for (Rec* f : {&w.b, &w.x, &w.r})
     if (!f->data) QCD_TRY(rec_alloc(*f, P64, 24, Vn));
-  if (w.rprec != rprec) {  // the recursion vectors change precision: reallocate them
+  if (w.rprec != rprec || w.pprec != pprec) {  // the recursion vectors change precision: reallocate them
     graphs_clear(w);
     rec_free(w.rho);
     for (auto& r : w.phi) rec_free(r);
@@ -118,6 +120,7 @@ int ws_prepare(qcd_ctx* c, Workspace& w, const qcd_solver_params& sp, cudaStream
     scalars_free(w);
     w.nkv = 0;
     w.rprec = rprec;
+    w.pprec = pprec;
   }
   if (!w.rho.data) QCD_TRY(rec_alloc(w.rho, rprec, 24, Vn));
   if (!w.d_part) {
@@ -410,7 +413,7 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
         st = QCD_ERR_CUDA;
       for (int q = 0; q < G.nr() && st == QCD_OK; ++q) w.h_pin[q * hp + w.nkv + 1] = w.h_pin[q * hp + w.nkv];
     } else {
-      st = res_df ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.phi[0], w.d_rn + w.nkv + 1, G.s, batch_of(w, nullptr))
+      st = res_df ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.chi[0], w.d_rn + w.nkv + 1, G.s, batch_of(w, nullptr))
                   : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 1, G.s, batch_of(w, nullptr));
       if (st == QCD_OK) st = read_rn(w, w.nkv + 1, G.s);
     }
@@ -543,14 +546,15 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
       } else if (st == QCD_OK && w.rprec == PDF) {
         const float4* phi_p[64];
         for (int j = 0; j < kmax; ++j) phi_p[j] = (const float4*)w.phi[j].data;
-        st = blas_df_update(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B);
+        st = w.pprec == P32 ? blas_df_update32(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B)
+                            : blas_df_update(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B);
       } else if (st == QCD_OK) {
         const double* phi_p[64];
         for (int j = 0; j < kmax; ++j) phi_p[j] = (const double*)w.phi[j].data;
         st = blas_multi_axpy<double>(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B);
       }
-      if (st == QCD_OK)  // (phi_0 is free: the update above was its last use)
-        st = res_df ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.phi[0], w.d_rn + w.nkv + 2, G.s, B)
+      if (st == QCD_OK)  // (chi_0 is free: this cycle's Gram-Schmidt was its last use)
+        st = res_df ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.chi[0], w.d_rn + w.nkv + 2, G.s, B)
                     : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 2, G.s, B);
       if (st == QCD_OK) st = read_rn(w, w.nkv + 2, G.s);
       if (st == QCD_OK && cudaMemcpyAsync(&w.h_pin[w.nkv + 3], (const double*)(G.c->d_scalars + 128), dsz,
