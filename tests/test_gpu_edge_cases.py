@@ -113,10 +113,33 @@ def test_bad_solver_parameters():
     lat, U, rng = _lat((8, 8, 8, 8), (4, 4, 2, 2))
     b = torch.from_numpy(synth.gaussian_spinor((8, 8, 8, 8), rng)).cuda()
     for kw in (dict(tol=0.0), dict(nkv=0), dict(nkv=65), dict(ncy=0), dict(sap_prec=7),
-               dict(outer_prec="f32", inner_tol=1.5)):
+               dict(outer_prec="f32", inner_tol=1.5), dict(outer_prec="df64", residual_prec="f32")):
         x = torch.zeros_like(b)
         st, _ = binding.qcd_solve(lat.ctx, b, x, 1, binding.solver_params(**kw), raise_on_fail=False)
         assert st == -1, kw
+    lat.close()
+
+
+def test_df64_recursion_with_and_without_preconditioner(orc):
+    """The double-float recursion keeps phi_k in FP32 behind the SAP (its
+    output is FP32-exact) and in double-float without a preconditioner (phi_k =
+    rho_k); the same workspace switches between the two.  Every solve meets the
+    oracle's residual, and the SAP solve after the switch repeats the first."""
+    dims = (8, 8, 8, 8)
+    lat, U, rng = _lat(dims, (4, 4, 4, 4))
+    bn = synth.gaussian_spinor(dims, rng)
+    b = torch.from_numpy(bn).cuda()
+    A = orc.clover(dims, U, 0.0, 1.5)
+    runs = []
+    for precond in ("sap", "none", "sap"):
+        x, info = lat.solve(b, tol=1e-10, precond=precond, sap_prec="f16", outer_prec="df64", max_restarts=200)
+        assert info[0]["status"] == 0, (precond, info)
+        xn = x.cpu().numpy()
+        res = np.linalg.norm(bn - orc.apply_D(dims, U, A, AP, xn)) / np.linalg.norm(bn)
+        assert res <= 1.05e-10 and abs(res - info[0]["true_residual"]) < 1e-13, precond
+        runs.append((xn, info[0]["iterations"]))
+    assert runs[2][1] == runs[0][1] and np.array_equal(runs[2][0], runs[0][0])
+    assert runs[1][1] > runs[0][1]  # the unpreconditioned recursion takes more iterations
     lat.close()
 
 
