@@ -217,10 +217,14 @@ int qcd_solve_dagger(qcd_ctx* ctx, const double* b, double* x, const qcd_solver_
 
 /*
  * Solve one right-hand side on each of n contexts (lattices of possibly
- * different sizes, Sec. 4 "flexibility in the choice of lattice sizes") in one
- * batched launch sequence: each SAP colour sweep, operator apply and vector
- * reduction runs over the blocks of all lattices at once.  b[i], x[i]: device
- * pointers for ctxs[i].  info: n entries (may be NULL).
+ * different sizes, Sec. 4 "flexibility in the choice of lattice sizes")
+ * together: the lattices iterate in lock step, each on its own context stream
+ * (forked from and joined to `stream`) so that their launches run
+ * concurrently on the GPU, every FGCR iteration of a lattice replayed from a
+ * captured CUDA graph, with one host synchronisation per iteration for all of
+ * them.  Each lattice keeps its own Krylov basis and convergence test, and a
+ * converged one stops iterating while the others continue.  b[i], x[i]: device
+ * pointers for ctxs[i] (distinct contexts).  info: n entries (may be NULL).
  */
 int qcd_solve_batch(qcd_ctx** ctxs, int n, const double* const* b, double* const* x,
                     const qcd_solver_params* sp, qcd_solve_info* info, void* stream);
