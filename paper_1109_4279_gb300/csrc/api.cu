@@ -171,6 +171,7 @@ void qcd_destroy(qcd_ctx* c) {
     rec_free(c->Ahat[p]);
   }
   for (auto st : c->streams) cudaStreamDestroy(st);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   c->streams.clear();
   if (c->d_tables) cudaFree(c->d_tables);
   if (c->d_scalars) cudaFree(c->d_scalars);
@@ -303,21 +304,15 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
         w.stage_bytes = 2 * fbytes;
       }
       stage[k] = w.stage;
-      cudaError_t e = cudaMemcpyAsync(stage[k], b[k], fbytes, cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess && !sp.zero_guess)
-        e = cudaMemcpyAsync(stage[k] + p.c->V * 24, x[k], fbytes, cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) st = cuda_fail(e, "solve upload");
-      bd = stage[k];
-      xd = stage[k] + p.c->V * 24;
+      st = upload_spinor(p.c, b[k], stage[k], p.b, s);
+      if (st == QCD_OK && !sp.zero_guess) st = upload_spinor(p.c, x[k], stage[k] + p.c->V * 24, p.x, s);
+    } else {
+      st = import_spinor(p.c, bd, p.b, 1, s);
+      if (st == QCD_OK && !sp.zero_guess) st = import_spinor(p.c, xd, p.x, 1, s);
     }
-    if (st == QCD_OK) st = import_spinor(p.c, bd, p.b, 1, s);
-    if (st == QCD_OK) {
-      if (sp.zero_guess) {
-        const cudaError_t e = cudaMemsetAsync(p.x.data, 0, fbytes, s);  // FP64 block-major, same size
-        if (e != cudaSuccess) st = cuda_fail(e, "solve zero guess");
-      } else {
-        st = import_spinor(p.c, xd, p.x, 1, s);
-      }
+    if (st == QCD_OK && sp.zero_guess) {
+      const cudaError_t e = cudaMemsetAsync(p.x.data, 0, fbytes, s);  // FP64 block-major, same size
+      if (e != cudaSuccess) st = cuda_fail(e, "solve zero guess");
     }
   }
   if (st == QCD_OK) {
@@ -341,12 +336,8 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
     for (auto& p : probs) p.info.time_ms = ms;
     for (int k = 0; k < n; ++k) {
       Problem& p = probs[k];
-      double* xd = dev ? x[k] : stage[k] + p.c->V * 24;
-      int e2 = export_spinor(p.c, p.x, xd, 1, s);
-      if (e2 == QCD_OK && !dev) {
-        cudaError_t e = cudaMemcpyAsync(x[k], xd, (size_t)p.c->V * 24 * sizeof(double), cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) e2 = cuda_fail(e, "solve download");
-      }
+      const int e2 = dev ? export_spinor(p.c, p.x, x[k], 1, s)
+                         : download_spinor(p.c, p.x, stage[k] + p.c->V * 24, x[k], s);
       if (e2 != QCD_OK && p.status == QCD_OK) p.status = p.info.status = e2;
       if (e2 != QCD_OK && st == QCD_OK) st = e2;
     }

@@ -167,6 +167,7 @@ struct qcd_ctx {
   qcd::Workspace* tile_ws = nullptr;       // right-hand sides solved together by batched launches
   std::vector<qcd::Workspace*> batch_ws;  // extra right-hand sides of a multi-RHS solve (one workspace each)
   std::vector<cudaStream_t> streams;      // one stream per right-hand side of a batch
+  cudaStream_t copy_stream = nullptr;     // host transfers overlapped with the layout kernels
   // instrumentation
   bool prof = false;
   qcd::Timer timers[QCD_KERNEL_COUNT];
@@ -219,6 +220,10 @@ Workspace* ensure_ws(qcd_ctx* c);
 int setup_geometry(qcd_ctx* c);
 int import_spinor(qcd_ctx* c, const double* lex, const Rec& out, int nrhs, cudaStream_t s);
 int export_spinor(qcd_ctx* c, const Rec& in, double* lex, int nrhs, cudaStream_t s);
+// one lattice's field between host memory and the internal layout through a
+// device staging field, copies and layout kernels overlapped slab by slab
+int upload_spinor(qcd_ctx* c, const double* host, double* stage, const Rec& out, cudaStream_t s);
+int download_spinor(qcd_ctx* c, const Rec& in, double* stage, double* host, cudaStream_t s);
 int load_gauge_device(qcd_ctx* c, const double* lex_dev, cudaStream_t s);
 int ensure_gauge(qcd_ctx* c, int prec, cudaStream_t s);
 // convert records between precisions (same layout family)

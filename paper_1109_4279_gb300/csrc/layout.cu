@@ -65,10 +65,12 @@ int setup_geometry(qcd_ctx* c) {
 // ------------------------------------------------------------------------
 // spinor import / export: lexicographic (V, 4, 3) complex128 <-> internal
 // ------------------------------------------------------------------------
+// sites [s0, s1) of the internal order (whole blocks: a range of blocks)
 template <int P>
-__global__ void import_kernel(Geom g, const double* __restrict__ lex, FieldPtr out, long long field_stride_sites) {
-  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.V) return;
+__global__ void import_kernel(Geom g, const double* __restrict__ lex, FieldPtr out, long long field_stride_sites,
+                              long long s0, long long s1) {
+  long long s = s0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= s1) return;
   const int rhs = blockIdx.y;
   int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
   int x[4];
@@ -96,9 +98,10 @@ __global__ void import_kernel(Geom g, const double* __restrict__ lex, FieldPtr o
 }
 
 template <int P>
-__global__ void export_kernel(Geom g, FieldPtr in, double* __restrict__ lex, long long field_stride_sites) {
-  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.V) return;
+__global__ void export_kernel(Geom g, FieldPtr in, double* __restrict__ lex, long long field_stride_sites,
+                              long long s0, long long s1) {
+  long long s = s0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= s1) return;
   const int rhs = blockIdx.y;
   int blk = (int)(s / g.Vb), r = (int)(s - (long long)blk * g.Vb);
   int x[4];
@@ -121,33 +124,108 @@ __global__ void export_kernel(Geom g, FieldPtr in, double* __restrict__ lex, lon
   for (int k = 0; k < 12; ++k) dst[k] = make_double2(v[2 * k], v[2 * k + 1]);
 }
 
-int import_spinor(qcd_ctx* c, const double* lex, const Rec& out, int nrhs, cudaStream_t s) {
+static int import_range(qcd_ctx* c, const double* lex, const Rec& out, int nrhs, long long s0, long long s1,
+                        cudaStream_t s) {
   if (out.nreal != 24) return QCD_ERR_ARG;
-  dim3 grid((unsigned)((c->V + 255) / 256), nrhs);
+  if (s1 <= s0) return QCD_OK;
+  dim3 grid((unsigned)((s1 - s0 + 255) / 256), nrhs);
   switch (out.prec) {
-    case P64: import_kernel<P64><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
-    case PDF: import_kernel<PDF><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
-    case P32: import_kernel<P32><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
-    case P16: import_kernel<P16><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
-    case PB16: import_kernel<PB16><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V); break;
+    case P64: import_kernel<P64><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V, s0, s1); break;
+    case PDF: import_kernel<PDF><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V, s0, s1); break;
+    case P32: import_kernel<P32><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V, s0, s1); break;
+    case P16: import_kernel<P16><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V, s0, s1); break;
+    case PB16: import_kernel<PB16><<<grid, 256, 0, s>>>(c->g, lex, out.ptr(), c->V, s0, s1); break;
     default: return QCD_ERR_ARG;
   }
   QCD_LAUNCHED();
   return QCD_OK;
 }
 
-int export_spinor(qcd_ctx* c, const Rec& in, double* lex, int nrhs, cudaStream_t s) {
+static int export_range(qcd_ctx* c, const Rec& in, double* lex, int nrhs, long long s0, long long s1, cudaStream_t s) {
   if (in.nreal != 24) return QCD_ERR_ARG;
-  dim3 grid((unsigned)((c->V + 255) / 256), nrhs);
+  if (s1 <= s0) return QCD_OK;
+  dim3 grid((unsigned)((s1 - s0 + 255) / 256), nrhs);
   switch (in.prec) {
-    case P64: export_kernel<P64><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
-    case PDF: export_kernel<PDF><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
-    case P32: export_kernel<P32><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
-    case P16: export_kernel<P16><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
-    case PB16: export_kernel<PB16><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V); break;
+    case P64: export_kernel<P64><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V, s0, s1); break;
+    case PDF: export_kernel<PDF><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V, s0, s1); break;
+    case P32: export_kernel<P32><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V, s0, s1); break;
+    case P16: export_kernel<P16><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V, s0, s1); break;
+    case PB16: export_kernel<PB16><<<grid, 256, 0, s>>>(c->g, in.ptr(), lex, c->V, s0, s1); break;
     default: return QCD_ERR_ARG;
   }
   QCD_LAUNCHED();
+  return QCD_OK;
+}
+
+int import_spinor(qcd_ctx* c, const double* lex, const Rec& out, int nrhs, cudaStream_t s) {
+  return import_range(c, lex, out, nrhs, 0, c->V, s);
+}
+
+int export_spinor(qcd_ctx* c, const Rec& in, double* lex, int nrhs, cudaStream_t s) {
+  return export_range(c, in, lex, nrhs, 0, c->V, s);
+}
+
+// Host transfers in slabs of time slices: with x0 the slowest lexicographic
+// coordinate, the blocks of block time coordinates [n0, n1) are block indices
+// [n0, n1) * bstr0 and lexicographic sites [n0, n1) * b0 * L1 L2 L3, so one
+// slab is one contiguous range in both orders.  The copy of slab k+1 runs on
+// the context's copy stream while slab k is imported (or exported) on s.
+static int slabs(const qcd_ctx* c) {
+  const int nb0 = c->g.nb[0];
+  for (int k = 8; k > 1; --k)
+    if (nb0 % k == 0) return k;
+  return 1;
+}
+
+static int copy_stream(qcd_ctx* c, cudaStream_t* cs) {
+  if (!c->copy_stream) QCD_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  *cs = c->copy_stream;
+  return QCD_OK;
+}
+
+// one lattice's lexicographic host field -> stage (device) -> out (internal)
+int upload_spinor(qcd_ctx* c, const double* host, double* stage, const Rec& out, cudaStream_t s) {
+  cudaStream_t cs;
+  QCD_TRY(copy_stream(c, &cs));
+  const int n = slabs(c);
+  const long long vs = c->V / n;  // sites per slab, both orders
+  cudaEvent_t e;
+  QCD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEventRecord(e, s);  // the copies follow s's earlier work on the stage
+  cudaStreamWaitEvent(cs, e, 0);
+  cudaEventDestroy(e);
+  for (int k = 0; k < n; ++k) {
+    QCD_CUDA(cudaMemcpyAsync(stage + k * vs * 24, host + k * vs * 24, (size_t)vs * 24 * sizeof(double),
+                             cudaMemcpyHostToDevice, cs));
+    QCD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEventRecord(e, cs);
+    cudaStreamWaitEvent(s, e, 0);
+    cudaEventDestroy(e);
+    QCD_TRY(import_range(c, stage, out, 1, k * vs, (k + 1) * vs, s));
+  }
+  return QCD_OK;
+}
+
+// in (internal) -> stage -> the lexicographic host field; s waits for the copies
+int download_spinor(qcd_ctx* c, const Rec& in, double* stage, double* host, cudaStream_t s) {
+  cudaStream_t cs;
+  QCD_TRY(copy_stream(c, &cs));
+  const int n = slabs(c);
+  const long long vs = c->V / n;
+  cudaEvent_t e;
+  for (int k = 0; k < n; ++k) {
+    QCD_TRY(export_range(c, in, stage, 1, k * vs, (k + 1) * vs, s));
+    QCD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEventRecord(e, s);
+    cudaStreamWaitEvent(cs, e, 0);
+    cudaEventDestroy(e);
+    QCD_CUDA(cudaMemcpyAsync(host + k * vs * 24, stage + k * vs * 24, (size_t)vs * 24 * sizeof(double),
+                             cudaMemcpyDeviceToHost, cs));
+  }
+  QCD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEventRecord(e, cs);
+  cudaStreamWaitEvent(s, e, 0);
+  cudaEventDestroy(e);
   return QCD_OK;
 }
 
