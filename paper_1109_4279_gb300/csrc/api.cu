@@ -172,6 +172,7 @@ void qcd_destroy(qcd_ctx* c) {
   }
   for (auto st : c->streams) cudaStreamDestroy(st);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->deliver_stream) cudaStreamDestroy(c->deliver_stream);
   c->streams.clear();
   if (c->d_tables) cudaFree(c->d_tables);
   if (c->d_scalars) cudaFree(c->d_scalars);
@@ -314,6 +315,12 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
       const cudaError_t e = cudaMemsetAsync(p.x.data, 0, fbytes, s);  // FP64 block-major, same size
       if (e != cudaSuccess) st = cuda_fail(e, "solve zero guess");
     }
+    // FGCR hands each restart's updated x to the caller's field at once; the
+    // export at the end is then needed only if x changed after the last one
+    if (sp.solver == QCD_SOLVER_FGCR) {
+      p.dlv_lex = x[k];
+      p.dlv_stage = dev ? nullptr : stage[k] + p.c->V * 24;
+    }
   }
   if (st == QCD_OK) {
     cudaEvent_t e0, e1;
@@ -336,13 +343,18 @@ static int solve_problems(std::vector<Problem>& probs, const double* const* b, d
     for (auto& p : probs) p.info.time_ms = ms;
     for (int k = 0; k < n; ++k) {
       Problem& p = probs[k];
-      const int e2 = dev ? export_spinor(p.c, p.x, x[k], 1, s)
-                         : download_spinor(p.c, p.x, stage[k] + p.c->V * 24, x[k], s);
+      int e2 = QCD_OK;
+      // s follows the last delivery (its writes to the caller's field end first)
+      if (p.dlv_event && cudaStreamWaitEvent(s, p.dlv_event, 0) != cudaSuccess) e2 = QCD_ERR_CUDA;
+      if (e2 == QCD_OK && !p.delivered)
+        e2 = dev ? export_spinor(p.c, p.x, x[k], 1, s) : download_spinor(p.c, p.x, stage[k] + p.c->V * 24, x[k], s);
       if (e2 != QCD_OK && p.status == QCD_OK) p.status = p.info.status = e2;
       if (e2 != QCD_OK && st == QCD_OK) st = e2;
     }
   }
   cudaStreamSynchronize(s);
+  for (auto& p : probs)
+    if (p.dlv_event) cudaEventDestroy(p.dlv_event);
   for (int k = 0; k < n; ++k) {
 
     if (info) info[k] = probs[k].info;

@@ -168,6 +168,7 @@ struct qcd_ctx {
   std::vector<qcd::Workspace*> batch_ws;  // extra right-hand sides of a multi-RHS solve (one workspace each)
   std::vector<cudaStream_t> streams;      // one stream per right-hand side of a batch
   cudaStream_t copy_stream = nullptr;     // host transfers overlapped with the layout kernels
+  cudaStream_t deliver_stream = nullptr;  // early delivery of solutions (Problem::dlv_lex)
   // instrumentation
   bool prof = false;
   qcd::Timer timers[QCD_KERNEL_COUNT];
@@ -359,7 +360,18 @@ struct Problem {
   int kused = 0, slow = 0;
   bool active = true, cycle_done = false;
   int status = QCD_OK;
+  // early delivery of the solution to the caller's lexicographic field (set
+  // up by the API): after every restart update of x the field is exported on
+  // the context's delivery stream -- through dlv_stage when dlv_lex is host
+  // memory -- while the solver goes on to the residual; `delivered` says the
+  // last delivery followed the last change of x, dlv_event marks its end
+  double* dlv_lex = nullptr;
+  double* dlv_stage = nullptr;
+  bool delivered = false;
+  cudaEvent_t dlv_event = nullptr;
 };
+// deliver p.x to p.dlv_lex now (ordered after s's work), off the solver's stream
+int deliver_solution(Problem& p, cudaStream_t s);
 // right-hand sides of one lattice that share a workspace and are iterated by
 // the same launches (each kernel of an FGCR iteration runs over all of them);
 // rhs[q]->b / ->x view right-hand side q of the workspace's fields

@@ -206,6 +206,31 @@ int upload_spinor(qcd_ctx* c, const double* host, double* stage, const Rec& out,
   return QCD_OK;
 }
 
+int deliver_solution(Problem& p, cudaStream_t s) {
+  qcd_ctx* c = p.c;
+  if (!c->deliver_stream) {
+    // the highest priority: its export CTAs take SM slots as the residual's free up,
+    // so the copies start while the residual is still running
+    int least = 0, greatest = 0;
+    QCD_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    QCD_CUDA(cudaStreamCreateWithPriority(&c->deliver_stream, cudaStreamNonBlocking, greatest));
+  }
+  if (!p.dlv_event) QCD_CUDA(cudaEventCreateWithFlags(&p.dlv_event, cudaEventDisableTiming));
+  cudaStream_t ds = c->deliver_stream;
+  cudaEvent_t e;
+  QCD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEventRecord(e, s);  // after the update of x
+  cudaStreamWaitEvent(ds, e, 0);
+  cudaEventDestroy(e);
+  if (p.dlv_stage)
+    QCD_TRY(download_spinor(c, p.x, p.dlv_stage, p.dlv_lex, ds));
+  else
+    QCD_TRY(export_spinor(c, p.x, p.dlv_lex, 1, ds));
+  QCD_CUDA(cudaEventRecord(p.dlv_event, ds));
+  p.delivered = true;
+  return QCD_OK;
+}
+
 // in (internal) -> stage -> the lexicographic host field; s waits for the copies
 int download_spinor(qcd_ctx* c, const Rec& in, double* stage, double* host, cudaStream_t s) {
   cudaStream_t cs;

@@ -538,6 +538,10 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
         B.k = w.d_k;
       }
       if (st == QCD_OK) st = fgcr_backsub(w.d_a1, w.d_a2, w.d_cr, kmax, sp.nkv, w.d_gam, G.s, B);
+      // x changes below: a delivery of the previous x must have read it first
+      for (auto* p : G.rhs)
+        if (p->dlv_event && cudaStreamWaitEvent(G.s, p->dlv_event, 0) != cudaSuccess) st = QCD_ERR_CUDA;
+      for (auto* p : G.rhs) p->delivered = false;
       if (st == QCD_OK && w.rprec == P32) {
         const float* phi_p[64];
         for (int j = 0; j < kmax; ++j) phi_p[j] = (const float*)w.phi[j].data;
@@ -553,6 +557,8 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
         for (int j = 0; j < kmax; ++j) phi_p[j] = (const double*)w.phi[j].data;
         st = blas_multi_axpy<double>(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B);
       }
+      // the updated x to the caller while the residual decides whether it is final
+      if (st == QCD_OK && G.nr() == 1 && G.rhs[0]->dlv_lex) st = deliver_solution(*G.rhs[0], G.s);
       if (st == QCD_OK)  // (chi_0 is free: this cycle's Gram-Schmidt was its last use)
         st = res_df ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.chi[0], w.d_rn + w.nkv + 2, G.s, B)
                     : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 2, G.s, B);
@@ -664,6 +670,10 @@ int run_solver(std::vector<Problem>& probs, const qcd_solver_params& sp, bool us
     bool any = false;
     for (auto& p : probs) any |= (p.status == QCD_STAGNATED || p.status == QCD_NOT_CONVERGED);
     if (any) {
+      for (auto& p : probs) {  // the fallback goes on from x: after any delivery of it has read it
+        p.delivered = false;
+        if (p.dlv_event) cudaStreamWaitEvent(p.s, p.dlv_event, 0);
+      }
       cg_batch(probs, sp, true);
       st = QCD_OK;
       for (auto& p : probs)
