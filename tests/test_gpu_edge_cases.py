@@ -232,25 +232,33 @@ def test_zero_guess_with_several_right_hand_sides_on_host(orc):
     lat.close()
 
 
-@pytest.mark.parametrize("dims,block", [((16, 8, 8, 8), (4, 4, 4, 4)), ((12, 8, 8, 8), (2, 4, 4, 4))])
-def test_host_buffers_match_device_buffers(dims, block):
+@pytest.mark.parametrize("dims,block,nkv", [((16, 8, 8, 8), (4, 4, 4, 4), 16), ((12, 8, 8, 8), (2, 4, 4, 4), 16),
+                                            ((16, 8, 8, 8), (4, 4, 4, 4), 2)])
+def test_host_buffers_match_device_buffers(orc, dims, block, nkv):
     """A single right-hand side from host memory (pinned, with and without an
     initial guess) goes up and comes back in slabs of time slices, copies
-    overlapped with the layout kernels: the solution equals the one from
-    device buffers bit for bit (16 / 4 = 4 slabs; 12 / 2 = 6 slabs)."""
+    overlapped with the layout kernels, and every restart's x is handed to the
+    caller while the residual is computed: the solution equals the one from
+    device buffers bit for bit and meets the oracle's residual (16 / 4 = 4
+    slabs; 12 / 2 = 6 slabs; nkv = 2: many restarts, each delivering x)."""
     from paper_1109_4279_gb300 import binding
     lat, U, rng = _lat(dims, block)
     bn = synth.gaussian_spinor(dims, rng)
     x0n = 0.1 * synth.gaussian_spinor(dims, rng)
+    A = orc.clover(dims, U, 0.0, 1.5)
     for guess in (False, True):
-        kw = dict(tol=1e-10, sap_prec="f16", outer_prec="df64", zero_guess=0 if guess else 1)
+        kw = dict(tol=1e-10, nkv=nkv, sap_prec="f16", outer_prec="df64", zero_guess=0 if guess else 1)
         bd = torch.from_numpy(bn).cuda()
         xd = torch.from_numpy(x0n).cuda() if guess else torch.zeros_like(bd)
         st, _ = binding.qcd_solve(lat.ctx, bd, xd, 1, binding.solver_params(**kw))
         bh = torch.from_numpy(bn).pin_memory()
         xh = torch.from_numpy(x0n).pin_memory() if guess else torch.full_like(bh, float("nan")).pin_memory()
-        st, _ = binding.qcd_solve(lat.ctx, bh, xh, 1, binding.solver_params(**kw))
+        st, info = binding.qcd_solve(lat.ctx, bh, xh, 1, binding.solver_params(**kw))
         assert np.array_equal(xh.numpy(), xd.cpu().numpy()), guess
+        res = np.linalg.norm(bn - orc.apply_D(dims, U, A, AP, xh.numpy())) / np.linalg.norm(bn)
+        assert res <= 1.05e-10 and abs(res - info[0]["true_residual"]) < 1e-13, (guess, info)
+        if nkv == 2:
+            assert info[0]["restarts"] > 2
     lat.close()
 
 
