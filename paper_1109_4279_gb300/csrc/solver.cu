@@ -393,9 +393,13 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
     Workspace& w = *G.w;
     const Batch B = batch_of(w, nullptr);
     int st = blas_norm2<double>(G.c, w.d_part, (const double*)w.b.data, w.d_rn + w.nkv, G.s, B);
-    if (st == QCD_OK) st = blas_norm2<double>(G.c, w.d_part, (const double*)w.x.data, w.d_rn + w.nkv + 3, G.s, B);
     if (st == QCD_OK) st = read_rn(w, w.nkv, G.s);
-    if (st == QCD_OK) st = read_rn(w, w.nkv + 3, G.s);
+    if (sp.zero_guess) {  // the caller stated x = 0 (and the API cleared it): no norm to take
+      for (int q = 0; q < G.nr(); ++q) w.h_pin[q * (w.nkv + 8) + w.nkv + 3] = 0.0;
+    } else {
+      if (st == QCD_OK) st = blas_norm2<double>(G.c, w.d_part, (const double*)w.x.data, w.d_rn + w.nkv + 3, G.s, B);
+      if (st == QCD_OK) st = read_rn(w, w.nkv + 3, G.s);
+    }
     if (st != QCD_OK) group_fail(G, st);
   }
   QCD_TRY(sync_groups(groups));
