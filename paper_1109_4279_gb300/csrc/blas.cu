@@ -578,10 +578,11 @@ __global__ void __launch_bounds__(kBlasThreads)
 template <int K>
 __global__ void __launch_bounds__(kBlasThreads)
     df_update32_kernel(VecList<float4> vl, int k, const double* __restrict__ gam, double2* __restrict__ x,
-                       long long nchunk, int Vb, BatchDev bd, int koff) {
+                       long long nchunk, int Vb, BatchDev bd, int koff, float4* __restrict__ xs) {
   if (rhs_skipped(bd)) return;
   const long long ro = blockIdx.y * (bd.vs / 2);  // phi: half the float4 elements of an x-sized field
   x += blockIdx.y * bd.vs;
+  if (xs) xs += blockIdx.y * bd.vs;
   gam += blockIdx.y * bd.ss;
   if (bd.k) k = min(k, max(0, bd.k[blockIdx.y] - koff));
   df gr[K], gi[K];
@@ -608,10 +609,18 @@ __global__ void __launch_bounds__(kBlasThreads)
     v.x += acc_value(tr0);
     v.y += acc_value(ti0);
     x[i0] = v;
+    if (xs) {  // the updated x's double-float split too (same element order)
+      const df a = df_from_f64(v.x), b = df_from_f64(v.y);
+      xs[i0] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
     v = x[i0 + Vb];
     v.x += acc_value(tr1);
     v.y += acc_value(ti1);
     x[i0 + Vb] = v;
+    if (xs) {
+      const df a = df_from_f64(v.x), b = df_from_f64(v.y);
+      xs[i0 + Vb] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
   }
 }
 
@@ -1033,7 +1042,7 @@ int blas_df_update(qcd_ctx* c, const float4* const* phi, int k, const double* d_
 }
 
 int blas_df_update32(qcd_ctx* c, const float4* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s,
-                     const Batch& B) {
+                     const Batch& B, float* xs) {
   const long long n = c->V * 12, nchunk = c->V * 6;
   const dim3 g2(blas_grid(nchunk), B.n);
   const BatchDev bd = dev_of(B, n);
@@ -1043,13 +1052,16 @@ int blas_df_update32(qcd_ctx* c, const float4* const* phi, int k, const double* 
     const int kk = k - done < 16 ? k - done : 16;
     auto vl = make_df_list(phi + done, kk);
     ProfScope ps(c, QCD_KERNEL_BLAS, s, (8.0 * kk + 32.0) * (double)n * B.n, 8.0 * c->V * 12 * kk * B.n);
+    float4* x4 = done + kk == k ? (float4*)xs : nullptr;  // the split after the last part of the update
     if (kk <= 4)
-      df_update32_kernel<4><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, nchunk, Vb, bd, done);
+      df_update32_kernel<4><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, nchunk, Vb, bd, done,
+                                                         x4);
     else if (kk <= 8)
-      df_update32_kernel<8><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, nchunk, Vb, bd, done);
+      df_update32_kernel<8><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, nchunk, Vb, bd, done,
+                                                         x4);
     else
       df_update32_kernel<16><<<g2, kBlasThreads, 0, s>>>(vl, kk, d_gamma + 2 * done, (double2*)x, nchunk, Vb, bd,
-                                                          done);
+                                                          done, x4);
     QCD_LAUNCHED();
     done += kk;
   }

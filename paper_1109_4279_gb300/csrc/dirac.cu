@@ -827,13 +827,13 @@ int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& 
 }
 
 int residual_df(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, const Rec& tmp, double* d_norm2,
-                cudaStream_t s, const Batch& B) {
+                cudaStream_t s, const Batch& B, bool presplit) {
   NvtxRange nv("residual_df");
   if (b.prec != P64 || x.prec != P64 || r.prec != P64 || tmp.prec != PDF || tmp.bytes < (size_t)c->V * 192 * B.n)
     return QCD_ERR_ARG;
   QCD_TRY(ensure_gauge(c, PDF, s));
   QCD_TRY(ensure_clover(c, PDF, s));
-  QCD_TRY(blas_df_split(c, (const double*)x.data, (float*)tmp.data, s, B));
+  if (!presplit) QCD_TRY(blas_df_split(c, (const double*)x.data, (float*)tmp.data, s, B));
   const unsigned grid = (unsigned)((c->V + 255) / 256);
   {
     ProfScope ps(c, QCD_KERNEL_RESIDUAL, s, (bytes_per_site(P64) + 192) * (double)c->V * B.n,

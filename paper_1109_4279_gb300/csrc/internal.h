@@ -246,10 +246,11 @@ int dirac_apply(qcd_ctx* c, const Rec& in, const Rec& out, int dagger, cudaStrea
 int residual64(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, double* d_norm2, cudaStream_t s,
                const Batch& B = Batch());
 // the same residual with D x in double-float arithmetic (x split into tmp, a
-// double-float field of B.n right-hand sides); the FGCR restart of the
-// double-float recursion
+// double-float field of B.n right-hand sides, unless presplit says tmp holds
+// the split already); the FGCR restart of the double-float recursion
 int residual_df(qcd_ctx* c, double* part, const Rec& b, const Rec& x, const Rec& r, const Rec& tmp, double* d_norm2,
-                cudaStream_t s, const Batch& B = Batch());
+                cudaStream_t s, const Batch& B = Batch(),
+                bool presplit = false);
 // even/odd split (FP64): on the sites of parity par,
 //   pre = 1: out = c1 M x + c2 H y;  pre = 0: out = M (c1 x + c2 H y),
 // H the hopping term of D (of D^+ with dagger) from the other parity, M the
@@ -324,7 +325,7 @@ int blas_df_update(qcd_ctx* c, const float4* const* phi, int k, const double* d_
 // the same with FP32 phi_j (FP32-exact fields: the SAP outputs of the
 // double-float recursion), read at half the bytes
 int blas_df_update32(qcd_ctx* c, const float4* const* phi, int k, const double* d_gamma, double* x, cudaStream_t s,
-                     const Batch& B = Batch());
+                     const Batch& B = Batch(), float* xs = nullptr);
 // FP64 field <-> double-float field (same internal layout)
 int blas_df_split(qcd_ctx* c, const double* in, float* out, cudaStream_t s, const Batch& B = Batch());
 int blas_df_join(qcd_ctx* c, const float* in, double* out, cudaStream_t s, const Batch& B = Batch());

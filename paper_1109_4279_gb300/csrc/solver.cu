@@ -554,7 +554,9 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
       } else if (st == QCD_OK && w.rprec == PDF) {
         const float4* phi_p[64];
         for (int j = 0; j < kmax; ++j) phi_p[j] = (const float4*)w.phi[j].data;
-        st = w.pprec == P32 ? blas_df_update32(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B)
+        // with the FP32 phi the update also leaves the split of x for the residual in chi_0
+        st = w.pprec == P32 ? blas_df_update32(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B,
+                                               res_df ? (float*)w.chi[0].data : nullptr)
                             : blas_df_update(G.c, phi_p, kmax, w.d_gam, (double*)w.x.data, G.s, B);
       } else if (st == QCD_OK) {
         const double* phi_p[64];
@@ -564,7 +566,8 @@ int fgcr_groups(std::vector<Group>& groups, const qcd_solver_params& sp, bool us
       // the updated x to the caller while the residual decides whether it is final
       if (st == QCD_OK && G.nr() == 1 && G.rhs[0]->dlv_lex) st = deliver_solution(*G.rhs[0], G.s);
       if (st == QCD_OK)  // (chi_0 is free: this cycle's Gram-Schmidt was its last use)
-        st = res_df ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.chi[0], w.d_rn + w.nkv + 2, G.s, B)
+        st = res_df ? residual_df(G.c, w.d_part, w.b, w.x, w.r, w.chi[0], w.d_rn + w.nkv + 2, G.s, B,
+                                  w.rprec == PDF && w.pprec == P32)
                     : residual64(G.c, w.d_part, w.b, w.x, w.r, w.d_rn + w.nkv + 2, G.s, B);
       if (st == QCD_OK) st = read_rn(w, w.nkv + 2, G.s);
       if (st == QCD_OK && cudaMemcpyAsync(&w.h_pin[w.nkv + 3], (const double*)(G.c->d_scalars + 128), dsz,
