@@ -195,9 +195,13 @@ int qcd_apply_D(qcd_ctx* ctx, const double* in, double* out, int dagger, int pre
 
 /*
  * Solve D x = b for nrhs right-hand sides by SAP-preconditioned FGCR (Sec. 4)
- * to |b - D x| / |b| <= sp->tol in a true FP64 residual.  b, x: nrhs * (V, 4,
- * 3) complex128, both host or both device pointers (detected); x holds the
- * initial guess on entry (zeros for none) and the solution on return.
+ * to |b - D x| / |b| <= sp->tol in the true residual (see residual_prec).
+ * b, x: nrhs * (V, 4, 3) complex128, both host or both device pointers
+ * (detected); x holds the initial guess on entry (zeros for none, or any
+ * content with sp->zero_guess) and the solution on return.  The call returns
+ * when x is complete; while it runs, a single-right-hand-side FGCR solve may
+ * write x more than once (each restart's iterate is handed over while the
+ * residual is checked), so x must not be read or written concurrently.
  * sp = NULL uses qcd_solver_defaults.  info (may be NULL) receives one
  * qcd_solve_info per right-hand side.  Returns QCD_OK when every right-hand
  * side converged, else the first failing status (QCD_NOT_CONVERGED,
