@@ -162,18 +162,19 @@ __global__ void __launch_bounds__(kBlasThreads)
   w += ro;
   if (cond) cond += blockIdx.y * bd.ss;
   part += blockIdx.y * bd.ps;
+  if (cond != nullptr && !second_pass_needed(cond)) {  // skipped: zero partial sums, no reduction
+    if (threadIdx.x < 2 * K + NORM) part[(long long)blockIdx.x * (2 * K + NORM) + threadIdx.x] = 0.0;
+    return;
+  }
   R acc[2 * K + NORM];
 #pragma unroll
   for (int j = 0; j < 2 * K + NORM; ++j) acc[j] = 0;
-  if (cond == nullptr || second_pass_needed(cond)) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-      const E b = __ldg(w + i);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const E b = __ldg(w + i);
 #pragma unroll
-      for (int j = 0; j < K; ++j)
-        if (j < k) dot_acc(__ldg(vl.v[j] + ro + i), b, acc[2 * j], acc[2 * j + 1]);
-      if (NORM) nrm_acc(b, acc[2 * K]);
-    }
+    for (int j = 0; j < K; ++j)
+      if (j < k) dot_acc(__ldg(vl.v[j] + ro + i), b, acc[2 * j], acc[2 * j + 1]);
+    if (NORM) nrm_acc(b, acc[2 * K]);
   }
   cta_reduce_store<2 * K + NORM>(acc, part);
 }
@@ -454,18 +455,19 @@ __global__ void __launch_bounds__(kBlasThreads)
   w += ro;
   if (cond) cond += blockIdx.y * bd.ss;
   part += blockIdx.y * bd.ps;
+  if (cond != nullptr && !second_pass_needed(cond)) {  // skipped: zero partial sums, no reduction
+    if (threadIdx.x < 2 * K + NORM) part[(long long)blockIdx.x * (2 * K + NORM) + threadIdx.x] = 0.0;
+    return;
+  }
   dfacc acc[2 * K + NORM];
 #pragma unroll
   for (int j = 0; j < 2 * K + NORM; ++j) acc[j] = {0.f, 0.f};
-  if (cond == nullptr || second_pass_needed(cond)) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-      const float4 b = __ldg(w + i);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float4 b = __ldg(w + i);
 #pragma unroll
-      for (int j = 0; j < K; ++j)
-        if (j < k) df_dot_acc(__ldg(vl.v[j] + ro + i), b, acc[2 * j], acc[2 * j + 1]);
-      if (NORM) df_nrm_acc(b, acc[2 * K]);
-    }
+    for (int j = 0; j < K; ++j)
+      if (j < k) df_dot_acc(__ldg(vl.v[j] + ro + i), b, acc[2 * j], acc[2 * j + 1]);
+    if (NORM) df_nrm_acc(b, acc[2 * K]);
   }
   df_reduce_store<2 * K + NORM>(acc, part);
 }
