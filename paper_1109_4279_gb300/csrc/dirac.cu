@@ -486,6 +486,27 @@ __device__ __forceinline__ cdf df_load(const float4* __restrict__ f, int Vb, int
   }
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// the lines hop h reads (the neighbour's spinor and the link) asked for in L1
+// one hop ahead: the arithmetic of a hop is long, and the gathers of the next
+// one then find their lines near instead of waiting a DRAM round trip
+template <bool IN32>
+__device__ __forceinline__ void df_prefetch_hop(const Geom& g, const float4* __restrict__ U,
+                                                const float4* __restrict__ fin, int blk, int r, const DfSite& ds,
+                                                int h) {
+  int hb, hr;
+  float cf;
+  df_hop_nbr(g, blk, ds, h, hb, hr, cf);
+  constexpr int NQ = IN32 ? 6 : 12;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) prefetch_l1(fin + ((long long)hb * NQ + q) * g.Vb + hr);
+  const int mu = h >> 1, bwd = h & 1;
+  const float4* ud = U + ((long long)((bwd ? hb : blk) * 4 + mu) * 9) * g.Vb + (bwd ? hr : r);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) prefetch_l1(ud + (long long)k * g.Vb);
+}
+
 // (D psi)(x) (D^+ with DAG) at site (blk, r) of the field fin (double-float,
 // or FP32 with IN32), into the double-float accumulators acc
 template <int DAG, bool IN32 = false>
@@ -503,6 +524,7 @@ __device__ __forceinline__ void df_site(const Geom& g, const float4* __restrict_
     int hb, hr;
     float cf;
     df_hop_nbr(g, blk, ds, h, hb, hr, cf);
+    if (h < 7) df_prefetch_hop<IN32>(g, U, fin, blk, r, ds, h + 1);
     // chiral-basis projection (1 + S g_mu): h_i = p_i + S ph_i p_{sigma_i}, with
     // sigma = (2, 3) or (3, 2) and phases -1 / -i (see SpinDir)
     const bool swap = mu == 1 || mu == 2;

@@ -274,6 +274,39 @@ __device__ __forceinline__ void stage_issue(const SapArgs& a, int blk, unsigned 
   }
 }
 
+// L2 prefetch of a contiguous range (16-byte aligned start and size)
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// What a block reads only after its staging and block solve: the faces its
+// eight neighbours wrote in the previous half-sweep and its accumulated
+// solution.  With one CTA per SM nothing overlaps those loads, so the lanes of
+// warp 1 ask for them in L2 at the start (one range per face, chunk and
+// direction; the block's solution is one range), where the later loads find them.
+template <typename T, int PS>
+__device__ __forceinline__ void prefetch_late_reads(const SapArgs& a, const void* faces, const FieldPtr& psi, int blk,
+                                                    const int n[4]) {
+  const Geom& g = a.g;
+  const int lane = threadIdx.x & 31;
+  constexpr int NCF = FaceChunks<T>::n;
+  if (a.faces_in) {
+    for (int t = lane; t < 8 * NCF; t += 32) {
+      const int f = t / NCF, k = t - f * NCF, mu = f >> 1;
+      const int nmu = mu == 0 ? n[0] : (mu == 1 ? n[1] : (mu == 2 ? n[2] : n[3]));  // no local-memory copy of n
+      // face 2 mu comes from the block at +mu, face 2 mu + 1 from the block at -mu
+      const int nbk = (f & 1) == 0 ? (nmu + 1 < g.nb[mu] ? blk + g.bstr[mu] : blk - (g.nb[mu] - 1) * g.bstr[mu])
+                                   : (nmu > 0 ? blk - g.bstr[mu] : blk + (g.nb[mu] - 1) * g.bstr[mu]);
+      const long long e = (long long)nbk * NCF * a.F + (long long)k * a.F + a.fo[f];
+      prefetch_l2((const char*)faces + 16 * e, (uint32_t)(16 * (g.Vb / g.b[mu])));
+    }
+  }
+  if ((a.psi_mode == 1 || a.psi_mode == 3) && lane == 31) {
+    constexpr int NCH = PS == P64 ? 12 : 6;  // 16-byte chunks per site
+    prefetch_l2((const char*)psi.data + (size_t)16 * NCH * g.Vb * blk, (uint32_t)(16 * NCH * g.Vb));
+  }
+}
+
 // rebuild the compressed 16-bit links of the landing zone (rows 0-1, layout of
 // the storage format) into full 16-bit matrices (HalfExpStage layout)
 template <int P>
@@ -913,6 +946,8 @@ __global__ void __launch_bounds__(512) sap_sweep_kernel(SapArgs a) {
 #pragma unroll 1
   for (int rr = rhs0; rr < rhs1; ++rr) {
     if (TILED && a.mask != nullptr && a.mask[rr] == 0) continue;  // uniform across the CTA
+    if (threadIdx.x >= 32 && threadIdx.x < 64)
+      prefetch_late_reads<T, PsiPrec<P>::value>(a, rhs_faces(a, rr), rhs_psi(a, rr), blk, n);
 
     // ---- residual of the two sites (own halves only: the pair's two threads
     // read complementary halves)
