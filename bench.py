@@ -240,8 +240,9 @@ def oracle_iteration_seconds(w, U, b):
 
 
 # the Schwarz block shape the autotuner picks on these workloads (complete
-# solves: 8x4x4x4 76.8 ms against 4^4 83.3 ms on 32^3x64) and the FP64
-# recursion's iteration count with it; the oracle legs run the same method
+# solves on 32^3x64 with the double-float recursion: 8x4x4x4 44.3 ms against
+# 4^4 47.4 ms) and the iteration count with it (6, as with the FP64
+# recursion); the oracle legs run the same method
 REFERENCE_BLOCK = (8, 4, 4, 4)
 
 
@@ -265,9 +266,9 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "dims": list(w["dims"]), "block": list(w["block"]),
-                       "m0": w["m0"], "csw": w["csw"], "ncy": w["ncy"], "nmr": w["nmr"], "nkv": w["nkv"],
-                       "tol": 1e-10, "sap_prec": "f64 (oracle)", "outer_prec": "f64"},
+            "config": {"workload": args.workload, "dims": list(w["dims"]), "block": list(w["block"]), "m0": w["m0"],
+                       "csw": w["csw"], "eps": w["eps"], "seed": w["seed"], "tol": 1e-10, "nkv": w["nkv"],
+                       "ncy": w["ncy"], "nmr": w["nmr"], "sap_prec": "f64 (oracle)", "outer_prec": "f64"},
             "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
